@@ -76,7 +76,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
  * paper does not say how its benchmark draws random numbers).
  *   stream 0: connection (target, k)      -> words: source, delay, 2 normal
  *   stream 1: initial membrane potential  (neuron, 0)
- *   stream 2: Poisson drive               (neuron, step) */
+ *   stream 2: Poisson drive               (neuron, step / 4), word step % 4 */
 static void orc_draw(uint64_t seed, uint32_t a, uint64_t b, uint32_t stream,
                      uint32_t out[4]) {
   uint32_t ctr[4] = {a, (uint32_t)b, (uint32_t)(b >> 32), stream};
@@ -208,11 +208,14 @@ static int orc_poisson_from_u32(uint32_t u, const uint64_t* thr, int n) {
   return k;
 }
 
+/* One Philox call yields four words; the drive of neuron i at step t uses
+ * word (t mod 4) of the call at counter (i, floor(t / 4)) on stream 2. */
 int orc_poisson_count(uint64_t seed, uint32_t neuron, int64_t step,
                       const uint64_t* thr, int n) {
   uint32_t r[4];
-  orc_draw(seed, neuron, (uint64_t)step, 2u, r);
-  return orc_poisson_from_u32(r[0], thr, n);
+  int64_t block = step >= 0 ? step / 4 : -((-step + 3) / 4);
+  orc_draw(seed, neuron, (uint64_t)block, 2u, r);
+  return orc_poisson_from_u32(r[(int)(step - 4 * block)], thr, n);
 }
 
 /* Initial potential: V0 = V_reset + (V_th - V_reset) u, u = x 2^-32. */
