@@ -186,19 +186,24 @@ int orc_refractory_steps(const orc_neuron* nm) {
 /* ------------------------------------------------------------------------ */
 /* Poisson drive: count = min{k : u < T_k} with T_k = floor(F_k 2^32), F_k   */
 /* the Poisson(lambda) CDF and u the raw 32-bit Philox word (inversion).    */
+/* The table ends at the first k whose threshold reaches 2^32 - 1 (the FP64 */
+/* CDF may never reach 1 exactly); that last threshold is set to 2^32, so    */
+/* the tail beyond it (mass below 2^-31) is folded into the last outcome.  */
 /* ------------------------------------------------------------------------ */
 int orc_poisson_table(double lambda, uint64_t* thr, int cap) {
   double p = exp(-lambda), F = p;
   int n = 0;
   for (int k = 0; k < cap; ++k) {
     double T = floor(F * 4294967296.0);
-    if (T >= 4294967296.0) T = 4294967296.0;
+    if (T >= 4294967295.0) {
+      thr[n++] = 4294967296ull;
+      return n;
+    }
     thr[n++] = (uint64_t)T;
-    if (T >= 4294967296.0) break;
     p *= lambda / (double)(k + 1);
     F += p;
   }
-  if (thr[n - 1] < 4294967296ull) thr[n - 1] = 4294967296ull; /* close tail */
+  thr[n - 1] = 4294967296ull; /* cap reached: close the table */
   return n;
 }
 
@@ -267,6 +272,14 @@ void orc_draw_synapse(const orc_conn* cp, uint32_t tgt, uint32_t k,
   if (cp->wfmt == 1) x = orc_round_f32(x);
   else if (cp->wfmt == 2) x = orc_round_bf16(x);
   *w = x;
+}
+
+/* The K_E + K_I incoming synapses of one target, in draw order k. */
+void orc_incoming(const orc_conn* cp, uint32_t tgt, uint32_t* src,
+                  int32_t* delay, double* w) {
+  uint32_t kk = cp->k_e + cp->k_i;
+  for (uint32_t k = 0; k < kk; ++k)
+    orc_draw_synapse(cp, tgt, k, &src[k], &delay[k], &w[k]);
 }
 
 /* Full source-major store.  Segments are ordered by (delay, target, k):
