@@ -1,0 +1,269 @@
+/*
+ * snn.h -- C ABI of libsnn: spike delivery and neuron update for a
+ * time-driven simulation of a balanced random network of current-based
+ * leaky integrate-and-fire neurons with alpha-shaped synaptic currents,
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the one studied in arXiv 2109.12855 ("Routing brain traffic
+ * through the von Neumann bottleneck"): neurons are updated on a fixed time
+ * grid (Section 2.1); once per min-delay interval the spikes emitted in that
+ * interval are delivered, each spike walking its source's target segment
+ * and adding every synapse's weight into the target neuron's spike ring
+ * buffer at (emission step + delay) (Section 3.2, Algorithm REF; Section 3.1,
+ * Fig. 3 for the data structures).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns an int status: SNN_OK (0) or a negative SNN_E_* code.
+ *    snn_last_error() returns a message for the calling thread's last error.
+ *  - A net handle is opaque; the library owns all device memory behind it
+ *    (allocated with cudaMalloc on the current device at snn_create and at
+ *    connection time) and frees it in snn_destroy.
+ *  - Caller buffers are borrowed for the duration of the call only.  Each
+ *    buffer argument is accompanied by a `mem` flag: SNN_MEM_HOST (pageable
+ *    or pinned host memory) or SNN_MEM_DEVICE (device memory of the net's
+ *    device, e.g. a PyTorch CUDA tensor's data pointer).
+ *  - Work is enqueued on the stream given to snn_create (a cudaStream_t
+ *    passed as void*; NULL is the legacy default stream).  Calls that write
+ *    to host memory, or return counts, synchronise that stream; all others
+ *    are asynchronous.
+ *  - Neuron i in [0, n_exc) is excitatory, [n_exc, n_exc + n_inh) inhibitory.
+ *  - Time is counted in integer grid steps of h ms.  The ring buffer has
+ *    n_slots slots (a power of two); absolute step u uses slot u mod n_slots.
+ *  - Not thread-safe per net: one host thread at a time per handle.
+ */
+#ifndef SNN_H
+#define SNN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SNN_ABI_VERSION 1
+
+/* Status codes. */
+enum {
+  SNN_OK = 0,
+  SNN_E_OOM = -1,      /* device or host allocation failed */
+  SNN_E_ARG = -2,      /* invalid argument (null pointer, size, range) */
+  SNN_E_STATE = -3,    /* call not valid in the net's current state */
+  SNN_E_TIMEOUT = -4,  /* a bounded device wait gave up */
+  SNN_E_OVERFLOW = -5, /* an output did not fit; data was truncated */
+  SNN_E_CUDA = -6      /* a CUDA runtime call failed */
+};
+
+/* Memory kinds for caller buffers. */
+enum { SNN_MEM_HOST = 0, SNN_MEM_DEVICE = 1 };
+
+/* Synapse record formats of the connection store.
+ *  SNN_W_FP32_12B: 12 bytes {uint32 target; float32 weight; uint8 delay;
+ *                  3 pad bytes}.
+ *  SNN_W_BF16_8B:  8 bytes {uint32 target; uint8 delay; uint8 pad;
+ *                  bfloat16 weight}; weights are rounded FP64 -> BF16 to
+ *                  nearest, ties to even, in one step.
+ * Both accumulate into a float32 ring buffer. */
+enum { SNN_W_FP32_12B = 0, SNN_W_BF16_8B = 1 };
+
+/* Device error flags (snn_stats.error_flags, sticky until snn_clear_errors). */
+enum {
+  SNN_ERRF_SPIKE_LIST = 1u << 0, /* interval spike list overflowed */
+  SNN_ERRF_SPIKE_LOG = 1u << 1,  /* spike recording log overflowed */
+  SNN_ERRF_BAD_SOURCE = 1u << 2, /* external spike with source >= N */
+  SNN_ERRF_CHUNKS = 1u << 3      /* chunk counter of one interval overflowed */
+};
+
+/* Neuron model and simulation parameters (iaf_psc_alpha, resting potential
+ * 0 mV; Section 1 and Section 2.1 of the paper: linear subthreshold
+ * dynamics integrated exactly, threshold, reset, refractory period).
+ *   dV/dt = -V/tau_m + I/C;  dI/dt = -I/tau_syn + J;  dJ/dt = -J/tau_syn;
+ *   an arriving weight w (pA) adds (e/tau_syn) w to J (PSC peak = w).
+ * One step t: (1) V <- P31 J + P32 I + P33 V unless refractory (then the
+ * refractory count decreases); (2) I <- P21 J + P22 I, J <- P11 J;
+ * (3) J += (e/tau_syn)(rb[t] + w_ext * Poisson(nu_ext h)), rb[t] <- 0;
+ * (4) if V >= v_th: V <- v_reset, refractory for round(t_ref/h) steps, spike.
+ * State is float32 on the device; the propagator entries are computed in
+ * FP64 on the host once and rounded to float32. */
+typedef struct snn_params {
+  uint32_t n_exc, n_inh;  /* population sizes; n_exc + n_inh in [1, 2^24) */
+  double h;               /* grid step, ms (> 0) */
+  double tau_m;           /* membrane time constant, ms */
+  double c_m;             /* membrane capacitance, pF */
+  double v_th;            /* threshold, mV */
+  double v_reset;         /* reset potential, mV */
+  double t_ref;           /* refractory period, ms */
+  double tau_syn;         /* synaptic time constant, ms (!= tau_m) */
+  double nu_ext;          /* Poisson drive rate per neuron, Hz (>= 0) */
+  double w_ext;           /* weight of one drive spike, pA */
+  uint64_t seed;          /* initial potentials (stream 1), drive (stream 2) */
+  int32_t weight_format;  /* SNN_W_FP32_12B or SNN_W_BF16_8B */
+  int32_t n_slots;        /* ring-buffer slots: power of two in [2, 256] */
+  int32_t interval;       /* steps per update/deliver interval; 0 = the
+                             minimum delay of the connections */
+  int32_t init_v_random;  /* 1: V0 ~ U[v_reset, v_th) from Philox stream 1;
+                             0: V0 = 0 */
+  int32_t count_events;   /* 1: keep a uint32 [n_slots][N] per-cell count of
+                             delivered events (test instrument) */
+  int32_t pad_;
+  uint64_t spike_log_capacity; /* entries kept for snn_read_spikes (0: none) */
+} snn_params;
+
+/* Fixed in-degree connection rule (the benchmark model's random
+ * connectivity, Section 2.2).  Every target j draws k_exc sources uniformly
+ * from the excitatory and k_inh from the inhibitory population, with
+ * replacement (multapses and autapses allowed).  Draw k of target j uses
+ * Philox4x32-10 (Salmon et al., SC'11) with counter (j, k, 0, 0) and key
+ * (seed low, seed high): word 0 -> source floor(u N_pop 2^-32) (+ n_exc for
+ * inhibitory draws, k >= k_exc), word 1 -> delay d_lo + floor(u (d_hi-d_lo+1)
+ * 2^-32) steps, words 2, 3 -> Box-Muller normal z when sd != 0 (w = mean +
+ * sd z, computed in FP64, then clipped if requested, then rounded to the
+ * store's format). */
+typedef struct snn_conn_params {
+  uint32_t k_exc, k_inh;  /* in-degree per target from each population */
+  double w_exc, w_inh;    /* mean weights, pA */
+  double sd_exc, sd_inh;  /* weight standard deviations, pA (0: fixed) */
+  int32_t d_lo, d_hi;     /* delay range in steps, 1 <= d_lo <= d_hi <= n_slots,
+                             d_hi <= 255 */
+  uint64_t seed;          /* connectivity key */
+  int32_t clip_exc;       /* 1: excitatory weights clipped at >= 0 */
+  int32_t clip_inh;       /* 1: inhibitory weights clipped at <= 0 */
+} snn_conn_params;
+
+/* Counters and timings of a net. */
+typedef struct snn_stats {
+  uint64_t events_delivered; /* synaptic events added into ring buffers */
+  uint64_t spikes;           /* spikes emitted by snn_update/snn_simulate */
+  uint64_t n_synapses;       /* synapses in the store */
+  int64_t t_now;             /* next step to be updated */
+  int32_t interval;          /* steps per interval */
+  int32_t min_delay, max_delay;
+  uint32_t error_flags;      /* SNN_ERRF_* */
+  uint64_t kernel_launches;  /* library kernels launched since creation */
+  uint64_t update_launches, deliver_launches;
+  double ms_update, ms_deliver; /* CUDA-event times while profiling is on */
+  uint64_t bytes_per_record;    /* 12 or 8 */
+  uint64_t store_bytes;         /* device bytes of the record array */
+} snn_stats;
+
+typedef struct snn_net snn_net;
+
+/* Library identity and diagnostics. */
+int snn_abi_version(void);
+const char* snn_last_error(void);
+
+/* Fill *p with the benchmark defaults: 1,000 E + 250 I neurons, h = 0.1 ms,
+ * tau_m = 10 ms, C = 250 pF, V_th = 20 mV, V_reset = 0, t_ref = 2 ms,
+ * tau_syn = 0.5 ms, no drive, FP32 records, 32 slots, random V0. */
+int snn_default_params(snn_params* p);
+
+/* PSC amplitude w (pA) whose membrane response peaks at psp_mv (mV) for the
+ * neuron model in *p ("J = 0.1 mV" weights of the benchmark model are given
+ * as peak PSP amplitudes).  Host-only arithmetic; needs no GPU. */
+int snn_psc_weight_for_psp(const snn_params* p, double psp_mv, double* w_pa);
+
+/* Create a net on the current CUDA device.  Allocates neuron state (SoA
+ * float32 V, I, J and int32 refractory counts), the ring buffer
+ * rb[n_slots][N] (float32, zeroed) and, if requested, the event counts and
+ * the spike log.  Initial V per init_v_random.  stream: cudaStream_t as
+ * void*.  Errors: SNN_E_ARG (bad parameter), SNN_E_OOM, SNN_E_CUDA. */
+int snn_create(const snn_params* p, void* stream, snn_net** out);
+
+/* Build the connection store from the fixed in-degree rule (see
+ * snn_conn_params) on the device: count out-degrees, prefix-sum them into
+ * row offsets, scatter, sort every target segment by (delay, target, k) and
+ * pack records (Section 3.1: source-specific target segments).  One connect
+ * call per net.  Errors: SNN_E_STATE (already connected), SNN_E_ARG,
+ * SNN_E_OOM. */
+int snn_connect_fixed_indegree(snn_net* net, const snn_conn_params* c);
+
+/* Build the store from an explicit edge list of n edges: edge e connects
+ * src[e] -> tgt[e] with delay[e] steps (1 <= delay <= min(n_slots, 255)) and
+ * weight w[e] pA (rounded to the store's format).  Segments are sorted by
+ * (delay, target, e).  Requires n < 2^32.  mem: where the four arrays live.
+ * Errors: SNN_E_STATE, SNN_E_ARG (index or delay out of range), SNN_E_OOM. */
+int snn_connect_edges(snn_net* net, const uint32_t* src, const uint32_t* tgt,
+                      const uint8_t* delay, const double* w, uint64_t n,
+                      int mem);
+
+/* Freeze the store and size the interval buffers: interval = params.interval
+ * or the minimum delay (n_slots when there are no synapses); requires
+ * interval <= min delay and max delay <= n_slots.  Must precede update,
+ * deliver and simulate.  Errors: SNN_E_STATE, SNN_E_ARG, SNN_E_OOM. */
+int snn_finalize(snn_net* net);
+
+/* Update all neurons for n_steps (1 <= n_steps <= interval) grid steps
+ * starting at absolute step t0 (Section 2.1), reading and clearing ring
+ * buffer slots t0 .. t0+n_steps-1.  Spikes go to the pending interval list
+ * (and to the log).  Errors: SNN_E_STATE if spikes of an earlier update are
+ * still pending (deliver or discard them first), SNN_E_ARG. */
+int snn_update(snn_net* net, int64_t t0, int32_t n_steps);
+
+/* Deliver the pending interval list produced by snn_update (Algorithm REF
+ * semantics), or drop it.  Asynchronous. */
+int snn_deliver_pending(snn_net* net);
+int snn_discard_pending(snn_net* net);
+
+/* Deliver an external spike list (Section 3.2, Algorithm REF): for every
+ * spike s and every synapse (src[s] -> target, delay d, weight w) in the
+ * source's segment, rb[(t_emit[s] + d) mod n_slots][target] += w in float32.
+ * src, t_emit: n_spikes entries in `mem` memory; duplicates allowed.
+ * n_events_out (optional, host): number of additions; when non-null the
+ * call synchronises.  A source >= N is skipped and sets SNN_ERRF_BAD_SOURCE
+ * (host inputs are checked up front and give SNN_E_ARG). */
+int snn_deliver(snn_net* net, const uint32_t* src, const int32_t* t_emit,
+                uint32_t n_spikes, int mem, uint64_t* n_events_out);
+
+/* Advance the net by n_steps grid steps from its current time: repeat
+ * {update one interval; deliver its spikes} (the time-driven cycle of
+ * Section 1); the last interval may be shorter.  Full intervals run as
+ * captured CUDA graphs unless profiling is on.  Asynchronous. */
+int snn_simulate(snn_net* net, int64_t n_steps);
+
+/* Copy up to cap logged spikes (source, step) in emission-interval order
+ * (order within an interval unspecified) into src/t and clear the log;
+ * *n receives the number logged (> cap: the rest are dropped and the call
+ * returns SNN_E_OVERFLOW).  Synchronises. */
+int snn_read_spikes(snn_net* net, uint32_t* src, int32_t* t, uint64_t cap,
+                    uint64_t* n, int mem);
+
+/* Ring buffer as float32 [n_slots][N] (row u holds slot u).  Read
+ * synchronises for host memory. */
+int snn_read_rb(snn_net* net, float* dst, int mem);
+int snn_write_rb(snn_net* net, const float* src, int mem);
+/* Event counts as uint32 [n_slots][N] (requires count_events). */
+int snn_read_counts(snn_net* net, uint32_t* dst, int mem);
+/* Zero the ring buffer and the event counts. */
+int snn_clear_rb(snn_net* net);
+
+/* Neuron state, N entries each (float32 V mV, I pA, J pA/ms; int32
+ * remaining refractory steps).  Any pointer may be NULL to skip it. */
+int snn_read_state(snn_net* net, float* V, float* I, float* J, int32_t* refr,
+                   int mem);
+int snn_write_state(snn_net* net, const float* V, const float* I,
+                    const float* J, const int32_t* refr, int mem);
+
+/* The finalized store: row_ptr uint64 [N+1]; per synapse target uint32,
+ * delay uint8 and weight widened to float32 (n_synapses entries each).
+ * Synchronises for host memory. */
+int snn_read_store(snn_net* net, uint64_t* row_ptr, uint32_t* tgt,
+                   uint8_t* delay, float* w, int mem);
+
+/* Set the step counter (next step to update). */
+int snn_set_time(snn_net* net, int64_t t);
+/* Profiling on: every update and deliver launch is bracketed by CUDA events
+ * on the net's stream and graphs are not used; times accumulate into
+ * snn_stats.ms_update / ms_deliver. */
+int snn_set_profiling(snn_net* net, int on);
+/* Counters (synchronises). */
+int snn_get_stats(snn_net* net, snn_stats* out);
+int snn_clear_errors(snn_net* net);
+/* Wait for all work of the net. */
+int snn_sync(snn_net* net);
+/* Free everything; net may be NULL. */
+int snn_destroy(snn_net* net);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNN_H */

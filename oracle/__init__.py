@@ -104,6 +104,7 @@ def _declare(lib):
     lib.orc_init_v.argtypes = [C.POINTER(NeuronC), C.c_uint32, C.c_uint64, _P]
     lib.orc_draw_synapse.argtypes = [C.POINTER(ConnC), C.c_uint32, C.c_uint32,
                                      _P, _P, _P]
+    lib.orc_incoming.argtypes = [C.POINTER(ConnC), C.c_uint32, _P, _P, _P]
     lib.orc_build_fixed_indegree.argtypes = [C.POINTER(ConnC), _P, _P, _P, _P]
     lib.orc_build_fixed_indegree.restype = C.c_int
     lib.orc_build_fixed_indegree_targets.argtypes = [
@@ -271,12 +272,11 @@ def draw_synapse(cp: Conn, tgt: int, k: int):
 def incoming(cp: Conn, tgt: int):
     """All K_E + K_I incoming synapses of one target: (src, delay, w) arrays."""
     kk = cp.k_e + cp.k_i
-    src = np.zeros(kk, np.uint32)
-    dl = np.zeros(kk, np.int32)
-    w = np.zeros(kk)
-    for k in range(kk):
-        src[k], dl[k], w[k] = draw_synapse(cp, tgt, k)
-    return src, dl, w
+    src = np.zeros(max(kk, 1), np.uint32)
+    dl = np.zeros(max(kk, 1), np.int32)
+    w = np.zeros(max(kk, 1))
+    _load().orc_incoming(C.byref(cp.c()), tgt, _ptr(src), _ptr(dl), _ptr(w))
+    return src[:kk], dl[:kk], w[:kk]
 
 
 def build_fixed_indegree(cp: Conn) -> Store:

@@ -1,0 +1,1057 @@
+// snn_api.cu -- host side of the libsnn C ABI (declared in include/snn.h).
+//
+// Owns every device allocation of a net, drives the construction pipeline
+// (snn_build.cu) and the interval loop update -> deliver (snn_kernels.cu),
+// captures full intervals into CUDA graphs, and implements the read-back,
+// state and statistics calls.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "snn_internal.cuh"
+
+using namespace snn;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                            \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess)                                                  \
+      return fail(e_ == cudaErrorMemoryAllocation ? SNN_E_OOM : SNN_E_CUDA, \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                  __FILE__, __LINE__);                                      \
+  } while (0)
+
+#define REQ(cond, code, ...)                  \
+  do {                                        \
+    if (!(cond)) return fail(code, __VA_ARGS__); \
+  } while (0)
+
+constexpr uint32_t kSortCap = 16384;  // must match k_sort_pack's shared cap
+constexpr int kGraphIntervals = 8;
+
+// ---------------------------------------------------------------------------
+// Neuron constants, computed in FP64.
+// ---------------------------------------------------------------------------
+// exp(M) of a 3x3 matrix by scaling and squaring with a Taylor series.
+void expm3(const double A[3][3], double E[3][3]) {
+  double norm = 0;
+  for (int c = 0; c < 3; ++c) {
+    double s = 0;
+    for (int r = 0; r < 3; ++r) s += fabs(A[r][c]);
+    norm = std::max(norm, s);
+  }
+  int sq = 0;
+  while (norm / ldexp(1.0, sq) > 0.25) ++sq;
+  double B[3][3], T[3][3], S[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      B[r][c] = ldexp(A[r][c], -sq);
+      T[r][c] = (r == c) ? 1.0 : 0.0;   // current term B^k / k!
+      S[r][c] = T[r][c];
+    }
+  for (int k = 1; k < 30; ++k) {
+    double N[3][3] = {};
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        double acc = 0;
+        for (int q = 0; q < 3; ++q) acc += T[r][q] * B[q][c];
+        N[r][c] = acc / k;
+      }
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        T[r][c] = N[r][c];
+        S[r][c] += N[r][c];
+      }
+  }
+  for (int i = 0; i < sq; ++i) {
+    double N[3][3] = {};
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c)
+        for (int q = 0; q < 3; ++q) N[r][c] += S[r][q] * S[q][c];
+    memcpy(S, N, sizeof S);
+  }
+  memcpy(E, S, sizeof S);
+}
+
+// Poisson(lam) inversion thresholds floor(F_k 2^32) for k = 0, 1, ... up to
+// the first that reaches 2^32 - 1; that outcome takes the rest of the unit
+// interval (its threshold is implicit on the device).  Returns the number of
+// outcomes (thresholds + 1), or -1 if more than cap are needed.
+int poisson_thresholds(double lam, uint32_t* thr, int cap) {
+  double pk = exp(-lam), F = pk;
+  for (int k = 0; k < cap; ++k) {
+    double T = floor(F * 4294967296.0);
+    if (T >= 4294967295.0) return k + 1;
+    thr[k] = (uint32_t)T;
+    pk *= lam / (double)(k + 1);
+    F += pk;
+  }
+  return -1;
+}
+
+int make_upd_const(const snn_params& p, UpdConst* c) {
+  memset(c, 0, sizeof *c);
+  const double a = 1.0 / p.tau_syn, b = 1.0 / p.tau_m;
+  // state (J, I, V): J' = -a J; I' = J - a I; V' = I / C - b V
+  double A[3][3] = {{-a * p.h, 0, 0}, {p.h, -a * p.h, 0},
+                    {0, p.h / p.c_m, -b * p.h}};
+  double E[3][3];
+  expm3(A, E);
+  c->p11 = (float)E[0][0];
+  c->p21 = (float)E[1][0];
+  c->p22 = (float)E[1][1];
+  c->p31 = (float)E[2][0];
+  c->p32 = (float)E[2][1];
+  c->p33 = (float)E[2][2];
+  c->psc = (float)(M_E / p.tau_syn);
+  c->v_th = (float)p.v_th;
+  c->v_reset = (float)p.v_reset;
+  c->w_ext = (float)p.w_ext;
+  c->refr_steps = (int)llround(p.t_ref / p.h);
+  c->seed = p.seed;
+  c->n_thr = 0;
+  if (p.nu_ext > 0.0 && p.w_ext != 0.0) {
+    int n = poisson_thresholds(p.nu_ext * p.h * 1e-3, c->thr, kMaxPoisson);
+    if (n < 0) return -1;
+    c->n_thr = n;
+  }
+  return 0;
+}
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// The net.
+// ---------------------------------------------------------------------------
+struct snn_net {
+  snn_params p{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  uint32_t n = 0, pitch = 0;
+  int fmt = 0, n_slots = 0;
+  UpdConst uc{};
+  float *V = nullptr, *I = nullptr, *J = nullptr;
+  int32_t* refr = nullptr;
+  float* rb = nullptr;
+  uint32_t* counts = nullptr;
+  Ctl* ctl = nullptr;
+  uint64_t* row_ptr = nullptr;
+  void* recs = nullptr;
+  uint64_t n_syn = 0, recs_bytes = 0;
+  SpikeEntry* list = nullptr;
+  uint64_t list_cap = 0;
+  SpikeEntry* ext_list = nullptr;
+  uint32_t* ext_src = nullptr;
+  int32_t* ext_t = nullptr;
+  uint64_t ext_cap = 0;
+  uint32_t* log_src = nullptr;
+  int32_t* log_t = nullptr;
+  uint64_t log_cap = 0;
+  bool connected = false, finalized = false, pending = false;
+  int interval = 0, dmin = 0, dmax = 0;
+  long long t_host = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;
+  double ms_update = 0, ms_deliver = 0;
+  uint64_t launches = 0, upd_launches = 0, del_launches = 0;
+  cudaGraphExec_t graph = nullptr;
+
+  NetView view() const {
+    NetView v;
+    v.n = n;
+    v.pitch = pitch;
+    v.slot_mask = (uint32_t)n_slots - 1u;
+    v.chunk = (uint32_t)chunk_records(fmt);
+    v.fmt = fmt;
+    v.V = V;
+    v.I = I;
+    v.J = J;
+    v.refr = refr;
+    v.rb = rb;
+    v.counts = counts;
+    v.row_ptr = row_ptr;
+    v.recs = recs;
+    v.list = list;
+    v.list_cap = list_cap;
+    v.log_src = log_src;
+    v.log_t = log_t;
+    v.log_cap = log_cap;
+    v.ctl = ctl;
+    return v;
+  }
+};
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(T** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+cudaMemcpyKind kind_to(int mem) {
+  return mem == SNN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+}
+cudaMemcpyKind kind_from(int mem) {
+  return mem == SNN_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+}
+
+int check_mem(int mem) {
+  return mem == SNN_MEM_HOST || mem == SNN_MEM_DEVICE;
+}
+
+int set_device(snn_net* net) {
+  CK(cudaSetDevice(net->device));
+  return SNN_OK;
+}
+
+// Build the store from per-row key arrays: host row offsets from the device
+// out-degrees, scatter (callback), sort and pack.
+template <class Scatter>
+int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
+                const BuildFixed* bf, const double* d_edge_w) {
+  cudaStream_t s = net->stream;
+  const uint32_t n = net->n;
+  std::vector<uint32_t> deg(n);
+  CK(cudaMemcpyAsync(deg.data(), d_deg, n * sizeof(uint32_t),
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<uint64_t> rp(n + 1, 0);
+  uint32_t max_row = 0;
+  std::vector<uint32_t> long_rows;
+  std::vector<uint64_t> long_off;
+  uint64_t scratch = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    rp[i + 1] = rp[i] + deg[i];
+    max_row = std::max(max_row, deg[i]);
+    if (deg[i] > kSortCap) {
+      long_rows.push_back(i);
+      long_off.push_back(scratch);
+      uint64_t P = 1;
+      while (P < deg[i]) P <<= 1;
+      scratch += P;
+    }
+  }
+  const uint64_t n_syn = rp[n];
+  const uint32_t ch = (uint32_t)chunk_records(net->fmt);
+  const uint64_t padded = (n_syn + ch - 1) / ch * ch + ch;
+  const int rec_bytes = net->fmt == SNN_W_FP32_12B ? 12 : 8;
+  CK(dalloc(&net->row_ptr, (n + 1) * sizeof(uint64_t)));
+  CK(cudaMemcpyAsync(net->row_ptr, rp.data(), (n + 1) * sizeof(uint64_t),
+                     cudaMemcpyHostToDevice, s));
+  // keys; for 8-byte records the key array becomes the record array
+  uint64_t* keys = nullptr;
+  CK(dalloc(&keys, padded * sizeof(uint64_t)));
+  uint32_t* cursor = d_deg;  // reuse as the scatter cursor
+  CK(cudaMemsetAsync(cursor, 0, n * sizeof(uint32_t), s));
+  CK(scatter(net->row_ptr, cursor, keys));
+  void* recs = nullptr;
+  if (rec_bytes == 8) {
+    recs = keys;
+  } else {
+    cudaError_t e = dalloc(&recs, padded * rec_bytes);
+    if (e != cudaSuccess) {
+      dfree(keys);
+      return fail(SNN_E_OOM, "store allocation of %llu bytes failed",
+                  (unsigned long long)(padded * rec_bytes));
+    }
+  }
+  // zero the padding records once (target 0, weight 0; never delivered)
+  CK(cudaMemsetAsync(static_cast<char*>(recs) + n_syn * rec_bytes, 0,
+                     (padded - n_syn) * rec_bytes, s));
+  uint32_t* d_long = nullptr;
+  uint64_t *d_loff = nullptr, *d_scr = nullptr;
+  if (!long_rows.empty()) {
+    CK(dalloc(&d_long, long_rows.size() * sizeof(uint32_t)));
+    CK(dalloc(&d_loff, long_off.size() * sizeof(uint64_t)));
+    CK(dalloc(&d_scr, scratch * sizeof(uint64_t)));
+    CK(cudaMemcpyAsync(d_long, long_rows.data(),
+                       long_rows.size() * sizeof(uint32_t),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_loff, long_off.data(),
+                       long_off.size() * sizeof(uint64_t),
+                       cudaMemcpyHostToDevice, s));
+  }
+  CK(build_sort_pack(net->fmt, n, net->row_ptr, keys, recs, bf, d_edge_w,
+                     max_row, d_long, (uint32_t)long_rows.size(), d_scr,
+                     d_loff, s));
+  CK(cudaStreamSynchronize(s));
+  if (recs != keys) dfree(keys);
+  dfree(d_long);
+  dfree(d_loff);
+  dfree(d_scr);
+  net->recs = recs;
+  net->n_syn = n_syn;
+  net->recs_bytes = padded * rec_bytes;
+  net->connected = true;
+  return SNN_OK;
+}
+
+int ensure_ext(snn_net* net, uint64_t n) {
+  if (n <= net->ext_cap) return SNN_OK;
+  uint64_t cap = std::max<uint64_t>(n, 2 * net->ext_cap);
+  dfree(net->ext_list);
+  dfree(net->ext_src);
+  dfree(net->ext_t);
+  net->ext_list = nullptr;
+  net->ext_src = nullptr;
+  net->ext_t = nullptr;
+  net->ext_cap = 0;
+  CK(dalloc(&net->ext_list, cap * sizeof(SpikeEntry)));
+  CK(dalloc(&net->ext_src, cap * sizeof(uint32_t)));
+  CK(dalloc(&net->ext_t, cap * sizeof(int32_t)));
+  net->ext_cap = cap;
+  return SNN_OK;
+}
+
+cudaEvent_t pool_event(snn_net* net, size_t k) {
+  while (net->ev.size() <= k) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    net->ev.push_back(e);
+  }
+  return net->ev[k];
+}
+
+// One interval: update (time from the control block) then deliver.
+int launch_interval(snn_net* net, int steps) {
+  NetView v = net->view();
+  CK(launch_update(v, net->uc, steps, 1, 0, net->stream));
+  CK(launch_deliver(v, &net->ctl->pair, &net->ctl->done, net->list, 1,
+                    net->stream));
+  net->launches += 2;
+  net->upd_launches += 1;
+  net->del_launches += 1;
+  return SNN_OK;
+}
+
+int capture_graph(snn_net* net) {
+  if (net->graph) return SNN_OK;
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
+  NetView v = net->view();
+  for (int k = 0; k < kGraphIntervals; ++k) {
+    cudaError_t e1 = launch_update(v, net->uc, net->interval, 1, 0, net->stream);
+    cudaError_t e2 = launch_deliver(v, &net->ctl->pair, &net->ctl->done,
+                                    net->list, 1, net->stream);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      cudaStreamEndCapture(net->stream, &g);
+      return fail(SNN_E_CUDA, "graph capture failed: %s",
+                  cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    }
+  }
+  CK(cudaStreamEndCapture(net->stream, &g));
+  cudaError_t e = cudaGraphInstantiate(&net->graph, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  return SNN_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int snn_abi_version(void) { return SNN_ABI_VERSION; }
+
+const char* snn_last_error(void) { return g_err.c_str(); }
+
+int snn_default_params(snn_params* p) {
+  REQ(p, SNN_E_ARG, "null params");
+  memset(p, 0, sizeof *p);
+  p->n_exc = 1000;
+  p->n_inh = 250;
+  p->h = 0.1;
+  p->tau_m = 10.0;
+  p->c_m = 250.0;
+  p->v_th = 20.0;
+  p->v_reset = 0.0;
+  p->t_ref = 2.0;
+  p->tau_syn = 0.5;
+  p->nu_ext = 0.0;
+  p->w_ext = 0.0;
+  p->seed = 1;
+  p->weight_format = SNN_W_FP32_12B;
+  p->n_slots = 32;
+  p->interval = 0;
+  p->init_v_random = 1;
+  p->count_events = 0;
+  p->spike_log_capacity = 0;
+  return SNN_OK;
+}
+
+int snn_psc_weight_for_psp(const snn_params* p, double psp_mv, double* w_pa) {
+  REQ(p && w_pa, SNN_E_ARG, "null argument");
+  REQ(p->tau_syn > 0 && p->tau_m > 0 && p->c_m > 0 && p->tau_syn != p->tau_m,
+      SNN_E_ARG, "bad time constants");
+  // Membrane response to a unit PSC: (e/tau_s)/C * f(t)/c^2 with
+  // f(t) = e^{-bt} - e^{-at}(1 + ct), a = 1/tau_s, b = 1/tau_m, c = a - b.
+  // Its maximum solves b e^{ct} = b + a c t (t > 0): g(t) = b e^{ct} - b -
+  // a c t is negative just after 0 and grows without bound; bisect it.
+  const double a = 1.0 / p->tau_syn, b = 1.0 / p->tau_m, c = a - b;
+  auto g = [&](double t) { return b * expm1(c * t) - a * c * t; };
+  double lo = 1e-12 * p->tau_syn, hi = 1e-3 * p->tau_syn;
+  while (g(hi) < 0.0) hi *= 2.0;
+  for (int it = 0; it < 400 && hi - lo > 1e-15 * hi; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (g(mid) < 0.0) lo = mid; else hi = mid;
+  }
+  const double t = 0.5 * (lo + hi);
+  const double f = exp(-b * t) - exp(-a * t) * (1.0 + c * t);
+  const double peak = (M_E / p->tau_syn) / p->c_m * f / (c * c);
+  *w_pa = psp_mv / peak;
+  return SNN_OK;
+}
+
+int snn_create(const snn_params* p, void* stream, snn_net** out) {
+  REQ(p && out, SNN_E_ARG, "null argument");
+  *out = nullptr;
+  const uint64_t n = (uint64_t)p->n_exc + p->n_inh;
+  REQ(n >= 1 && n < (1u << 24), SNN_E_ARG, "N = %llu outside [1, 2^24)",
+      (unsigned long long)n);
+  REQ(p->h > 0 && p->tau_m > 0 && p->c_m > 0 && p->tau_syn > 0 &&
+          p->tau_syn != p->tau_m && p->t_ref >= 0 && p->nu_ext >= 0,
+      SNN_E_ARG, "bad neuron parameters");
+  REQ(p->weight_format == SNN_W_FP32_12B || p->weight_format == SNN_W_BF16_8B,
+      SNN_E_ARG, "bad weight format %d", p->weight_format);
+  REQ(is_pow2(p->n_slots) && p->n_slots >= 2 && p->n_slots <= 256, SNN_E_ARG,
+      "n_slots must be a power of two in [2, 256]");
+  REQ(p->interval >= 0 && p->interval <= p->n_slots, SNN_E_ARG,
+      "bad interval");
+  snn_net* net = new snn_net();
+  net->p = *p;
+  net->n = (uint32_t)n;
+  net->pitch = (uint32_t)((n + 31) / 32 * 32);
+  net->fmt = p->weight_format;
+  net->n_slots = p->n_slots;
+  if (make_upd_const(*p, &net->uc) != 0) {
+    delete net;
+    return fail(SNN_E_ARG, "Poisson drive rate too high for the inversion table");
+  }
+  int rc = SNN_OK;
+  auto bail = [&](int code) {
+    snn_destroy(net);
+    return code;
+  };
+  if (cudaGetDevice(&net->device) != cudaSuccess)
+    return bail(fail(SNN_E_CUDA, "no CUDA device"));
+  if (stream) {
+    net->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    // a blocking stream stays ordered with the legacy default stream and,
+    // unlike it, can be captured into graphs
+    if (cudaStreamCreate(&net->stream) != cudaSuccess)
+      return bail(fail(SNN_E_CUDA, "stream creation failed"));
+    net->own_stream = true;
+  }
+  cudaStream_t s = net->stream;
+  const size_t rb_bytes = (size_t)net->n_slots * net->pitch * sizeof(float);
+#define ALLOC(ptr, bytes)                                                   \
+  do {                                                                      \
+    if (dalloc(&(ptr), (bytes)) != cudaSuccess)                             \
+      return bail(fail(SNN_E_OOM, "allocation of %zu bytes failed",        \
+                       (size_t)(bytes)));                                   \
+  } while (0)
+  ALLOC(net->V, n * sizeof(float));
+  ALLOC(net->I, n * sizeof(float));
+  ALLOC(net->J, n * sizeof(float));
+  ALLOC(net->refr, n * sizeof(int32_t));
+  ALLOC(net->rb, rb_bytes);
+  ALLOC(net->ctl, sizeof(Ctl));
+  if (p->count_events) ALLOC(net->counts, rb_bytes);
+  if (p->spike_log_capacity) {
+    ALLOC(net->log_src, p->spike_log_capacity * sizeof(uint32_t));
+    ALLOC(net->log_t, p->spike_log_capacity * sizeof(int32_t));
+    net->log_cap = p->spike_log_capacity;
+  }
+#undef ALLOC
+  if (cudaMemsetAsync(net->rb, 0, rb_bytes, s) != cudaSuccess ||
+      cudaMemsetAsync(net->ctl, 0, sizeof(Ctl), s) != cudaSuccess ||
+      (net->counts && cudaMemsetAsync(net->counts, 0, rb_bytes, s) != cudaSuccess))
+    return bail(fail(SNN_E_CUDA, "memset failed"));
+  NetView v = net->view();
+  if (launch_init_v(v, &net->uc, p->init_v_random, s) != cudaSuccess)
+    return bail(fail(SNN_E_CUDA, "init kernel launch failed"));
+  net->launches += 1;
+  if ((rc = snn_sync(net)) != SNN_OK) return bail(rc);
+  *out = net;
+  return SNN_OK;
+}
+
+int snn_connect_fixed_indegree(snn_net* net, const snn_conn_params* c) {
+  REQ(net && c, SNN_E_ARG, "null argument");
+  REQ(!net->connected && !net->finalized, SNN_E_STATE, "net already connected");
+  const snn_params& p = net->p;
+  REQ(c->d_lo >= 1 && c->d_hi >= c->d_lo && c->d_hi <= net->n_slots &&
+          c->d_hi <= 255,
+      SNN_E_ARG, "delays [%d, %d] outside [1, min(n_slots, 255)]", c->d_lo,
+      c->d_hi);
+  REQ(c->k_exc == 0 || p.n_exc > 0, SNN_E_ARG, "k_exc > 0 without E neurons");
+  REQ(c->k_inh == 0 || p.n_inh > 0, SNN_E_ARG, "k_inh > 0 without I neurons");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  BuildFixed b;
+  b.n_e = p.n_exc;
+  b.n_i = p.n_inh;
+  b.k_e = c->k_exc;
+  b.k_i = c->k_inh;
+  b.w_e = c->w_exc;
+  b.w_i = c->w_inh;
+  b.sd_e = c->sd_exc;
+  b.sd_i = c->sd_inh;
+  b.d_lo = c->d_lo;
+  b.d_hi = c->d_hi;
+  b.seed = c->seed;
+  b.clip_e = c->clip_exc;
+  b.clip_i = c->clip_inh;
+  uint32_t* deg = nullptr;
+  CK(dalloc(&deg, net->n * sizeof(uint32_t)));
+  CK(cudaMemsetAsync(deg, 0, net->n * sizeof(uint32_t), net->stream));
+  cudaError_t e = build_count_fixed(b, deg, net->stream);
+  if (e != cudaSuccess) {
+    dfree(deg);
+    CK(e);
+  }
+  cudaStream_t s = net->stream;
+  rc = build_store(
+      net, deg,
+      [&](const uint64_t* rp, uint32_t* cur, uint64_t* keys) {
+        return build_scatter_fixed(b, rp, cur, keys, s);
+      },
+      &b, nullptr);
+  dfree(deg);
+  net->launches += 3;
+  return rc;
+}
+
+int snn_connect_edges(snn_net* net, const uint32_t* src, const uint32_t* tgt,
+                      const uint8_t* delay, const double* w, uint64_t n,
+                      int mem) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(!net->connected && !net->finalized, SNN_E_STATE, "net already connected");
+  REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
+  REQ(n < (1ull << 32), SNN_E_ARG, "too many edges");
+  REQ(n == 0 || (src && tgt && delay && w), SNN_E_ARG, "null edge array");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  // validate on the host
+  std::vector<uint32_t> hs, ht;
+  std::vector<uint8_t> hd;
+  std::vector<double> hw;
+  const uint32_t *ps = src, *pt = tgt;
+  const uint8_t* pd = delay;
+  const double* pw = w;
+  if (mem == SNN_MEM_DEVICE && n) {
+    hs.resize(n);
+    ht.resize(n);
+    hd.resize(n);
+    hw.resize(n);
+    CK(cudaMemcpyAsync(hs.data(), src, n * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ht.data(), tgt, n * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hd.data(), delay, n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hw.data(), w, n * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ps = hs.data();
+    pt = ht.data();
+    pd = hd.data();
+    pw = hw.data();
+  }
+  const int dmax = std::min(net->n_slots, 255);
+  for (uint64_t e = 0; e < n; ++e) {
+    REQ(ps[e] < net->n && pt[e] < net->n, SNN_E_ARG,
+        "edge %llu: index out of range", (unsigned long long)e);
+    REQ(pd[e] >= 1 && pd[e] <= dmax, SNN_E_ARG,
+        "edge %llu: delay %d outside [1, %d]", (unsigned long long)e,
+        (int)pd[e], dmax);
+    REQ(isfinite(pw[e]), SNN_E_ARG, "edge %llu: weight not finite",
+        (unsigned long long)e);
+  }
+  uint32_t *d_src = nullptr, *d_tgt = nullptr, *deg = nullptr;
+  uint8_t* d_del = nullptr;
+  double* d_w = nullptr;
+  CK(dalloc(&d_src, n * 4));
+  CK(dalloc(&d_tgt, n * 4));
+  CK(dalloc(&d_del, n));
+  CK(dalloc(&d_w, n * 8));
+  CK(dalloc(&deg, net->n * sizeof(uint32_t)));
+  if (n) {
+    CK(cudaMemcpyAsync(d_src, ps, n * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_tgt, pt, n * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_del, pd, n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_w, pw, n * 8, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemsetAsync(deg, 0, net->n * sizeof(uint32_t), s));
+  CK(build_count_edges(d_src, n, deg, s));
+  rc = build_store(
+      net, deg,
+      [&](const uint64_t* rp, uint32_t* cur, uint64_t* keys) {
+        return build_scatter_edges(d_src, d_tgt, d_del, n, rp, cur, keys, s);
+      },
+      nullptr, d_w);
+  dfree(d_src);
+  dfree(d_tgt);
+  dfree(d_del);
+  dfree(d_w);
+  dfree(deg);
+  net->launches += 3;
+  return rc;
+}
+
+int snn_finalize(snn_net* net) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(!net->finalized, SNN_E_STATE, "already finalized");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  if (!net->connected) {
+    // a net without synapses: empty store
+    CK(dalloc(&net->row_ptr, (net->n + 1) * sizeof(uint64_t)));
+    CK(cudaMemsetAsync(net->row_ptr, 0, (net->n + 1) * sizeof(uint64_t), s));
+    CK(dalloc(&net->recs, 4096));
+    CK(cudaMemsetAsync(net->recs, 0, 4096, s));
+    net->n_syn = 0;
+    net->connected = true;
+  }
+  unsigned* dd = nullptr;
+  unsigned h[2] = {0xFFFFFFFFu, 0u};
+  CK(dalloc(&dd, 2 * sizeof(unsigned)));
+  CK(cudaMemcpyAsync(dd, h, sizeof h, cudaMemcpyHostToDevice, s));
+  CK(delay_range(net->fmt, net->recs, net->n_syn, dd, s));
+  CK(cudaMemcpyAsync(h, dd, sizeof h, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  dfree(dd);
+  net->dmin = net->n_syn ? (int)h[0] : 0;
+  net->dmax = net->n_syn ? (int)h[1] : 0;
+  int iv = net->p.interval;
+  if (iv == 0) iv = net->n_syn ? net->dmin : net->n_slots;
+  REQ(iv >= 1 && (net->n_syn == 0 || iv <= net->dmin), SNN_E_ARG,
+      "interval %d exceeds the minimum delay %d", iv, net->dmin);
+  REQ(net->dmax <= net->n_slots, SNN_E_ARG, "max delay %d exceeds n_slots %d",
+      net->dmax, net->n_slots);
+  net->interval = iv;
+  net->list_cap = (uint64_t)net->n * iv;
+  CK(dalloc(&net->list, net->list_cap * sizeof(SpikeEntry)));
+  (void)deliver_grid_size(net->fmt);
+  CK(cudaGetLastError());
+  net->finalized = true;
+  return SNN_OK;
+}
+
+int snn_update(snn_net* net, int64_t t0, int32_t n_steps) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  REQ(!net->pending, SNN_E_STATE, "spikes of the previous update are pending");
+  REQ(n_steps >= 1 && n_steps <= net->interval, SNN_E_ARG,
+      "n_steps %d outside [1, interval %d]", n_steps, net->interval);
+  REQ(t0 >= 0 && t0 + n_steps < (1ll << 31), SNN_E_ARG, "t0 out of range");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  CK(launch_update(net->view(), net->uc, n_steps, 0, t0, net->stream));
+  net->launches += 1;
+  net->upd_launches += 1;
+  net->pending = true;
+  net->t_host = t0 + n_steps;
+  return SNN_OK;
+}
+
+int snn_deliver_pending(snn_net* net) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  if (!net->pending) return SNN_OK;
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  CK(launch_deliver(net->view(), &net->ctl->pair, &net->ctl->done, net->list, 1,
+                    net->stream));
+  net->launches += 1;
+  net->del_launches += 1;
+  net->pending = false;
+  return SNN_OK;
+}
+
+int snn_discard_pending(snn_net* net) {
+  REQ(net, SNN_E_ARG, "null net");
+  if (!net->pending) return SNN_OK;
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  CK(cudaMemsetAsync(&net->ctl->pair, 0, sizeof(unsigned long long),
+                     net->stream));
+  CK(cudaMemcpyAsync(&net->ctl->t_now, &net->t_host, sizeof(long long),
+                     cudaMemcpyHostToDevice, net->stream));
+  CK(cudaStreamSynchronize(net->stream));
+  net->pending = false;
+  return SNN_OK;
+}
+
+int snn_deliver(snn_net* net, const uint32_t* src, const int32_t* t_emit,
+                uint32_t n_spikes, int mem, uint64_t* n_events_out) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
+  REQ(n_spikes == 0 || (src && t_emit), SNN_E_ARG, "null spike arrays");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  if (n_spikes == 0) {
+    if (n_events_out) *n_events_out = 0;
+    return SNN_OK;
+  }
+  if ((rc = ensure_ext(net, n_spikes)) != SNN_OK) return rc;
+  const uint32_t* d_src = src;
+  const int32_t* d_t = t_emit;
+  if (mem == SNN_MEM_HOST) {
+    for (uint32_t k = 0; k < n_spikes; ++k)
+      REQ(src[k] < net->n, SNN_E_ARG, "spike %u: source %u >= N", k, src[k]);
+    CK(cudaMemcpyAsync(net->ext_src, src, n_spikes * 4ull,
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(net->ext_t, t_emit, n_spikes * 4ull,
+                       cudaMemcpyHostToDevice, s));
+    d_src = net->ext_src;
+    d_t = net->ext_t;
+  }
+  unsigned long long ev0 = 0, ev1 = 0;
+  if (n_events_out) {
+    CK(cudaMemcpyAsync(&ev0, &net->ctl->events, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  NetView v = net->view();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (net->profiling) {
+    e0 = pool_event(net, 0);
+    e1 = pool_event(net, 1);
+  }
+  CK(launch_prepare_external(v, d_src, d_t, n_spikes, net->ext_list,
+                             &net->ctl->ext_pair, s));
+  if (e0) CK(cudaEventRecord(e0, s));
+  CK(launch_deliver(v, &net->ctl->ext_pair, &net->ctl->ext_done, net->ext_list,
+                    0, s));
+  if (e1) CK(cudaEventRecord(e1, s));
+  net->launches += 2;
+  net->del_launches += 1;
+  if (e1) {
+    float ms = 0;
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    net->ms_deliver += ms;
+  }
+  if (n_events_out) {
+    CK(cudaMemcpyAsync(&ev1, &net->ctl->events, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *n_events_out = ev1 - ev0;
+  }
+  return SNN_OK;
+}
+
+int snn_simulate(snn_net* net, int64_t n_steps) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  REQ(!net->pending, SNN_E_STATE, "spikes of an update are pending");
+  REQ(n_steps >= 0 && net->t_host + n_steps < (1ll << 31), SNN_E_ARG,
+      "n_steps out of range");
+  if (n_steps == 0) return SNN_OK;
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  const int D = net->interval;
+  int64_t full = n_steps / D;
+  const int rem = (int)(n_steps % D);
+  cudaStream_t s = net->stream;
+  if (net->profiling) {
+    const int64_t n_iv = full + (rem ? 1 : 0);
+    for (int64_t k = 0; k < n_iv; ++k) {
+      const int steps = k < full ? D : rem;
+      cudaEvent_t a = pool_event(net, 3 * (size_t)k);
+      cudaEvent_t b = pool_event(net, 3 * (size_t)k + 1);
+      cudaEvent_t c = pool_event(net, 3 * (size_t)k + 2);
+      REQ(a && b && c, SNN_E_CUDA, "event creation failed");
+      NetView v = net->view();
+      CK(cudaEventRecord(a, s));
+      CK(launch_update(v, net->uc, steps, 1, 0, s));
+      CK(cudaEventRecord(b, s));
+      CK(launch_deliver(v, &net->ctl->pair, &net->ctl->done, net->list, 1, s));
+      CK(cudaEventRecord(c, s));
+      net->launches += 2;
+      net->upd_launches += 1;
+      net->del_launches += 1;
+    }
+    CK(cudaStreamSynchronize(s));
+    for (int64_t k = 0; k < n_iv; ++k) {
+      float mu = 0, md = 0;
+      CK(cudaEventElapsedTime(&mu, net->ev[3 * k], net->ev[3 * k + 1]));
+      CK(cudaEventElapsedTime(&md, net->ev[3 * k + 1], net->ev[3 * k + 2]));
+      net->ms_update += mu;
+      net->ms_deliver += md;
+    }
+  } else {
+    if (full >= kGraphIntervals) {
+      if ((rc = capture_graph(net)) != SNN_OK) return rc;
+      for (; full >= kGraphIntervals; full -= kGraphIntervals) {
+        CK(cudaGraphLaunch(net->graph, s));
+        net->launches += 2 * kGraphIntervals;
+        net->upd_launches += kGraphIntervals;
+        net->del_launches += kGraphIntervals;
+      }
+    }
+    for (; full > 0; --full)
+      if ((rc = launch_interval(net, D)) != SNN_OK) return rc;
+    if (rem)
+      if ((rc = launch_interval(net, rem)) != SNN_OK) return rc;
+  }
+  net->t_host += n_steps;
+  return SNN_OK;
+}
+
+int snn_read_spikes(snn_net* net, uint32_t* src, int32_t* t, uint64_t cap,
+                    uint64_t* n, int mem) {
+  REQ(net && n, SNN_E_ARG, "null argument");
+  REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  unsigned long long cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, &net->ctl->log_count, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *n = cnt;
+  uint64_t kept = std::min<uint64_t>(std::min<uint64_t>(cnt, net->log_cap), cap);
+  if (kept) {
+    REQ(src && t, SNN_E_ARG, "null output arrays");
+    CK(cudaMemcpyAsync(src, net->log_src, kept * 4, kind_to(mem), s));
+    CK(cudaMemcpyAsync(t, net->log_t, kept * 4, kind_to(mem), s));
+  }
+  CK(cudaMemsetAsync(&net->ctl->log_count, 0, 8, s));
+  CK(cudaStreamSynchronize(s));
+  if (cnt > kept)
+    return fail(SNN_E_OVERFLOW, "%llu spikes logged, %llu returned",
+                (unsigned long long)cnt, (unsigned long long)kept);
+  return SNN_OK;
+}
+
+static int copy_slots(snn_net* net, void* host_or_dev, const void* dev_base,
+                      int to_caller, int mem, size_t elem) {
+  REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
+  cudaStream_t s = net->stream;
+  const size_t w = (size_t)net->n * elem, pitch = (size_t)net->pitch * elem;
+  if (to_caller)
+    CK(cudaMemcpy2DAsync(host_or_dev, w, dev_base, pitch, w, net->n_slots,
+                         kind_to(mem), s));
+  else
+    CK(cudaMemcpy2DAsync(const_cast<void*>(dev_base), pitch, host_or_dev, w, w,
+                         net->n_slots, kind_from(mem), s));
+  if (mem == SNN_MEM_HOST) CK(cudaStreamSynchronize(s));
+  return SNN_OK;
+}
+
+int snn_read_rb(snn_net* net, float* dst, int mem) {
+  REQ(net && dst, SNN_E_ARG, "null argument");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  return copy_slots(net, dst, net->rb, 1, mem, sizeof(float));
+}
+
+int snn_write_rb(snn_net* net, const float* src, int mem) {
+  REQ(net && src, SNN_E_ARG, "null argument");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  return copy_slots(net, const_cast<float*>(src), net->rb, 0, mem,
+                    sizeof(float));
+}
+
+int snn_read_counts(snn_net* net, uint32_t* dst, int mem) {
+  REQ(net && dst, SNN_E_ARG, "null argument");
+  REQ(net->counts, SNN_E_STATE, "net created without count_events");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  return copy_slots(net, dst, net->counts, 1, mem, sizeof(uint32_t));
+}
+
+int snn_clear_rb(snn_net* net) {
+  REQ(net, SNN_E_ARG, "null net");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  const size_t bytes = (size_t)net->n_slots * net->pitch * 4;
+  CK(cudaMemsetAsync(net->rb, 0, bytes, net->stream));
+  if (net->counts) CK(cudaMemsetAsync(net->counts, 0, bytes, net->stream));
+  return SNN_OK;
+}
+
+int snn_read_state(snn_net* net, float* V, float* I, float* J, int32_t* refr,
+                   int mem) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  const size_t b = (size_t)net->n * 4;
+  if (V) CK(cudaMemcpyAsync(V, net->V, b, kind_to(mem), s));
+  if (I) CK(cudaMemcpyAsync(I, net->I, b, kind_to(mem), s));
+  if (J) CK(cudaMemcpyAsync(J, net->J, b, kind_to(mem), s));
+  if (refr) CK(cudaMemcpyAsync(refr, net->refr, b, kind_to(mem), s));
+  if (mem == SNN_MEM_HOST) CK(cudaStreamSynchronize(s));
+  return SNN_OK;
+}
+
+int snn_write_state(snn_net* net, const float* V, const float* I,
+                    const float* J, const int32_t* refr, int mem) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  const size_t b = (size_t)net->n * 4;
+  if (V) CK(cudaMemcpyAsync(net->V, V, b, kind_from(mem), s));
+  if (I) CK(cudaMemcpyAsync(net->I, I, b, kind_from(mem), s));
+  if (J) CK(cudaMemcpyAsync(net->J, J, b, kind_from(mem), s));
+  if (refr) CK(cudaMemcpyAsync(net->refr, refr, b, kind_from(mem), s));
+  if (mem == SNN_MEM_HOST) CK(cudaStreamSynchronize(s));
+  return SNN_OK;
+}
+
+int snn_read_store(snn_net* net, uint64_t* row_ptr, uint32_t* tgt,
+                   uint8_t* delay, float* w, int mem) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(net->connected, SNN_E_STATE, "net has no store");
+  REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  if (row_ptr)
+    CK(cudaMemcpyAsync(row_ptr, net->row_ptr, (net->n + 1) * 8ull,
+                       kind_to(mem), s));
+  const uint64_t m = net->n_syn;
+  if (m && (tgt || delay || w)) {
+    if (mem == SNN_MEM_DEVICE) {
+      CK(unpack_store(net->fmt, net->recs, m, tgt, delay, w, s));
+    } else {
+      uint32_t* dt = nullptr;
+      uint8_t* dd = nullptr;
+      float* dw = nullptr;
+      CK(dalloc(&dt, m * 4));
+      CK(dalloc(&dd, m));
+      CK(dalloc(&dw, m * 4));
+      CK(unpack_store(net->fmt, net->recs, m, dt, dd, dw, s));
+      if (tgt) CK(cudaMemcpyAsync(tgt, dt, m * 4, cudaMemcpyDeviceToHost, s));
+      if (delay) CK(cudaMemcpyAsync(delay, dd, m, cudaMemcpyDeviceToHost, s));
+      if (w) CK(cudaMemcpyAsync(w, dw, m * 4, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      dfree(dt);
+      dfree(dd);
+      dfree(dw);
+    }
+    net->launches += 1;
+  }
+  if (mem == SNN_MEM_HOST) CK(cudaStreamSynchronize(s));
+  return SNN_OK;
+}
+
+int snn_set_time(snn_net* net, int64_t t) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(t >= 0 && t < (1ll << 31), SNN_E_ARG, "t out of range");
+  REQ(!net->pending, SNN_E_STATE, "spikes of an update are pending");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  net->t_host = t;
+  CK(cudaMemcpyAsync(&net->ctl->t_now, &net->t_host, sizeof(long long),
+                     cudaMemcpyHostToDevice, net->stream));
+  CK(cudaStreamSynchronize(net->stream));
+  return SNN_OK;
+}
+
+int snn_set_profiling(snn_net* net, int on) {
+  REQ(net, SNN_E_ARG, "null net");
+  net->profiling = on != 0;
+  return SNN_OK;
+}
+
+int snn_get_stats(snn_net* net, snn_stats* out) {
+  REQ(net && out, SNN_E_ARG, "null argument");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  Ctl c;
+  CK(cudaMemcpyAsync(&c, net->ctl, sizeof c, cudaMemcpyDeviceToHost,
+                     net->stream));
+  CK(cudaStreamSynchronize(net->stream));
+  memset(out, 0, sizeof *out);
+  out->events_delivered = c.events;
+  out->spikes = c.spikes;
+  out->n_synapses = net->n_syn;
+  out->t_now = c.t_now;
+  out->interval = net->interval;
+  out->min_delay = net->dmin;
+  out->max_delay = net->dmax;
+  out->error_flags = c.error_flags;
+  out->kernel_launches = net->launches;
+  out->update_launches = net->upd_launches;
+  out->deliver_launches = net->del_launches;
+  out->ms_update = net->ms_update;
+  out->ms_deliver = net->ms_deliver;
+  out->bytes_per_record = net->fmt == SNN_W_FP32_12B ? 12 : 8;
+  out->store_bytes = net->recs_bytes;
+  return SNN_OK;
+}
+
+int snn_clear_errors(snn_net* net) {
+  REQ(net, SNN_E_ARG, "null net");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  CK(cudaMemsetAsync(&net->ctl->error_flags, 0, sizeof(unsigned),
+                     net->stream));
+  CK(cudaStreamSynchronize(net->stream));
+  return SNN_OK;
+}
+
+int snn_sync(snn_net* net) {
+  REQ(net, SNN_E_ARG, "null net");
+  CK(cudaStreamSynchronize(net->stream));
+  CK(cudaGetLastError());
+  return SNN_OK;
+}
+
+int snn_destroy(snn_net* net) {
+  if (!net) return SNN_OK;
+  cudaSetDevice(net->device);
+  if (net->stream) cudaStreamSynchronize(net->stream);
+  if (net->graph) cudaGraphExecDestroy(net->graph);
+  for (cudaEvent_t e : net->ev) cudaEventDestroy(e);
+  void* bufs[] = {net->V,        net->I,        net->J,       net->refr,
+                  net->rb,       net->counts,   net->ctl,     net->row_ptr,
+                  net->recs,     net->list,     net->ext_list, net->ext_src,
+                  net->ext_t,    net->log_src,  net->log_t};
+  for (void* b : bufs) dfree(b);
+  if (net->own_stream) cudaStreamDestroy(net->stream);
+  delete net;
+  return SNN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,352 @@
+// snn_build.cu -- construction of the source-major connection store on the
+// device (network construction is outside the paper's measurements, Section
+// 2.2; the store layout follows its Section 3.1: source-specific target
+// segments).
+//
+// Pipeline: (1) count out-degrees with one generator call per synapse,
+// (2) the host turns them into row offsets, (3) scatter one 64-bit sort key
+// per synapse into its row -- key = delay << 56 | target << 32 | tie, where
+// tie is the draw index k (fixed in-degree rule) or the edge index -- (4) sort
+// every row by key in shared memory (bitonic network; rows longer than the
+// shared-memory capacity are sorted in a global scratch buffer) and pack the
+// records, regenerating the weight from the tie.  Sorting by the full key
+// makes the store independent of the scatter's atomic order.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "snn_internal.cuh"
+
+namespace snn {
+namespace {
+
+__device__ __forceinline__ uint64_t make_key(uint32_t d, uint32_t tgt,
+                                             uint32_t tie) {
+  return ((uint64_t)d << 56) | ((uint64_t)tgt << 32) | tie;
+}
+
+__device__ __forceinline__ uint32_t fixed_source(const BuildFixed& b,
+                                                 uint32_t k, uint32_t u) {
+  return k < b.k_e ? scale_u32(u, b.n_e) : b.n_e + scale_u32(u, b.n_i);
+}
+
+__global__ void k_count_fixed(BuildFixed b, uint32_t* deg) {
+  const uint32_t tgt = blockIdx.x;
+  const uint32_t kk = b.k_e + b.k_i;
+  for (uint32_t k = threadIdx.x; k < kk; k += blockDim.x) {
+    U4 r = draw(b.seed, tgt, k, 0u);
+    atomicAdd(&deg[fixed_source(b, k, r.x)], 1u);
+  }
+}
+
+__global__ void k_scatter_fixed(BuildFixed b, const uint64_t* row_ptr,
+                                uint32_t* cursor, uint64_t* keys) {
+  const uint32_t tgt = blockIdx.x;
+  const uint32_t kk = b.k_e + b.k_i;
+  const uint32_t span = (uint32_t)(b.d_hi - b.d_lo + 1);
+  for (uint32_t k = threadIdx.x; k < kk; k += blockDim.x) {
+    U4 r = draw(b.seed, tgt, k, 0u);
+    uint32_t src = fixed_source(b, k, r.x);
+    uint32_t d = (uint32_t)b.d_lo + scale_u32(r.y, span);
+    uint32_t pos = atomicAdd(&cursor[src], 1u);
+    keys[row_ptr[src] + pos] = make_key(d, tgt, k);
+  }
+}
+
+__global__ void k_count_edges(const uint32_t* src, uint64_t n, uint32_t* deg) {
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n;
+       e += (uint64_t)gridDim.x * blockDim.x)
+    atomicAdd(&deg[src[e]], 1u);
+}
+
+__global__ void k_scatter_edges(const uint32_t* src, const uint32_t* tgt,
+                                const uint8_t* delay, uint64_t n,
+                                const uint64_t* row_ptr, uint32_t* cursor,
+                                uint64_t* keys) {
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t s = src[e];
+    uint32_t pos = atomicAdd(&cursor[s], 1u);
+    keys[row_ptr[s] + pos] = make_key(delay[e], tgt[e], (uint32_t)e);
+  }
+}
+
+// Weight of a synapse, FP64: per-edge value, or the fixed rule's mean plus
+// a Box-Muller normal from words 2 and 3 of the synapse's draw.
+template <int WMODE>
+__device__ double weight_of(const BuildFixed& b, const double* edge_w,
+                            bool exc, uint32_t tgt, uint32_t tie) {
+  if (WMODE == 1) return edge_w[tie];
+  double mean = exc ? b.w_e : b.w_i, sd = exc ? b.sd_e : b.sd_i;
+  double x = mean;
+  if (sd != 0.0) {
+    U4 r = draw(b.seed, tgt, tie, 0u);
+    double u1 = ((double)r.z + 1.0) * 0x1p-32;
+    double u2 = (double)r.w * 0x1p-32;
+    double z = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.14159265358979323846 * u2);
+    x = mean + sd * z;
+  }
+  if (exc && b.clip_e && x < 0.0) x = 0.0;
+  if (!exc && b.clip_i && x > 0.0) x = 0.0;
+  return x;
+}
+
+template <int FMT>
+__device__ __forceinline__ void store_rec(void* recs, uint64_t idx,
+                                          uint32_t tgt, uint32_t d, double w) {
+  if (FMT == SNN_W_FP32_12B) {
+    uint32_t* p = reinterpret_cast<uint32_t*>(recs) + idx * 3u;
+    p[0] = tgt;
+    p[1] = __float_as_uint(__double2float_rn(w));
+    p[2] = d & 0xFFu;
+  } else {
+    uint2 r;
+    r.x = tgt;
+    r.y = (d & 0xFFu) | ((uint32_t)bf16_bits_rne(w) << 16);
+    reinterpret_cast<uint2*>(recs)[idx] = r;
+  }
+}
+
+template <int FMT, int WMODE>
+__device__ void pack_row(const uint64_t* sorted, uint32_t len, uint32_t row,
+                         uint64_t beg, void* recs, const BuildFixed& b,
+                         const double* edge_w) {
+  const bool exc = row < b.n_e;
+  for (uint32_t p = threadIdx.x; p < len; p += blockDim.x) {
+    uint64_t key = sorted[p];
+    uint32_t d = (uint32_t)(key >> 56);
+    uint32_t tgt = (uint32_t)(key >> 32) & 0xFFFFFFu;
+    uint32_t tie = (uint32_t)key;
+    store_rec<FMT>(recs, beg + p, tgt, d,
+                   weight_of<WMODE>(b, edge_w, exc, tgt, tie));
+  }
+}
+
+// In-place ascending bitonic sort of P (a power of two) keys.
+__device__ void bitonic(uint64_t* a, uint32_t P) {
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        uint32_t l = i ^ j;
+        if (l > i) {
+          uint64_t x = a[i], y = a[l];
+          bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t pow2_ceil(uint32_t x) {
+  uint32_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+template <int FMT, int WMODE>
+__global__ void k_sort_pack(uint32_t n, const uint64_t* row_ptr,
+                            uint64_t* keys, void* recs, BuildFixed b,
+                            const double* edge_w, uint32_t cap) {
+  extern __shared__ uint64_t sk[];
+  for (uint32_t row = blockIdx.x; row < n; row += gridDim.x) {
+    const uint64_t beg = row_ptr[row];
+    const uint32_t len = (uint32_t)(row_ptr[row + 1] - beg);
+    if (len == 0 || len > cap) continue;     // uniform per block
+    const uint32_t P = pow2_ceil(len);
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+      sk[i] = i < len ? keys[beg + i] : ~0ull;
+    __syncthreads();
+    bitonic(sk, P);
+    pack_row<FMT, WMODE>(sk, len, row, beg, recs, b, edge_w);
+    __syncthreads();
+  }
+}
+
+template <int FMT, int WMODE>
+__global__ void k_sort_long(const uint32_t* rows, const uint64_t* row_ptr,
+                            uint64_t* keys, void* recs, BuildFixed b,
+                            const double* edge_w, uint64_t* scratch,
+                            const uint64_t* scratch_off) {
+  const uint32_t row = rows[blockIdx.x];
+  const uint64_t beg = row_ptr[row];
+  const uint32_t len = (uint32_t)(row_ptr[row + 1] - beg);
+  uint64_t* a = scratch + scratch_off[blockIdx.x];
+  const uint32_t P = pow2_ceil(len);
+  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+    a[i] = i < len ? keys[beg + i] : ~0ull;
+  __syncthreads();
+  bitonic(a, P);
+  pack_row<FMT, WMODE>(a, len, row, beg, recs, b, edge_w);
+}
+
+template <int FMT>
+__global__ void k_unpack(const void* recs, uint64_t n, uint32_t* tgt,
+                         uint8_t* delay, float* w) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t t, d;
+    float x;
+    if (FMT == SNN_W_FP32_12B) {
+      const uint32_t* p = reinterpret_cast<const uint32_t*>(recs) + s * 3u;
+      t = p[0];
+      x = __uint_as_float(p[1]);
+      d = p[2] & 0xFFu;
+    } else {
+      uint2 r = reinterpret_cast<const uint2*>(recs)[s];
+      t = r.x;
+      d = r.y & 0xFFu;
+      x = bf16_to_f32(r.y >> 16);
+    }
+    if (tgt) tgt[s] = t;
+    if (delay) delay[s] = (uint8_t)d;
+    if (w) w[s] = x;
+  }
+}
+
+template <int FMT>
+__global__ void k_delay_range(const void* recs, uint64_t n, unsigned* out) {
+  unsigned lo = 0xFFFFFFFFu, hi = 0u;
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    unsigned d = FMT == SNN_W_FP32_12B
+                     ? reinterpret_cast<const uint32_t*>(recs)[s * 3u + 2u] & 0xFFu
+                     : reinterpret_cast<const uint2*>(recs)[s].y & 0xFFu;
+    lo = min(lo, d);
+    hi = max(hi, d);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+  }
+  if ((threadIdx.x & 31u) == 0) {
+    atomicMin(&out[0], lo);
+    atomicMax(&out[1], hi);
+  }
+}
+
+unsigned grid_for(uint64_t n, unsigned threads) {
+  uint64_t b = (n + threads - 1) / threads;
+  if (b > 65536u * 8u) b = 65536u * 8u;
+  return b ? (unsigned)b : 1u;
+}
+
+template <int FMT, int WMODE>
+cudaError_t sort_pack_t(uint32_t n, const uint64_t* row_ptr, uint64_t* keys,
+                        void* recs, const BuildFixed* b, const double* edge_w,
+                        uint32_t max_row, const uint32_t* long_rows,
+                        uint32_t n_long, uint64_t* long_scratch,
+                        const uint64_t* long_off, cudaStream_t s) {
+  constexpr uint32_t kCap = 16384;   // keys sorted in shared memory (128 KiB)
+  BuildFixed bb = b ? *b : BuildFixed{};
+  uint32_t cap = max_row < kCap ? max_row : kCap;
+  uint32_t P = 1;
+  while (P < cap) P <<= 1;
+  size_t smem = (size_t)P * sizeof(uint64_t);
+  cudaError_t e = cudaFuncSetAttribute(
+      k_sort_pack<FMT, WMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)smem);
+  if (e != cudaSuccess) return e;
+  unsigned threads = P >= 1024 ? 1024 : (P >= 128 ? P : 128);
+  unsigned blocks = n < (1u << 20) ? n : (1u << 20);
+  if (blocks && max_row > 0)
+    k_sort_pack<FMT, WMODE><<<blocks, threads, smem, s>>>(n, row_ptr, keys, recs,
+                                                          bb, edge_w, kCap);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (n_long)
+    k_sort_long<FMT, WMODE><<<n_long, 1024, 0, s>>>(long_rows, row_ptr, keys,
+                                                     recs, bb, edge_w,
+                                                     long_scratch, long_off);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t build_count_fixed(const BuildFixed& b, uint32_t* deg,
+                              cudaStream_t s) {
+  uint32_t n = b.n_e + b.n_i;
+  if (n == 0 || b.k_e + b.k_i == 0) return cudaSuccess;
+  k_count_fixed<<<n, 256, 0, s>>>(b, deg);
+  return cudaGetLastError();
+}
+
+cudaError_t build_scatter_fixed(const BuildFixed& b, const uint64_t* row_ptr,
+                                uint32_t* cursor, uint64_t* keys,
+                                cudaStream_t s) {
+  uint32_t n = b.n_e + b.n_i;
+  if (n == 0 || b.k_e + b.k_i == 0) return cudaSuccess;
+  k_scatter_fixed<<<n, 256, 0, s>>>(b, row_ptr, cursor, keys);
+  return cudaGetLastError();
+}
+
+cudaError_t build_count_edges(const uint32_t* src, uint64_t n, uint32_t* deg,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_count_edges<<<grid_for(n, 256), 256, 0, s>>>(src, n, deg);
+  return cudaGetLastError();
+}
+
+cudaError_t build_scatter_edges(const uint32_t* src, const uint32_t* tgt,
+                                const uint8_t* delay, uint64_t n,
+                                const uint64_t* row_ptr, uint32_t* cursor,
+                                uint64_t* keys, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_scatter_edges<<<grid_for(n, 256), 256, 0, s>>>(src, tgt, delay, n, row_ptr,
+                                                   cursor, keys);
+  return cudaGetLastError();
+}
+
+cudaError_t build_sort_pack(int fmt, uint32_t n, const uint64_t* row_ptr,
+                            uint64_t* keys, void* recs, const BuildFixed* b,
+                            const double* edge_w, uint32_t max_row,
+                            const uint32_t* long_rows, uint32_t n_long,
+                            uint64_t* long_scratch,
+                            const uint64_t* long_scratch_off,
+                            cudaStream_t s) {
+  if (fmt == SNN_W_FP32_12B)
+    return edge_w ? sort_pack_t<SNN_W_FP32_12B, 1>(
+                        n, row_ptr, keys, recs, b, edge_w, max_row, long_rows,
+                        n_long, long_scratch, long_scratch_off, s)
+                  : sort_pack_t<SNN_W_FP32_12B, 0>(
+                        n, row_ptr, keys, recs, b, edge_w, max_row, long_rows,
+                        n_long, long_scratch, long_scratch_off, s);
+  return edge_w ? sort_pack_t<SNN_W_BF16_8B, 1>(n, row_ptr, keys, recs, b,
+                                                 edge_w, max_row, long_rows,
+                                                 n_long, long_scratch,
+                                                 long_scratch_off, s)
+                : sort_pack_t<SNN_W_BF16_8B, 0>(n, row_ptr, keys, recs, b,
+                                                 edge_w, max_row, long_rows,
+                                                 n_long, long_scratch,
+                                                 long_scratch_off, s);
+}
+
+cudaError_t unpack_store(int fmt, const void* recs, uint64_t n_syn,
+                         uint32_t* tgt, uint8_t* delay, float* w,
+                         cudaStream_t s) {
+  if (n_syn == 0) return cudaSuccess;
+  if (fmt == SNN_W_FP32_12B)
+    k_unpack<SNN_W_FP32_12B><<<grid_for(n_syn, 256), 256, 0, s>>>(recs, n_syn,
+                                                                  tgt, delay, w);
+  else
+    k_unpack<SNN_W_BF16_8B><<<grid_for(n_syn, 256), 256, 0, s>>>(recs, n_syn,
+                                                                 tgt, delay, w);
+  return cudaGetLastError();
+}
+
+cudaError_t delay_range(int fmt, const void* recs, uint64_t n_syn,
+                        unsigned int* dmin_dmax, cudaStream_t s) {
+  if (n_syn == 0) return cudaSuccess;
+  if (fmt == SNN_W_FP32_12B)
+    k_delay_range<SNN_W_FP32_12B><<<grid_for(n_syn, 256), 256, 0, s>>>(
+        recs, n_syn, dmin_dmax);
+  else
+    k_delay_range<SNN_W_BF16_8B><<<grid_for(n_syn, 256), 256, 0, s>>>(
+        recs, n_syn, dmin_dmax);
+  return cudaGetLastError();
+}
+
+}  // namespace snn

@@ -1,0 +1,239 @@
+// snn_internal.cuh -- device-side definitions shared by the libsnn CUDA
+// translation units: record formats, the per-net control block, the
+// counter-based generator and small warp helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/snn.h"
+
+namespace snn {
+
+// ---------------------------------------------------------------------------
+// Connection store records.  A target segment (Section 3.1 of the paper) is
+// a contiguous run of records; the store is source-major with row offsets.
+// Chunking: every row is processed in chunks aligned to absolute record
+// indices that are multiples of kChunk, so that each lane of a warp issues
+// naturally aligned 16-byte loads; records of a chunk outside the row are
+// loaded and ignored.  The record array is padded to whole chunks.
+// ---------------------------------------------------------------------------
+struct RecF32 {       // 12 bytes
+  uint32_t target;
+  float weight;
+  uint32_t delay;     // low 8 bits; upper 24 bits are zero padding
+};
+struct RecBF16 {      // 8 bytes
+  uint32_t target;
+  uint32_t meta;      // bits 0-7 delay, 8-15 pad, 16-31 bfloat16 weight
+};
+
+template <int FMT> struct Fmt;
+template <> struct Fmt<SNN_W_FP32_12B> {
+  static constexpr int kRecBytes = 12;
+  static constexpr int kPerLane = 4;            // 48 bytes = 3 x 16 B
+  static constexpr int kChunk = 32 * kPerLane;  // 128 records, 1,536 B
+};
+template <> struct Fmt<SNN_W_BF16_8B> {
+  static constexpr int kRecBytes = 8;
+  static constexpr int kPerLane = 2;            // 16 bytes
+  static constexpr int kChunk = 32 * kPerLane;  // 64 records, 512 B
+};
+
+__host__ __device__ inline int chunk_records(int fmt) {
+  return fmt == SNN_W_FP32_12B ? Fmt<SNN_W_FP32_12B>::kChunk
+                               : Fmt<SNN_W_BF16_8B>::kChunk;
+}
+
+// Number of aligned chunks that cover records [beg, end).
+__host__ __device__ inline uint32_t row_chunks(uint64_t beg, uint64_t end,
+                                               uint32_t ch) {
+  return end > beg ? (uint32_t)((end - 1) / ch - beg / ch + 1) : 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Interval spike list entry (the GPU counterpart of the spike-receive
+// register): source, emission step and the entry's first chunk in the
+// interval's chunk space (an exclusive prefix sum of row chunk counts).
+// ---------------------------------------------------------------------------
+struct SpikeEntry {
+  uint32_t src;
+  int32_t t;
+  uint32_t choff;
+  uint32_t pad;
+};
+
+// Per-net control block in device memory.
+struct Ctl {
+  unsigned long long pair;      // (spikes << 32) | chunks of the pending list
+  unsigned int done;            // CTAs finished in the current delivery
+  unsigned int error_flags;     // SNN_ERRF_*
+  unsigned long long events;    // events delivered (accumulated)
+  unsigned long long spikes;    // spikes emitted (accumulated)
+  unsigned long long log_count; // entries in the spike log
+  long long t_now;              // next step to update
+  int iv_steps;                 // steps of the pending interval
+  unsigned int ext_done;        // CTAs finished delivering an external list
+  unsigned long long ext_pair;  // (spikes << 32) | chunks of an external list
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 32x32->64-bit multiplications, the high halves xor-ed with the other
+// counter words and the round key; the key advances by the golden-ratio
+// Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__host__ __device__ inline U4 philox10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint64_t m0 = (uint64_t)0xD2511F53u * c.x;
+    uint64_t m1 = (uint64_t)0xCD9E8D57u * c.z;
+    U4 n;
+    n.x = (uint32_t)(m1 >> 32) ^ c.y ^ k0;
+    n.y = (uint32_t)m1;
+    n.z = (uint32_t)(m0 >> 32) ^ c.w ^ k1;
+    n.w = (uint32_t)m0;
+    c = n;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Random streams of the model: 0 connection (target, k), 1 initial
+// potential (neuron, 0), 2 Poisson drive (neuron, step).
+__host__ __device__ inline U4 draw(uint64_t seed, uint32_t a, uint64_t b,
+                                   uint32_t stream) {
+  U4 c{a, (uint32_t)b, (uint32_t)(b >> 32), stream};
+  return philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// floor(u * n / 2^32)
+__host__ __device__ inline uint32_t scale_u32(uint32_t u, uint32_t n) {
+  return (uint32_t)(((uint64_t)u * n) >> 32);
+}
+
+// FP64 -> bfloat16 bits, round to nearest even in one step (finite inputs
+// of normal float range; values below the smallest normal float flush to
+// a signed zero).
+__host__ __device__ inline uint16_t bf16_bits_rne(double x) {
+  uint64_t b;
+  memcpy(&b, &x, 8);
+  uint32_t sign = (uint32_t)(b >> 63);
+  int e = (int)((b >> 52) & 0x7FF);
+  uint64_t mant = b & 0xFFFFFFFFFFFFFull;
+  if (e == 0) return (uint16_t)(sign << 15);             // zero / subnormal
+  int ef = e - 1023 + 127;                               // float exponent
+  if (ef <= 0) return (uint16_t)(sign << 15);
+  if (ef >= 255 || e == 0x7FF) return (uint16_t)((sign << 15) | 0x7F80u);
+  // keep 7 explicit mantissa bits; 45 bits are rounded away
+  uint64_t keep = mant >> 45;
+  uint64_t rest = mant & ((1ull << 45) - 1);
+  uint64_t half = 1ull << 44;
+  if (rest > half || (rest == half && (keep & 1))) ++keep;
+  uint32_t v = ((uint32_t)ef << 7) + (uint32_t)keep;     // carry may bump ef
+  if (v >= 0x7F80u) v = 0x7F80u;
+  return (uint16_t)((sign << 15) | v);
+}
+
+__host__ __device__ inline float bf16_to_f32(uint32_t bits16) {
+  uint32_t u = bits16 << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+// ---------------------------------------------------------------------------
+// Neuron update constants (FP64 on the host, rounded to float32 once).
+// ---------------------------------------------------------------------------
+constexpr int kMaxPoisson = 128;
+struct UpdConst {
+  float p11, p21, p22, p31, p32, p33;
+  float psc;       // e / tau_syn
+  float v_th, v_reset, w_ext;
+  int refr_steps;
+  int n_thr;       // 0: no drive
+  uint64_t seed;
+  uint32_t thr[kMaxPoisson];  // Poisson inversion thresholds (last = 2^32-1
+                              // sentinel handled by n_thr)
+};
+
+// Device view of one net.
+struct NetView {
+  uint32_t n;
+  uint32_t pitch;           // ring-buffer row pitch (floats)
+  uint32_t slot_mask;       // n_slots - 1
+  uint32_t chunk;           // records per chunk
+  int fmt;
+  float* V;
+  float* I;
+  float* J;
+  int32_t* refr;
+  float* rb;                // [n_slots][pitch]
+  uint32_t* counts;         // [n_slots][pitch] or null
+  const uint64_t* row_ptr;  // [n+1]
+  const void* recs;
+  SpikeEntry* list;         // interval list, capacity list_cap
+  uint64_t list_cap;
+  uint32_t* log_src;        // spike log, capacity log_cap
+  int32_t* log_t;
+  uint64_t log_cap;
+  Ctl* ctl;
+};
+
+__device__ inline unsigned lane_id() { return threadIdx.x & 31u; }
+
+}  // namespace snn
+
+// Launchers implemented in the .cu files (host side).
+namespace snn {
+cudaError_t launch_init_v(const NetView& v, const UpdConst* c, int random,
+                          cudaStream_t s);
+cudaError_t launch_update(const NetView& v, const UpdConst& c, int n_steps,
+                          int from_ctl_time, long long t0, cudaStream_t s);
+cudaError_t launch_deliver(const NetView& v, unsigned long long* pair,
+                           unsigned int* done, const SpikeEntry* list,
+                           int advance_time, cudaStream_t s);
+cudaError_t launch_prepare_external(const NetView& v, const uint32_t* src,
+                                    const int32_t* t, uint32_t n,
+                                    SpikeEntry* list,
+                                    unsigned long long* pair, cudaStream_t s);
+int deliver_grid_size(int fmt);
+
+// store construction
+struct BuildFixed {
+  uint32_t n_e, n_i, k_e, k_i;
+  double w_e, w_i, sd_e, sd_i;
+  int d_lo, d_hi;
+  uint64_t seed;
+  int clip_e, clip_i;
+};
+cudaError_t build_count_fixed(const BuildFixed& b, uint32_t* deg,
+                              cudaStream_t s);
+cudaError_t build_scatter_fixed(const BuildFixed& b, const uint64_t* row_ptr,
+                                uint32_t* cursor, uint64_t* keys,
+                                cudaStream_t s);
+cudaError_t build_count_edges(const uint32_t* src, uint64_t n, uint32_t* deg,
+                              cudaStream_t s);
+cudaError_t build_scatter_edges(const uint32_t* src, const uint32_t* tgt,
+                                const uint8_t* delay, uint64_t n,
+                                const uint64_t* row_ptr, uint32_t* cursor,
+                                uint64_t* keys, cudaStream_t s);
+// Sort every row's keys by value and pack records.  weights: either the
+// fixed-rule parameters (edge_w == null) or per-edge FP64 weights.
+cudaError_t build_sort_pack(int fmt, uint32_t n, const uint64_t* row_ptr,
+                            uint64_t* keys, void* recs, const BuildFixed* b,
+                            const double* edge_w, uint32_t max_row,
+                            const uint32_t* long_rows, uint32_t n_long,
+                            uint64_t* long_scratch,
+                            const uint64_t* long_scratch_off,
+                            cudaStream_t s);
+cudaError_t unpack_store(int fmt, const void* recs, uint64_t n_syn,
+                         uint32_t* tgt, uint8_t* delay, float* w,
+                         cudaStream_t s);
+cudaError_t delay_range(int fmt, const void* recs, uint64_t n_syn,
+                        unsigned int* dmin_dmax, cudaStream_t s);
+}  // namespace snn

@@ -1,0 +1,397 @@
+"""Thin ctypes binding of libsnn (``include/snn.h``): same names, argument
+marshalling only.  Every computation runs in the CUDA library; there is no
+fallback -- importing this module without the built library raises.
+
+Buffers may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory); the binding passes the matching ``SNN_MEM_*`` flag.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .native import LIB
+
+SNN_OK = 0
+SNN_E_OOM, SNN_E_ARG, SNN_E_STATE, SNN_E_TIMEOUT, SNN_E_OVERFLOW, SNN_E_CUDA = \
+    -1, -2, -3, -4, -5, -6
+SNN_MEM_HOST, SNN_MEM_DEVICE = 0, 1
+SNN_W_FP32_12B, SNN_W_BF16_8B = 0, 1
+SNN_ERRF_SPIKE_LIST, SNN_ERRF_SPIKE_LOG, SNN_ERRF_BAD_SOURCE, SNN_ERRF_CHUNKS = \
+    1, 2, 4, 8
+
+EXPORTS = [
+    "snn_abi_version", "snn_last_error", "snn_default_params",
+    "snn_psc_weight_for_psp", "snn_create", "snn_connect_fixed_indegree",
+    "snn_connect_edges", "snn_finalize", "snn_update", "snn_deliver_pending",
+    "snn_discard_pending", "snn_deliver", "snn_simulate", "snn_read_spikes",
+    "snn_read_rb", "snn_write_rb", "snn_read_counts", "snn_clear_rb",
+    "snn_read_state", "snn_write_state", "snn_read_store", "snn_set_time",
+    "snn_set_profiling", "snn_get_stats", "snn_clear_errors", "snn_sync",
+    "snn_destroy",
+]
+
+
+class SnnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libsnn error {code}: {msg}")
+        self.code = code
+
+
+class snn_params(C.Structure):
+    _fields_ = [("n_exc", C.c_uint32), ("n_inh", C.c_uint32),
+                ("h", C.c_double), ("tau_m", C.c_double), ("c_m", C.c_double),
+                ("v_th", C.c_double), ("v_reset", C.c_double),
+                ("t_ref", C.c_double), ("tau_syn", C.c_double),
+                ("nu_ext", C.c_double), ("w_ext", C.c_double),
+                ("seed", C.c_uint64), ("weight_format", C.c_int32),
+                ("n_slots", C.c_int32), ("interval", C.c_int32),
+                ("init_v_random", C.c_int32), ("count_events", C.c_int32),
+                ("pad_", C.c_int32), ("spike_log_capacity", C.c_uint64)]
+
+
+class snn_conn_params(C.Structure):
+    _fields_ = [("k_exc", C.c_uint32), ("k_inh", C.c_uint32),
+                ("w_exc", C.c_double), ("w_inh", C.c_double),
+                ("sd_exc", C.c_double), ("sd_inh", C.c_double),
+                ("d_lo", C.c_int32), ("d_hi", C.c_int32), ("seed", C.c_uint64),
+                ("clip_exc", C.c_int32), ("clip_inh", C.c_int32)]
+
+
+class snn_stats(C.Structure):
+    _fields_ = [("events_delivered", C.c_uint64), ("spikes", C.c_uint64),
+                ("n_synapses", C.c_uint64), ("t_now", C.c_int64),
+                ("interval", C.c_int32), ("min_delay", C.c_int32),
+                ("max_delay", C.c_int32), ("error_flags", C.c_uint32),
+                ("kernel_launches", C.c_uint64),
+                ("update_launches", C.c_uint64),
+                ("deliver_launches", C.c_uint64), ("ms_update", C.c_double),
+                ("ms_deliver", C.c_double), ("bytes_per_record", C.c_uint64),
+                ("store_bytes", C.c_uint64)]
+
+
+_P = C.c_void_p
+_lib = None
+
+
+def lib():
+    """Load libsnn.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(
+                f"{LIB} is missing: run `python -m paper_2109_12855_gb300.native` "
+                "(there is no CPU fallback)")
+        L = C.CDLL(LIB)
+        sig = {
+            "snn_abi_version": ([], C.c_int),
+            "snn_last_error": ([], C.c_char_p),
+            "snn_default_params": ([C.POINTER(snn_params)], C.c_int),
+            "snn_psc_weight_for_psp": ([C.POINTER(snn_params), C.c_double,
+                                        C.POINTER(C.c_double)], C.c_int),
+            "snn_create": ([C.POINTER(snn_params), _P, C.POINTER(_P)], C.c_int),
+            "snn_connect_fixed_indegree": ([_P, C.POINTER(snn_conn_params)],
+                                           C.c_int),
+            "snn_connect_edges": ([_P, _P, _P, _P, _P, C.c_uint64, C.c_int],
+                                  C.c_int),
+            "snn_finalize": ([_P], C.c_int),
+            "snn_update": ([_P, C.c_int64, C.c_int32], C.c_int),
+            "snn_deliver_pending": ([_P], C.c_int),
+            "snn_discard_pending": ([_P], C.c_int),
+            "snn_deliver": ([_P, _P, _P, C.c_uint32, C.c_int,
+                             C.POINTER(C.c_uint64)], C.c_int),
+            "snn_simulate": ([_P, C.c_int64], C.c_int),
+            "snn_read_spikes": ([_P, _P, _P, C.c_uint64, C.POINTER(C.c_uint64),
+                                 C.c_int], C.c_int),
+            "snn_read_rb": ([_P, _P, C.c_int], C.c_int),
+            "snn_write_rb": ([_P, _P, C.c_int], C.c_int),
+            "snn_read_counts": ([_P, _P, C.c_int], C.c_int),
+            "snn_clear_rb": ([_P], C.c_int),
+            "snn_read_state": ([_P, _P, _P, _P, _P, C.c_int], C.c_int),
+            "snn_write_state": ([_P, _P, _P, _P, _P, C.c_int], C.c_int),
+            "snn_read_store": ([_P, _P, _P, _P, _P, C.c_int], C.c_int),
+            "snn_set_time": ([_P, C.c_int64], C.c_int),
+            "snn_set_profiling": ([_P, C.c_int], C.c_int),
+            "snn_get_stats": ([_P, C.POINTER(snn_stats)], C.c_int),
+            "snn_clear_errors": ([_P], C.c_int),
+            "snn_sync": ([_P], C.c_int),
+            "snn_destroy": ([_P], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != SNN_OK:
+        raise SnnError(rc, lib().snn_last_error().decode(errors="replace"))
+    return rc
+
+
+def _buf(x, dtype=None):
+    """(pointer, mem kind) of a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None, SNN_MEM_HOST
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"], "array must be contiguous"
+        if dtype is not None:
+            assert x.dtype == dtype, f"expected {dtype}, got {x.dtype}"
+        return x.ctypes.data, SNN_MEM_HOST
+    # torch tensor
+    assert x.is_contiguous(), "tensor must be contiguous"
+    return x.data_ptr(), (SNN_MEM_DEVICE if x.is_cuda else SNN_MEM_HOST)
+
+
+def _mem_of(*xs):
+    kinds = {_buf(x)[1] for x in xs if x is not None}
+    assert len(kinds) <= 1, "buffers of one call must share a memory kind"
+    return kinds.pop() if kinds else SNN_MEM_HOST
+
+
+# --- same-named wrappers ----------------------------------------------------
+def snn_abi_version() -> int:
+    return lib().snn_abi_version()
+
+
+def snn_default_params() -> snn_params:
+    p = snn_params()
+    _check(lib().snn_default_params(C.byref(p)))
+    return p
+
+
+def snn_psc_weight_for_psp(p: snn_params, psp_mv: float) -> float:
+    w = C.c_double()
+    _check(lib().snn_psc_weight_for_psp(C.byref(p), psp_mv, C.byref(w)))
+    return w.value
+
+
+def snn_create(p: snn_params, stream: int | None = None):
+    h = _P()
+    _check(lib().snn_create(C.byref(p), stream or None, C.byref(h)))
+    return h
+
+
+def snn_connect_fixed_indegree(net, c: snn_conn_params):
+    _check(lib().snn_connect_fixed_indegree(net, C.byref(c)))
+
+
+def snn_connect_edges(net, src, tgt, delay, w):
+    mem = _mem_of(src, tgt, delay, w)
+    _check(lib().snn_connect_edges(net, _buf(src)[0], _buf(tgt)[0],
+                                   _buf(delay)[0], _buf(w)[0], len(src), mem))
+
+
+def snn_finalize(net):
+    _check(lib().snn_finalize(net))
+
+
+def snn_update(net, t0: int, n_steps: int):
+    _check(lib().snn_update(net, t0, n_steps))
+
+
+def snn_deliver_pending(net):
+    _check(lib().snn_deliver_pending(net))
+
+
+def snn_discard_pending(net):
+    _check(lib().snn_discard_pending(net))
+
+
+def snn_deliver(net, src, t_emit, want_events: bool = True):
+    mem = _mem_of(src, t_emit)
+    ev = C.c_uint64()
+    _check(lib().snn_deliver(net, _buf(src)[0], _buf(t_emit)[0], len(src), mem,
+                             C.byref(ev) if want_events else None))
+    return ev.value if want_events else None
+
+
+def snn_simulate(net, n_steps: int):
+    _check(lib().snn_simulate(net, n_steps))
+
+
+def snn_read_spikes(net, src, t):
+    """Fills src/t (capacity len(src)); returns the number logged."""
+    n = C.c_uint64()
+    mem = _mem_of(src, t)
+    rc = lib().snn_read_spikes(net, _buf(src)[0], _buf(t)[0], len(src),
+                               C.byref(n), mem)
+    if rc not in (SNN_OK, SNN_E_OVERFLOW):
+        _check(rc)
+    return n.value
+
+
+def snn_read_rb(net, dst):
+    p, mem = _buf(dst)
+    _check(lib().snn_read_rb(net, p, mem))
+
+
+def snn_write_rb(net, src):
+    p, mem = _buf(src)
+    _check(lib().snn_write_rb(net, p, mem))
+
+
+def snn_read_counts(net, dst):
+    p, mem = _buf(dst)
+    _check(lib().snn_read_counts(net, p, mem))
+
+
+def snn_clear_rb(net):
+    _check(lib().snn_clear_rb(net))
+
+
+def snn_read_state(net, V=None, I=None, J=None, refr=None):
+    mem = _mem_of(V, I, J, refr)
+    _check(lib().snn_read_state(net, _buf(V)[0], _buf(I)[0], _buf(J)[0],
+                                _buf(refr)[0], mem))
+
+
+def snn_write_state(net, V=None, I=None, J=None, refr=None):
+    mem = _mem_of(V, I, J, refr)
+    _check(lib().snn_write_state(net, _buf(V)[0], _buf(I)[0], _buf(J)[0],
+                                 _buf(refr)[0], mem))
+
+
+def snn_read_store(net, row_ptr=None, tgt=None, delay=None, w=None):
+    mem = _mem_of(row_ptr, tgt, delay, w)
+    _check(lib().snn_read_store(net, _buf(row_ptr)[0], _buf(tgt)[0],
+                                _buf(delay)[0], _buf(w)[0], mem))
+
+
+def snn_set_time(net, t: int):
+    _check(lib().snn_set_time(net, t))
+
+
+def snn_set_profiling(net, on: bool):
+    _check(lib().snn_set_profiling(net, int(on)))
+
+
+def snn_get_stats(net) -> snn_stats:
+    s = snn_stats()
+    _check(lib().snn_get_stats(net, C.byref(s)))
+    return s
+
+
+def snn_clear_errors(net):
+    _check(lib().snn_clear_errors(net))
+
+
+def snn_sync(net):
+    _check(lib().snn_sync(net))
+
+
+def snn_destroy(net):
+    _check(lib().snn_destroy(net))
+
+
+# --- convenience ------------------------------------------------------------
+def params(**kw) -> snn_params:
+    """Defaults of ``snn_default_params`` with fields overridden by ``kw``."""
+    p = snn_default_params()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def conn_params(**kw) -> snn_conn_params:
+    c = snn_conn_params()
+    c.clip_exc = 1
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise AttributeError(k)
+        setattr(c, k, v)
+    return c
+
+
+class Net:
+    """Owning wrapper around an ``snn_net*`` handle."""
+
+    def __init__(self, p: snn_params, stream: int | None = None):
+        self.p = p
+        self.n = p.n_exc + p.n_inh
+        self.h = snn_create(p, stream)
+
+    def close(self):
+        if self.h:
+            snn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # pass-throughs
+    def connect_fixed_indegree(self, c):
+        snn_connect_fixed_indegree(self.h, c)
+
+    def connect_edges(self, src, tgt, delay, w):
+        snn_connect_edges(self.h, np.ascontiguousarray(src, np.uint32),
+                          np.ascontiguousarray(tgt, np.uint32),
+                          np.ascontiguousarray(delay, np.uint8),
+                          np.ascontiguousarray(w, np.float64))
+
+    def finalize(self):
+        snn_finalize(self.h)
+
+    def stats(self) -> snn_stats:
+        return snn_get_stats(self.h)
+
+    def read_rb(self) -> np.ndarray:
+        out = np.zeros((self.p.n_slots, self.n), np.float32)
+        snn_read_rb(self.h, out)
+        return out
+
+    def read_counts(self) -> np.ndarray:
+        out = np.zeros((self.p.n_slots, self.n), np.uint32)
+        snn_read_counts(self.h, out)
+        return out
+
+    def read_state(self):
+        V = np.zeros(self.n, np.float32)
+        I = np.zeros(self.n, np.float32)
+        J = np.zeros(self.n, np.float32)
+        r = np.zeros(self.n, np.int32)
+        snn_read_state(self.h, V, I, J, r)
+        return V, I, J, r
+
+    def write_state(self, V, I, J, refr):
+        snn_write_state(self.h, np.ascontiguousarray(V, np.float32),
+                        np.ascontiguousarray(I, np.float32),
+                        np.ascontiguousarray(J, np.float32),
+                        np.ascontiguousarray(refr, np.int32))
+
+    def read_store(self):
+        st = self.stats()
+        m = st.n_synapses
+        rp = np.zeros(self.n + 1, np.uint64)
+        tg = np.zeros(max(m, 1), np.uint32)
+        dl = np.zeros(max(m, 1), np.uint8)
+        w = np.zeros(max(m, 1), np.float32)
+        snn_read_store(self.h, rp, tg, dl, w)
+        return rp, tg[:m], dl[:m], w[:m]
+
+    def deliver(self, src, t):
+        return snn_deliver(self.h, np.ascontiguousarray(src, np.uint32),
+                           np.ascontiguousarray(t, np.int32))
+
+    def read_spikes(self, cap: int | None = None):
+        cap = cap or max(self.p.spike_log_capacity, 1)
+        src = np.zeros(cap, np.uint32)
+        t = np.zeros(cap, np.int32)
+        n = snn_read_spikes(self.h, src, t)
+        k = min(n, cap)
+        return src[:k], t[:k]

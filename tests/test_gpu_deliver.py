@@ -1,0 +1,129 @@
+"""Spike delivery in isolation (Section 3.2, Algorithm REF) on identical spike
+lists: GPU vs oracle.  Event counts and per-(slot, target) counts bit-exact,
+ring-buffer values within 1e-5 * sum|w| per cell (FP32 accumulation of the
+stored weights against FP64)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_common import S, check_delivery, edge_net, fixed_net, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+@pytest.fixture(scope="module", params=[0, 1], ids=["fp32", "bf16"])
+def small(request):
+    net, cp = fixed_net(400, 100, 40, 10, 22.4, -112.0, 10, 20, seed=3,
+                        fmt=request.param)
+    store = O.build_fixed_indegree(cp)
+    yield net, store
+    net.close()
+
+
+def test_empty_list(small):
+    net, store = small
+    ev, rb, _, _ = check_delivery(net, store, np.zeros(0, np.uint32),
+                                  np.zeros(0, np.int64))
+    assert ev == 0 and not rb.any()
+
+
+def test_single_spike(small):
+    net, store = small
+    ev, *_ = check_delivery(net, store, [123], [7])
+    assert ev == int(store.row_ptr[124] - store.row_ptr[123])
+
+
+@pytest.mark.parametrize("n_spikes", [1, 31, 32, 33, 1000, 10007])
+def test_random_lists_with_duplicates(small, n_spikes):
+    net, store = small
+    src, t = W.random_spikes(500, n_spikes, 0, 64, seed=n_spikes)
+    check_delivery(net, store, src, t)
+
+
+def test_every_neuron_once(small):
+    net, store = small
+    src = np.arange(500, dtype=np.uint32)
+    ev, *_ = check_delivery(net, store, src, np.full(500, 3))
+    assert ev == 500 * 50
+
+
+def test_emission_steps_wrap_the_ring(small):
+    net, store = small
+    src, _ = W.random_spikes(500, 300, 0, 1, seed=9)
+    t = np.concatenate([np.full(100, 2 ** 31 - 40), np.full(100, 31),
+                        np.full(100, 1000003)])
+    check_delivery(net, store, src, t)
+
+
+def test_deliveries_accumulate(small):
+    net, store = small
+    from paper_2109_12855_gb300 import snn
+    snn.snn_clear_rb(net.h)
+    a = W.random_spikes(500, 700, 0, 20, seed=1)
+    b = W.random_spikes(500, 900, 5, 30, seed=2)
+    net.deliver(a[0], a[1].astype(np.int32))
+    net.deliver(b[0], b[1].astype(np.int32))
+    rb = net.read_rb()
+    rb_o, cnt, absw, _ = O.deliver_ref(store, S, *a)
+    O.deliver_ref(store, S, *b, rb=rb_o)
+    absw2 = O.deliver_ref(store, S, *b)[2]
+    assert np.all(np.abs(rb - rb_o) <= 1e-5 * (absw + absw2))
+
+
+def test_bernoulli_interval_lists_medium():
+    net, cp = fixed_net(16000, 4000, 1600, 400, 22.4, -112.0, 15, 15, seed=8)
+    with net:
+        store = O.build_fixed_indegree(cp)
+        for k, rate in enumerate((8.0, 40.0, 400.0)):
+            src, t = W.bernoulli_spikes(20000, 150 * k, 15, rate, 0.1, seed=k)
+            check_delivery(net, store, src, t)
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_edge_net_long_and_short_segments(fmt):
+    # hub row of 20,000 synapses; many sources with one synapse; sources
+    # with none; delays over the whole ring
+    n = 3000
+    src, tgt, d, w = W.random_edges(n, 3000, 1, 32, seed=12, hub=5,
+                                    hub_edges=20000)
+    net, store = edge_net(n, (src, tgt, d, w), fmt)
+    with net:
+        deg = np.diff(store.row_ptr.astype(np.int64))
+        assert (deg == 0).sum() > 100 and (deg == 1).sum() > 100
+        sp = np.concatenate([np.array([5, 5, 5], np.uint32),
+                             np.flatnonzero(deg == 0)[:50].astype(np.uint32),
+                             np.flatnonzero(deg == 1)[:400].astype(np.uint32)])
+        tt = np.arange(len(sp)) % 40
+        check_delivery(net, store, sp, tt)
+
+
+def test_bad_source_rejected(small):
+    net, _ = small
+    from paper_2109_12855_gb300 import snn
+    with pytest.raises(snn.SnnError) as e:
+        net.deliver([1, 500], [0, 0])
+    assert e.value.code == snn.SNN_E_ARG
+
+
+def test_device_resident_spike_list(small):
+    """Caller's spike list in device memory (torch tensors)."""
+    import torch
+    from paper_2109_12855_gb300 import snn
+    net, store = small
+    src, t = W.random_spikes(500, 2000, 0, 50, seed=44)
+    snn.snn_clear_rb(net.h)
+    ds = torch.from_numpy(src.astype(np.int32)).cuda()
+    dt = torch.from_numpy(t.astype(np.int32)).cuda()
+    ev = snn.snn_deliver(net.h, ds, dt)
+    rb_dev = torch.zeros((S, 500), dtype=torch.float32, device="cuda")
+    snn.snn_read_rb(net.h, rb_dev)
+    torch.cuda.synchronize()
+    rb_o, cnt, absw, ev_o = O.deliver_ref(store, S, src, t)
+    assert ev == ev_o
+    assert np.all(np.abs(rb_dev.cpu().numpy() - rb_o) <= 1e-5 * absw)

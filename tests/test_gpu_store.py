@@ -1,0 +1,101 @@
+"""GPU connection store vs the oracle's: integer parts bit-exact, weights as
+stored (FP32 or BF16 rounding of the same FP64 value)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_common import edge_net, fixed_net, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _compare(net, store, exact_w=True, fmt=0):
+    rp, tg, dl, w = net.read_store()
+    assert np.array_equal(rp, store.row_ptr)
+    assert np.array_equal(tg, store.tgt)
+    assert np.array_equal(dl.astype(np.int32), store.delay)
+    wo = store.w.astype(np.float32)
+    if exact_w:
+        assert np.array_equal(w, wo)
+    else:
+        # FP64 normals come from CUDA's and the host's log/cos, which may
+        # differ in the last FP64 bit; after rounding to the stored format
+        # at most a one-ulp difference can remain, and rarely
+        ulp = np.spacing(np.abs(wo)) * (65536.0 if fmt == 1 else 1.0)
+        diff = np.abs(w - wo)
+        assert np.all(diff <= ulp)
+        assert (diff == 0).mean() > 0.999
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_fixed_indegree_store_small(fmt):
+    net, cp = fixed_net(400, 100, 40, 10, 22.4, -112.0, 10, 20, seed=3,
+                        fmt=fmt)
+    with net:
+        _compare(net, O.build_fixed_indegree(cp))
+        st = net.stats()
+        assert st.min_delay == 10 and st.max_delay == 20 and st.interval == 10
+        assert st.n_synapses == 500 * 50
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_fixed_indegree_store_weight_spread(fmt):
+    net, cp = fixed_net(800, 200, 80, 20, 22.4, -112.0, 10, 20, seed=17,
+                        fmt=fmt, sd_e=2.24, sd_i=11.2)
+    with net:
+        _compare(net, O.build_fixed_indegree(cp), exact_w=False, fmt=fmt)
+
+
+def test_fixed_indegree_store_medium_fixed_delay():
+    net, cp = fixed_net(4000, 1000, 400, 100, 22.4, -112.0, 15, 15, seed=5)
+    with net:
+        _compare(net, O.build_fixed_indegree(cp))
+        assert net.stats().interval == 15
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_edge_store_with_long_segment(fmt):
+    # the hub's segment (20,000 synapses) exceeds the shared-memory sort and
+    # takes the global-memory path; delays span the full ring
+    edges = W.random_edges(3000, 40000, 1, 32, seed=4, hub=77,
+                           hub_edges=20000)
+    net, store = edge_net(3000, edges, fmt)
+    with net:
+        _compare(net, store)
+        assert net.stats().interval == 1
+
+
+def test_edge_store_rejects_bad_edges():
+    from paper_2109_12855_gb300 import snn
+    from gpu_common import stream
+    p = snn.params(n_exc=10, n_inh=0)
+    with snn.Net(p, stream()) as net:
+        with pytest.raises(snn.SnnError) as e:
+            net.connect_edges([1], [10], [3], [1.0])       # target >= N
+        assert e.value.code == snn.SNN_E_ARG
+        with pytest.raises(snn.SnnError):
+            net.connect_edges([1], [2], [33], [1.0])       # delay > n_slots
+        with pytest.raises(snn.SnnError):
+            net.connect_edges([1], [2], [0], [1.0])        # delay 0
+        net.connect_edges([1], [2], [3], [1.0])
+        with pytest.raises(snn.SnnError) as e:
+            net.connect_edges([1], [2], [3], [1.0])        # second connect
+        assert e.value.code == snn.SNN_E_STATE
+
+
+def test_empty_store():
+    from paper_2109_12855_gb300 import snn
+    from gpu_common import stream
+    p = snn.params(n_exc=50, n_inh=0, count_events=1)
+    with snn.Net(p, stream()) as net:
+        net.finalize()
+        st = net.stats()
+        assert st.n_synapses == 0 and st.interval == 32
+        assert net.deliver([1, 2, 3], [0, 0, 5]) == 0
+        assert not net.read_rb().any()
