@@ -1,0 +1,467 @@
+#!/usr/bin/env python
+"""Benchmark: synaptic events delivered per second, real-time factor and HBM
+roofline fraction of spike delivery on one GB300.
+
+Default workload (one JSON line on stdout): the balanced random network with
+112,500 neurons (90,000 E + 22,500 I), in-degree 11,250 (9,000 E + 2,250 I),
+1.27e9 static synapses in 12-byte FP32 records, delay 1.5 ms (15 steps of
+0.1 ms), Poisson drive tuned for about 8 Hz.  One step = 1 s of biological
+time (10,000 grid steps = 667 update/deliver intervals) of the whole hot path:
+fused update with spike compaction, then delivery, every interval.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference      # the FP64 oracle on the host cores
+
+Under torchrun (N > 1) every rank simulates its own independent network
+(replicas: the workload does not exchange data between GPUs); the reported
+value is all ranks' events over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "synaptic events delivered/s & real-time factor on 1 GB300; % of HBM roofline"
+UNIT = "events/s"
+# Poisson drive giving ~8 Hz in the 112,500-neuron network (found with
+# paper_2109_12855_gb300.tune on a GB300; fixed from then on)
+NU_EXT_8HZ = 25757.293701171875
+
+WORKLOADS = {
+    # name: (network recipe, record format, bio ms per step, kind)
+    "balanced-112500-fp32": (W.BALANCED_112500, 0, 1000.0, "simulate"),
+    "balanced-112500-bf16": (W.BALANCED_112500, 1, 1000.0, "simulate"),
+    "balanced-562500-bf16": (W.BALANCED_562500, 1, 500.0, "simulate"),
+    "balanced-1250-fp32": (W.BALANCED_1250, 0, 1000.0, "simulate"),
+    "deliver-112500-fp32": (W.BALANCED_112500, 0, 1000.0, "deliver"),
+    "deliver-562500-bf16": (W.BALANCED_562500, 1, 500.0, "deliver"),
+    # profiling case: the same segment length and launch size as the
+    # 112,500-neuron delivery, with a store of 2.7 GB
+    "deliver-20000-fp32": (W.Balanced("balanced-20000", 16000, 4000, 9000,
+                                      2250, 15, 15, "fp32", 0.0, 150.0),
+                           0, 150.0, "deliver"),
+}
+DEFAULT = "balanced-112500-fp32"
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_over_ranks(ms: float, events: int, extra: float = 0.0):
+    """(max ms, sum events, sum extra) over the process group (or identity)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return ms, events, extra
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    e = torch.tensor([float(events), extra], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(e[0].item()), float(e[1].item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, nu_ext, n_targets, seed=1, n_lists=50, rate_hz=8.0):
+    """The segments of the targets [0, n_targets) (what one NEST thread that
+    owns those targets holds), the oracle's neuron model for them, and a pool
+    of interval spike lists of all sources (Bernoulli at rate_hz) that the
+    timed steps cycle through."""
+    import oracle as O
+    nm = O.Neuron()
+    w_e = O.weight_for_psp(nm, wl.psp_mv)
+    cp = O.Conn(wl.n_e, wl.n_i, wl.k_e, wl.k_i, w_e, -wl.g * w_e, wl.d_lo,
+                wl.d_hi, seed + 1000, wfmt=1 if wl.weight_format == "fp32" else 2)
+    store = O.build_fixed_indegree_targets(cp, 0, n_targets)
+    lists = [W.bernoulli_spikes(wl.n, 0, wl.d_lo, rate_hz, 0.1, seed=100 + k)
+             for k in range(n_lists)]
+    st = O.State(O.init_v(nm, n_targets, seed), np.zeros(n_targets),
+                 np.zeros(n_targets), np.zeros(n_targets, np.int32))
+    return {"O": O, "nm": nm, "w_e": w_e, "store": store, "n": n_targets,
+            "lists": lists, "state": st, "rb_local": np.zeros((32, n_targets)),
+            "rb": np.zeros((32, wl.n)), "t": 0}
+
+
+def oracle_step(ctx, wl, nu_ext, n_intervals, seed=1):
+    """n_intervals of: the oracle's update of the sampled neurons for one
+    interval, then Algorithm REF delivery of one interval's spike list of all
+    sources onto the sampled targets.  Both phases are timed as they stand;
+    the delivered input is not fed back into the sampled neurons.  Returns
+    (events, seconds)."""
+    O, D = ctx["O"], wl.d_lo
+    events, secs = 0, 0.0
+    for _ in range(n_intervals):
+        t = ctx["t"]
+        src, tt = ctx["lists"][(t // D) % len(ctx["lists"])]
+        a = time.perf_counter()
+        O.update(ctx["nm"], ctx["state"], ctx["rb_local"], t, D, nu_ext,
+                 ctx["w_e"], seed)
+        _, _, _, ev = O.deliver_ref(ctx["store"], 32, src, tt + t,
+                                    rb=ctx["rb"], counts=False)
+        secs += time.perf_counter() - a
+        events += ev
+        ctx["t"] = t + D
+    return events, secs
+
+
+def sample_text(wl, n_targets, n_intervals):
+    return (f"targets [0, {n_targets:,}) of {wl.name} "
+            f"({n_targets * wl.k:,} synapses), {n_intervals} intervals of "
+            f"{wl.d_lo} steps: oracle update of those neurons + Algorithm REF "
+            f"delivery of 8 Hz Bernoulli spike lists of all {wl.n:,} sources "
+            f"onto them (single thread)")
+
+
+def run_reference(args, wl, nu_ext):
+    """--impl reference: the oracle as it stands, on the host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    n_targets = args.oracle_targets
+    ctx = oracle_sample(wl, nu_ext, n_targets)
+    per_step = args.oracle_intervals
+    for _ in range(args.warmup):
+        oracle_step(ctx, wl, nu_ext, per_step)
+    ev, secs = 0, 0.0
+    for _ in range(args.steps):
+        e, s_ = oracle_step(ctx, wl, nu_ext, per_step)
+        ev += e
+        secs += s_
+    value = ev / secs
+    sample = sample_text(wl, n_targets, per_step) + " per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def build_net(wl, fmt, nu_ext, seed, stream, log_cap=0):
+    from paper_2109_12855_gb300.tune import build_balanced
+    net, w_e = build_balanced(wl.n_e, wl.n_i, wl.k_e, wl.k_i, wl.d_lo, wl.d_hi,
+                              fmt, wl.sd_rel, seed, stream, psp_mv=wl.psp_mv,
+                              g=wl.g, nu_ext=nu_ext,
+                              spike_log_capacity=log_cap)
+    from paper_2109_12855_gb300 import snn
+    snn.snn_set_drive(net.h, nu_ext, w_e)
+    return net, w_e
+
+
+def timed(torch, stream, fn, k):
+    """Run fn k times between events on the library's stream; ms total."""
+    barrier()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(k):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    return a.elapsed_time(b)
+
+
+def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
+    import torch
+    from paper_2109_12855_gb300 import snn
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    s = torch.cuda.Stream()
+    torch.cuda.set_stream(s)
+    stream = s.cuda_stream
+    steps_per = int(round(bio_ms / 0.1))
+    rec_bytes = 12 if fmt == 0 else 8
+    expected_spikes = int(wl.n * 8.0 * bio_ms * 1e-3 * 4) + 100000
+    # the log must hold every spike of the timed region (read once after it)
+    log_cap = expected_spikes * (max(args.steps, 3) + 1)
+
+    t_build = time.perf_counter()
+    net, w_e = build_net(wl, fmt, nu_ext, 1 + rank, stream, log_cap=log_cap)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t_build
+    h = net.h
+    st0 = net.stats()
+    D = st0.interval
+
+    if kind == "deliver":
+        # record one step of the whole network's spikes (or draw Bernoulli
+        # lists at --replay-rate), then replay them interval by interval
+        # through snn_deliver from device memory
+        if args.replay_rate:
+            src, t = W.bernoulli_spikes(wl.n, 0, steps_per, args.replay_rate,
+                                        0.1, seed=5)
+        else:
+            snn.snn_simulate(h, steps_per)
+            src, t = net.read_spikes(log_cap)
+        order = np.lexsort((src, t))
+        src, t = src[order], t[order]
+        iv = (t // D).astype(np.int64)
+        bounds = np.searchsorted(iv, np.arange(iv.min(), iv.max() + 2)) \
+            if len(iv) else np.zeros(1, np.int64)
+        d_src = torch.from_numpy(src.astype(np.int32)).cuda()
+        d_t = torch.from_numpy(t.astype(np.int32)).cuda()
+        lists = [(int(a), int(b)) for a, b in zip(bounds[:-1], bounds[1:])]
+
+        def step():
+            for a, b in lists:
+                if b > a:
+                    snn.lib().snn_deliver(h, d_src.data_ptr() + 4 * a,
+                                          d_t.data_ptr() + 4 * a, b - a,
+                                          snn.SNN_MEM_DEVICE, None)
+    else:
+        def step():
+            snn.snn_simulate(h, steps_per)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    net.read_spikes(log_cap)      # empty the log
+
+    # ---- timed region: production path (graphs) --------------------------
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    clocks = Clocks(gpu_index)
+    a = net.stats()
+    clocks.start()
+    ms = timed(torch, s, step, args.steps)
+    clk = clocks.stop()
+    b = net.stats()
+    events = b.events_delivered - a.events_delivered
+    spikes = b.spikes - a.spikes
+    launches = b.kernel_launches - a.kernel_launches
+    net.read_spikes(log_cap)
+    ms_max, events_all, spikes_all = reduce_over_ranks(ms, events, spikes)
+    value = events_all / (ms_max * 1e-3)
+
+    # ---- roofline: the same steps with every launch between CUDA events ----
+    snn.snn_set_profiling(h, True)
+    a = net.stats()
+    ms_prof = timed(torch, s, step, args.steps)
+    b = net.stats()
+    snn.snn_set_profiling(h, False)
+    n_del = b.deliver_launches - a.deliver_launches
+    ms_del = b.ms_deliver - a.ms_deliver
+    ms_upd = b.ms_update - a.ms_update
+    ev_prof = b.events_delivered - a.events_delivered
+    sp_prof = b.spikes - a.spikes
+    net.read_spikes(log_cap)
+    # algorithmic bytes: one record per event; per spike a list entry (16 B)
+    # and its two row offsets (16 B)
+    n_listed = sp_prof if kind == "simulate" else len(src) * args.steps
+    alg_bytes = rec_bytes * ev_prof + 32 * n_listed
+    per_launch_bytes = alg_bytes / max(n_del, 1)
+    per_launch_s = ms_del * 1e-3 / max(n_del, 1)
+    hbm, peak_kind = peaks()
+    achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s else 0.0
+
+    # ---- end to end through the public API with host buffers --------------
+    e2e = None
+    if kind == "simulate":
+        n = wl.n
+        hV = torch.empty(n, dtype=torch.float32).pin_memory()
+        hI = torch.empty(n, dtype=torch.float32).pin_memory()
+        hJ = torch.empty(n, dtype=torch.float32).pin_memory()
+        hR = torch.empty(n, dtype=torch.int32).pin_memory()
+        hsrc = torch.empty(expected_spikes, dtype=torch.int32).pin_memory()
+        ht = torch.empty(expected_spikes, dtype=torch.int32).pin_memory()
+        snn.snn_read_state(h, hV, hI, hJ, hR)
+        counts = {"spikes": 0}
+
+        def e2e_step():
+            snn.snn_write_state(h, hV, hI, hJ, hR)           # h2d
+            snn.snn_simulate(h, steps_per)
+            counts["spikes"] += snn.snn_read_spikes(h, hsrc, ht)  # d2h
+            snn.snn_read_state(h, hV, hI, hJ, hR)            # d2h
+
+        k_e2e = max(1, min(args.steps, 3))
+        a = net.stats()
+        ms_e2e = timed(torch, s, e2e_step, k_e2e)
+        b = net.stats()
+        ev_e2e = b.events_delivered - a.events_delivered
+        ms_e2e_max, ev_e2e_all, _ = reduce_over_ranks(ms_e2e, ev_e2e)
+        e2e = {"value": ev_e2e_all / (ms_e2e_max * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": 16 * n,
+               "d2h_bytes_per_step": int(16 * n + 8 * counts["spikes"] / k_e2e),
+               "steps": k_e2e}
+    st = net.stats()
+    err = st.error_flags
+    net.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        ctx = oracle_sample(wl, nu_ext, args.oracle_targets)
+        oracle_step(ctx, wl, nu_ext, 5)
+        e_c, s_c = oracle_step(ctx, wl, nu_ext, args.cpu_intervals)
+        cpu = {"value": e_c / s_c, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "seconds": s_c,
+               "sample": sample_text(wl, args.oracle_targets,
+                                     args.cpu_intervals)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if fmt == 0 else "bf16-store/f32-accumulate",
+        "data": "synthetic",
+        "real_time_factor": (ms_max / args.steps) / bio_ms,
+        "config": {"workload": args.workload, "neurons": wl.n,
+                   "in_degree": wl.k, "synapses": wl.n_synapses,
+                   "record_bytes": rec_bytes, "interval_steps": D,
+                   "bio_ms_per_step": bio_ms, "nu_ext_hz": nu_ext,
+                   "mean_rate_hz": spikes_all / ws / wl.n / (
+                       args.steps * bio_ms * 1e-3),
+                   "build_s": t_build,
+                   "l2": "inputs larger than L2 (the record store is "
+                         f"{wl.n_synapses * rec_bytes / 1e9:.1f} GB, streamed "
+                         "from HBM every step)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_source": peak_kind,
+                     "traffic": None, "kernel": "k_deliver",
+                     "launches": n_del, "avg_launch_us": 1e3 * ms_del / max(n_del, 1),
+                     "bytes_per_event": rec_bytes,
+                     "ms_deliver_share": ms_del / ms_prof if ms_prof else None,
+                     "ms_update_share": ms_upd / ms_prof if ms_prof else None,
+                     "profiled_value": ev_prof / (ms_prof * 1e-3)},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "error_flags": err,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
+    ap.add_argument("--nu-ext", type=float, default=None)
+    ap.add_argument("--oracle-targets", type=int, default=4500)
+    ap.add_argument("--oracle-intervals", type=int, default=100,
+                    help="oracle intervals per --impl reference step")
+    ap.add_argument("--cpu-intervals", type=int, default=1500,
+                    help="oracle intervals timed for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--replay-rate", type=float, default=0.0,
+                    help="deliver workloads: Bernoulli lists at this rate "
+                         "instead of a recorded run")
+    args = ap.parse_args()
+    wl, fmt, bio_ms, kind = WORKLOADS[args.workload]
+    nu_ext = args.nu_ext if args.nu_ext is not None else NU_EXT_8HZ
+    if args.impl == "reference":
+        run_reference(args, wl, nu_ext)
+    else:
+        from paper_2109_12855_gb300 import build
+        build()
+        run_ours(args, wl, fmt, bio_ms, kind, nu_ext)
+
+
+if __name__ == "__main__":
+    main()

@@ -249,6 +249,10 @@ int snn_write_state(snn_net* net, const float* V, const float* I,
 int snn_read_store(snn_net* net, uint64_t* row_ptr, uint32_t* tgt,
                    uint8_t* delay, float* w, int mem);
 
+/* Replace the Poisson drive (rate nu_ext Hz, weight w_ext pA per drive
+ * spike) from the next update on.  Errors: SNN_E_ARG (negative rate, or a
+ * rate whose inversion table exceeds 128 outcomes). */
+int snn_set_drive(snn_net* net, double nu_ext, double w_ext);
 /* Set the step counter (next step to update). */
 int snn_set_time(snn_net* net, int64_t t);
 /* Profiling on: every update and deliver launch is bracketed by CUDA events

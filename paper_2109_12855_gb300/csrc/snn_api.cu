@@ -975,6 +975,26 @@ int snn_read_store(snn_net* net, uint64_t* row_ptr, uint32_t* tgt,
   return SNN_OK;
 }
 
+int snn_set_drive(snn_net* net, double nu_ext, double w_ext) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(nu_ext >= 0 && isfinite(nu_ext) && isfinite(w_ext), SNN_E_ARG,
+      "bad drive");
+  REQ(!net->pending, SNN_E_STATE, "spikes of an update are pending");
+  snn_params p = net->p;
+  p.nu_ext = nu_ext;
+  p.w_ext = w_ext;
+  UpdConst uc;
+  REQ(make_upd_const(p, &uc) == 0, SNN_E_ARG,
+      "Poisson drive rate too high for the inversion table");
+  net->p = p;
+  net->uc = uc;
+  if (net->graph) {  // the captured graph holds the old constants
+    cudaGraphExecDestroy(net->graph);
+    net->graph = nullptr;
+  }
+  return SNN_OK;
+}
+
 int snn_set_time(snn_net* net, int64_t t) {
   REQ(net, SNN_E_ARG, "null net");
   REQ(t >= 0 && t < (1ll << 31), SNN_E_ARG, "t out of range");

@@ -28,7 +28,8 @@ EXPORTS = [
     "snn_connect_edges", "snn_finalize", "snn_update", "snn_deliver_pending",
     "snn_discard_pending", "snn_deliver", "snn_simulate", "snn_read_spikes",
     "snn_read_rb", "snn_write_rb", "snn_read_counts", "snn_clear_rb",
-    "snn_read_state", "snn_write_state", "snn_read_store", "snn_set_time",
+    "snn_read_state", "snn_write_state", "snn_read_store", "snn_set_drive",
+    "snn_set_time",
     "snn_set_profiling", "snn_get_stats", "snn_clear_errors", "snn_sync",
     "snn_destroy",
 ]
@@ -112,6 +113,7 @@ def lib():
             "snn_read_state": ([_P, _P, _P, _P, _P, C.c_int], C.c_int),
             "snn_write_state": ([_P, _P, _P, _P, _P, C.c_int], C.c_int),
             "snn_read_store": ([_P, _P, _P, _P, _P, C.c_int], C.c_int),
+            "snn_set_drive": ([_P, C.c_double, C.c_double], C.c_int),
             "snn_set_time": ([_P, C.c_int64], C.c_int),
             "snn_set_profiling": ([_P, C.c_int], C.c_int),
             "snn_get_stats": ([_P, C.POINTER(snn_stats)], C.c_int),
@@ -260,6 +262,10 @@ def snn_read_store(net, row_ptr=None, tgt=None, delay=None, w=None):
     mem = _mem_of(row_ptr, tgt, delay, w)
     _check(lib().snn_read_store(net, _buf(row_ptr)[0], _buf(tgt)[0],
                                 _buf(delay)[0], _buf(w)[0], mem))
+
+
+def snn_set_drive(net, nu_ext: float, w_ext: float):
+    _check(lib().snn_set_drive(net, nu_ext, w_ext))
 
 
 def snn_set_time(net, t: int):
