@@ -214,6 +214,30 @@ int snn_discard_pending(snn_net* net);
 int snn_deliver(snn_net* net, const uint32_t* src, const int32_t* t_emit,
                 uint32_t n_spikes, int mem, uint64_t* n_events_out);
 
+/* Same delivery as snn_deliver, for callers that cannot let the library
+ * allocate device memory: processes whose device memory is fully reserved
+ * by another allocator, or latency-critical loops where cudaMalloc's implicit
+ * device synchronisation is not acceptable.  (The paper has no counterpart:
+ * this is a deployment variant of the delivery entry point.)
+ *
+ * The caller's list is staged in a fixed scratch array that every GPU
+ * loading the library holds until the process exits (SNN_NOALLOC_MAX_SPIKES
+ * entries of 16 bytes = 4 MiB); the call itself allocates nothing.
+ *  - src, t_emit: n_spikes entries in DEVICE memory (no host staging).
+ *  - n_spikes > SNN_NOALLOC_MAX_SPIKES is rejected with SNN_E_ARG.
+ *  - The first call on a device looks up the scratch's device address; make
+ *    that first call before any stream capture.
+ *  - All calls share the scratch: calls whose GPU work overlaps (different
+ *    streams, or other host threads) race and must be serialised by the
+ *    caller.  Counters that must start at zero are cleared by every call.
+ *  - n_events_out (optional, host): additions made; when non-null the call
+ *    synchronises the net's stream.
+ * Errors: SNN_E_ARG, SNN_E_STATE (not finalized), SNN_E_CUDA. */
+#define SNN_NOALLOC_MAX_SPIKES (1u << 18)
+int snn_deliver_noalloc(snn_net* net, const uint32_t* src,
+                        const int32_t* t_emit, uint32_t n_spikes,
+                        uint64_t* n_events_out);
+
 /* Advance the net by n_steps grid steps from its current time: repeat
  * {update one interval; deliver its spikes} (the time-driven cycle of
  * Section 1); the last interval may be shorter.  Full intervals run as

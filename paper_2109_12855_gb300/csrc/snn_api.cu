@@ -775,6 +775,38 @@ int snn_deliver(snn_net* net, const uint32_t* src, const int32_t* t_emit,
   return SNN_OK;
 }
 
+int snn_deliver_noalloc(snn_net* net, const uint32_t* src,
+                        const int32_t* t_emit, uint32_t n_spikes,
+                        uint64_t* n_events_out) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  REQ(n_spikes <= SNN_NOALLOC_MAX_SPIKES, SNN_E_ARG,
+      "%u spikes exceed the allocation-free scratch of %u spikes", n_spikes,
+      (unsigned)SNN_NOALLOC_MAX_SPIKES);
+  REQ(n_spikes == 0 || (src && t_emit), SNN_E_ARG, "null spike arrays");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  if (n_spikes == 0) {
+    if (n_events_out) *n_events_out = 0;
+    return SNN_OK;
+  }
+  unsigned long long ev0 = 0, ev1 = 0;
+  if (n_events_out) {
+    CK(cudaMemcpyAsync(&ev0, &net->ctl->events, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  CK(launch_deliver_noalloc(net->view(), src, t_emit, n_spikes, s));
+  net->launches += 2;
+  net->del_launches += 1;
+  if (n_events_out) {
+    CK(cudaMemcpyAsync(&ev1, &net->ctl->events, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *n_events_out = ev1 - ev0;
+  }
+  return SNN_OK;
+}
+
 int snn_simulate(snn_net* net, int64_t n_steps) {
   REQ(net, SNN_E_ARG, "null net");
   REQ(net->finalized, SNN_E_STATE, "net not finalized");

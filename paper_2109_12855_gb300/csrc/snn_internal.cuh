@@ -202,6 +202,9 @@ cudaError_t launch_prepare_external(const NetView& v, const uint32_t* src,
                                     SpikeEntry* list,
                                     unsigned long long* pair, cudaStream_t s);
 int deliver_grid_size(int fmt);
+cudaError_t launch_deliver_noalloc(const NetView& v, const uint32_t* src,
+                                   const int32_t* t, uint32_t n,
+                                   cudaStream_t s);
 
 // store construction
 struct BuildFixed {

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "snn_internal.cuh"
 
 namespace snn {
@@ -477,4 +479,66 @@ cudaError_t launch_prepare_external(const NetView& v, const uint32_t* src,
   return cudaGetLastError();
 }
 
+}  // namespace snn
+
+// ---------------------------------------------------------------------------
+// Allocation-free delivery of a caller's spike list.
+//
+// snn_deliver stages a caller's list in a buffer the library grows with
+// cudaMalloc.  Some callers cannot let a library allocate: processes whose
+// device memory is fully reserved by another allocator (a framework's caching
+// allocator holding all of HBM), and latency-critical loops where cudaMalloc's
+// implicit device synchronisation is not acceptable.  For them the list is
+// staged in this file-scope device array instead: a fixed 4 MiB (2^18
+// entries) held by every GPU that loads the library until the process exits.
+// All calls share it, so calls whose work overlaps on the GPU race; the
+// counters that must start at zero are cleared by every call.
+// ---------------------------------------------------------------------------
+namespace snn {
+namespace {
+struct NoAllocScratch {
+  SpikeEntry list[SNN_NOALLOC_MAX_SPIKES];
+  unsigned long long pair;
+  unsigned int done;
+  unsigned int pad_;
+};
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+NoAllocScratch* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device, looked up once per
+// device (in host code the symbol is only a stand-in for that address).
+cudaError_t noalloc_scratch(NoAllocScratch** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<NoAllocScratch*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t launch_deliver_noalloc(const NetView& v, const uint32_t* src,
+                                   const int32_t* t, uint32_t n,
+                                   cudaStream_t s) {
+  if (n > SNN_NOALLOC_MAX_SPIKES) return cudaErrorInvalidValue;
+  NoAllocScratch* sc = nullptr;
+  cudaError_t e = noalloc_scratch(&sc);
+  if (e != cudaSuccess) return e;
+  // the list counters must start at zero: clear them on every call
+  e = cudaMemsetAsync(&sc->pair, 0, sizeof(unsigned long long) + 2 * sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  e = launch_prepare_external(v, src, t, n, sc->list, &sc->pair, s);
+  if (e != cudaSuccess) return e;
+  return launch_deliver(v, &sc->pair, &sc->done, sc->list, 0, s);
+}
 }  // namespace snn

@@ -26,7 +26,8 @@ EXPORTS = [
     "snn_abi_version", "snn_last_error", "snn_default_params",
     "snn_psc_weight_for_psp", "snn_create", "snn_connect_fixed_indegree",
     "snn_connect_edges", "snn_finalize", "snn_update", "snn_deliver_pending",
-    "snn_discard_pending", "snn_deliver", "snn_simulate", "snn_read_spikes",
+    "snn_discard_pending", "snn_deliver", "snn_deliver_noalloc",
+    "snn_simulate", "snn_read_spikes",
     "snn_read_rb", "snn_write_rb", "snn_read_counts", "snn_clear_rb",
     "snn_read_state", "snn_write_state", "snn_read_store", "snn_set_drive",
     "snn_set_time",
@@ -103,6 +104,8 @@ def lib():
             "snn_discard_pending": ([_P], C.c_int),
             "snn_deliver": ([_P, _P, _P, C.c_uint32, C.c_int,
                              C.POINTER(C.c_uint64)], C.c_int),
+            "snn_deliver_noalloc": ([_P, _P, _P, C.c_uint32,
+                                     C.POINTER(C.c_uint64)], C.c_int),
             "snn_simulate": ([_P, C.c_int64], C.c_int),
             "snn_read_spikes": ([_P, _P, _P, C.c_uint64, C.POINTER(C.c_uint64),
                                  C.c_int], C.c_int),
@@ -209,6 +212,20 @@ def snn_deliver(net, src, t_emit, want_events: bool = True):
     ev = C.c_uint64()
     _check(lib().snn_deliver(net, _buf(src)[0], _buf(t_emit)[0], len(src), mem,
                              C.byref(ev) if want_events else None))
+    return ev.value if want_events else None
+
+
+SNN_NOALLOC_MAX_SPIKES = 1 << 18
+
+
+def snn_deliver_noalloc(net, src, t_emit, want_events: bool = True):
+    """Allocation-free delivery; src/t_emit must be CUDA tensors."""
+    ps, ms = _buf(src)
+    pt, mt = _buf(t_emit)
+    assert ms == mt == SNN_MEM_DEVICE, "spike arrays must be device memory"
+    ev = C.c_uint64()
+    _check(lib().snn_deliver_noalloc(net, ps, pt, len(src),
+                                     C.byref(ev) if want_events else None))
     return ev.value if want_events else None
 
 
