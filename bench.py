@@ -47,6 +47,11 @@ WORKLOADS = {
     "balanced-1250-fp32": (W.BALANCED_1250, 0, 1000.0, "simulate"),
     "deliver-112500-fp32": (W.BALANCED_112500, 0, 1000.0, "deliver"),
     "deliver-562500-bf16": (W.BALANCED_562500, 1, 500.0, "deliver"),
+    # profiling case for the update kernel: all 112,500 neurons, in-degree
+    # 1,125 (a 1.5 GB store)
+    "update-112500": (W.Balanced("balanced-112500-k1125", 90000, 22500, 900,
+                                 225, 15, 15, "fp32", 0.0, 1000.0),
+                      0, 1000.0, "simulate"),
     # profiling case: the same segment length and launch size as the
     # 112,500-neuron delivery, with a store of 2.7 GB
     "deliver-20000-fp32": (W.Balanced("balanced-20000", 16000, 4000, 9000,
@@ -230,12 +235,13 @@ def run_reference(args, wl, nu_ext):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def build_net(wl, fmt, nu_ext, seed, stream, log_cap=0):
+def build_net(wl, fmt, nu_ext, seed, stream, log_cap=0, deliver_mode=0):
     from paper_2109_12855_gb300.tune import build_balanced
     net, w_e = build_balanced(wl.n_e, wl.n_i, wl.k_e, wl.k_i, wl.d_lo, wl.d_hi,
                               fmt, wl.sd_rel, seed, stream, psp_mv=wl.psp_mv,
                               g=wl.g, nu_ext=nu_ext,
-                              spike_log_capacity=log_cap)
+                              spike_log_capacity=log_cap,
+                              deliver_mode=deliver_mode)
     from paper_2109_12855_gb300 import snn
     snn.snn_set_drive(net.h, nu_ext, w_e)
     return net, w_e
@@ -276,11 +282,14 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
     log_cap = expected_spikes * (max(args.steps, 3) + 1)
 
     t_build = time.perf_counter()
-    net, w_e = build_net(wl, fmt, nu_ext, 1 + rank, stream, log_cap=log_cap)
+    mode = {"tiled": 0, "atomic": 1}[args.deliver_mode]
+    net, w_e = build_net(wl, fmt, nu_ext, 1 + rank, stream, log_cap=log_cap,
+                         deliver_mode=mode)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t_build
     h = net.h
     st0 = net.stats()
+    st_tiles = st0
     D = st0.interval
 
     if kind == "deliver":
@@ -422,6 +431,9 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
                      "peak_source": peak_kind,
                      "traffic": None, "kernel": "k_deliver",
                      "launches": n_del, "avg_launch_us": 1e3 * ms_del / max(n_del, 1),
+                     "deliver_mode": args.deliver_mode,
+                     "tiles": [st_tiles.n_tiles, st_tiles.tile_width,
+                               st_tiles.window],
                      "bytes_per_event": rec_bytes,
                      "ms_deliver_share": ms_del / ms_prof if ms_prof else None,
                      "ms_update_share": ms_upd / ms_prof if ms_prof else None,
@@ -449,6 +461,8 @@ def main():
     ap.add_argument("--cpu-intervals", type=int, default=1500,
                     help="oracle intervals timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--deliver-mode", choices=["tiled", "atomic"],
+                    default="tiled")
     ap.add_argument("--replay-rate", type=float, default=0.0,
                     help="deliver workloads: Bernoulli lists at this rate "
                          "instead of a recorded run")

@@ -66,12 +66,25 @@ enum { SNN_MEM_HOST = 0, SNN_MEM_DEVICE = 1 };
  * Both accumulate into a float32 ring buffer. */
 enum { SNN_W_FP32_12B = 0, SNN_W_BF16_8B = 1 };
 
+/* Delivery kernels.
+ *  SNN_DELIVER_TILED: targets are cut into tiles of about N / (k * #SMs)
+ *    neurons (k the smallest integer for which a tile's ring-buffer window
+ *    fits in shared memory); each segment is stored sorted by (tile, delay,
+ *    target) with a per-row tile index, and one CTA per tile accumulates
+ *    the interval's events for its targets in shared memory, then adds them
+ *    into the ring buffer without global atomics.
+ *  SNN_DELIVER_ATOMIC: every event is one red.global.add.f32 (merge-path
+ *    split of the interval's chunks over all warps). */
+enum { SNN_DELIVER_TILED = 0, SNN_DELIVER_ATOMIC = 1 };
+
 /* Device error flags (snn_stats.error_flags, sticky until snn_clear_errors). */
 enum {
   SNN_ERRF_SPIKE_LIST = 1u << 0, /* interval spike list overflowed */
   SNN_ERRF_SPIKE_LOG = 1u << 1,  /* spike recording log overflowed */
   SNN_ERRF_BAD_SOURCE = 1u << 2, /* external spike with source >= N */
-  SNN_ERRF_CHUNKS = 1u << 3      /* chunk counter of one interval overflowed */
+  SNN_ERRF_CHUNKS = 1u << 3,     /* chunk counter of one interval overflowed */
+  SNN_ERRF_TIMEOUT = 1u << 4     /* a bounded device wait gave up (delivery of
+                                    that launch is incomplete) */
 };
 
 /* Neuron model and simulation parameters (iaf_psc_alpha, resting potential
@@ -105,7 +118,8 @@ typedef struct snn_params {
                              0: V0 = 0 */
   int32_t count_events;   /* 1: keep a uint32 [n_slots][N] per-cell count of
                              delivered events (test instrument) */
-  int32_t pad_;
+  int32_t deliver_mode;   /* SNN_DELIVER_TILED (0, default) or
+                             SNN_DELIVER_ATOMIC (1); see below */
   uint64_t spike_log_capacity; /* entries kept for snn_read_spikes (0: none) */
 } snn_params;
 
@@ -144,6 +158,9 @@ typedef struct snn_stats {
   double ms_update, ms_deliver; /* CUDA-event times while profiling is on */
   uint64_t bytes_per_record;    /* 12 or 8 */
   uint64_t store_bytes;         /* device bytes of the record array */
+  uint32_t n_tiles, tile_width; /* target tiles of the store */
+  int32_t window;               /* ring steps one interval reaches */
+  int32_t deliver_mode;         /* kernel used by update/simulate */
 } snn_stats;
 
 typedef struct snn_net snn_net;

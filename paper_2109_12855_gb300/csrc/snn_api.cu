@@ -49,8 +49,8 @@ int fail(int code, const char* fmt, ...) {
     if (!(cond)) return fail(code, __VA_ARGS__); \
   } while (0)
 
-constexpr uint32_t kSortCap = 16384;  // must match k_sort_pack's shared cap
 constexpr int kGraphIntervals = 8;
+constexpr size_t kTileSmemBudget = 200 * 1024;  // accumulator bytes per CTA
 
 // ---------------------------------------------------------------------------
 // Neuron constants, computed in FP64.
@@ -164,6 +164,12 @@ struct snn_net {
   uint64_t* row_ptr = nullptr;
   void* recs = nullptr;
   uint64_t n_syn = 0, recs_bytes = 0;
+  uint32_t* tile_off = nullptr;  // [n][n_tiles + 1]
+  uint32_t tile_w = 0, n_tiles = 0;
+  int lo_bits = 0;
+  int window = 0;
+  uint32_t mult_max = 0, k_in_max = 0, spikes_per_iv = 1;
+  float max_abs_w = 0.f;
   SpikeEntry* list = nullptr;
   uint64_t list_cap = 0;
   SpikeEntry* ext_list = nullptr;
@@ -197,6 +203,16 @@ struct snn_net {
     v.counts = counts;
     v.row_ptr = row_ptr;
     v.recs = recs;
+    v.tile_off = tile_off;
+    v.tile_w = tile_w;
+    v.n_tiles = n_tiles;
+    v.d_min = dmin;
+    v.d_max = dmax;
+    v.window = window;
+    v.mult_max = mult_max;
+    v.k_in_max = k_in_max;
+    v.spikes_per_iv = spikes_per_iv;
+    v.max_abs_w = max_abs_w;
     v.list = list;
     v.list_cap = list_cap;
     v.log_src = log_src;
@@ -236,11 +252,58 @@ int set_device(snn_net* net) {
   return SNN_OK;
 }
 
+// Tile geometry for the tiled delivery: the fewest tiles that are a
+// multiple of the SM count and whose ring-buffer window (window steps x
+// tile width cells of two int32 accumulators) fits the shared-memory budget.  The sort key holds the
+// tile and the position in it in 24 bits; when a non-power-of-two width
+// would not fit them, the width is rounded up to a power of two.
+void choose_tiles(uint32_t n, int window, uint32_t* tile_w, int* lo_bits,
+                  uint32_t* n_tiles) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms < 1) sms = 1;
+  const uint64_t tw_max =
+      std::max<uint64_t>(32, kTileSmemBudget / (8ull * std::max(window, 1)));
+  uint64_t tw = n;
+  for (uint64_t k = 1; k <= 4096; ++k) {
+    tw = (n + k * sms - 1) / (k * sms);
+    if (tw <= tw_max) break;
+  }
+  tw = std::max<uint64_t>(tw, std::min<uint64_t>(64, n));
+  int lb = 1;
+  while ((1ull << lb) < tw) ++lb;
+  uint64_t nt = (n + tw - 1) / tw;
+  if (nt > (1ull << (24 - lb))) {
+    tw = 1ull << lb;
+    nt = (n + tw - 1) / tw;
+  }
+  *tile_w = (uint32_t)tw;
+  *lo_bits = lb;
+  *n_tiles = (uint32_t)nt;
+}
+
+bool use_tiled(const snn_net* net) {
+  return net->p.deliver_mode == SNN_DELIVER_TILED && net->n_syn > 0 &&
+         net->tile_off && (size_t)net->window * net->tile_w * 8 <= kTileSmemBudget;
+}
+
+cudaError_t launch_deliver_any(snn_net* net, unsigned long long* pair,
+                               unsigned int* done, const SpikeEntry* list,
+                               int from_list_range, int advance_time) {
+  NetView v = net->view();
+  if (use_tiled(net))
+    return launch_deliver_tiled(v, pair, done, list, from_list_range,
+                                advance_time, net->stream);
+  return launch_deliver(v, pair, done, list, advance_time, net->stream);
+}
+
 // Build the store from per-row key arrays: host row offsets from the device
 // out-degrees, scatter (callback), sort and pack.
 template <class Scatter>
 int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
-                const BuildFixed* bf, const double* d_edge_w) {
+                const BuildFixed* bf, const double* d_edge_w, int d_lo,
+                int d_hi) {
   cudaStream_t s = net->stream;
   const uint32_t n = net->n;
   std::vector<uint32_t> deg(n);
@@ -270,12 +333,17 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
   CK(dalloc(&net->row_ptr, (n + 1) * sizeof(uint64_t)));
   CK(cudaMemcpyAsync(net->row_ptr, rp.data(), (n + 1) * sizeof(uint64_t),
                      cudaMemcpyHostToDevice, s));
+  // tiles sized for the widest window the interval can reach
+  const int iv = net->p.interval ? net->p.interval : d_lo;
+  choose_tiles(n, iv + (d_hi - d_lo), &net->tile_w, &net->lo_bits,
+               &net->n_tiles);
+  CK(dalloc(&net->tile_off, (uint64_t)n * (net->n_tiles + 1) * sizeof(uint32_t)));
   // keys; for 8-byte records the key array becomes the record array
   uint64_t* keys = nullptr;
   CK(dalloc(&keys, padded * sizeof(uint64_t)));
   uint32_t* cursor = d_deg;  // reuse as the scatter cursor
   CK(cudaMemsetAsync(cursor, 0, n * sizeof(uint32_t), s));
-  CK(scatter(net->row_ptr, cursor, keys));
+  CK(scatter(net->row_ptr, cursor, keys, net->tile_w, net->lo_bits));
   void* recs = nullptr;
   if (rec_bytes == 8) {
     recs = keys;
@@ -303,10 +371,19 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
                        long_off.size() * sizeof(uint64_t),
                        cudaMemcpyHostToDevice, s));
   }
+  uint32_t* d_stats = nullptr;
+  CK(dalloc(&d_stats, 2 * sizeof(uint32_t)));
+  CK(cudaMemsetAsync(d_stats, 0, 2 * sizeof(uint32_t), s));
   CK(build_sort_pack(net->fmt, n, net->row_ptr, keys, recs, bf, d_edge_w,
                      max_row, d_long, (uint32_t)long_rows.size(), d_scr,
-                     d_loff, s));
+                     d_loff, net->tile_w, net->lo_bits, net->n_tiles,
+                     net->tile_off, d_stats, s));
+  uint32_t h_stats[2] = {0, 0};
+  CK(cudaMemcpyAsync(h_stats, d_stats, sizeof h_stats, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  dfree(d_stats);
+  net->mult_max = h_stats[0];
+  memcpy(&net->max_abs_w, &h_stats[1], sizeof(float));
   if (recs != keys) dfree(keys);
   dfree(d_long);
   dfree(d_loff);
@@ -348,8 +425,8 @@ cudaEvent_t pool_event(snn_net* net, size_t k) {
 int launch_interval(snn_net* net, int steps) {
   NetView v = net->view();
   CK(launch_update(v, net->uc, steps, 1, 0, net->stream));
-  CK(launch_deliver(v, &net->ctl->pair, &net->ctl->done, net->list, 1,
-                    net->stream));
+  CK(launch_deliver_any(net, &net->ctl->pair, &net->ctl->done, net->list, 0,
+                        1));
   net->launches += 2;
   net->upd_launches += 1;
   net->del_launches += 1;
@@ -363,8 +440,8 @@ int capture_graph(snn_net* net) {
   NetView v = net->view();
   for (int k = 0; k < kGraphIntervals; ++k) {
     cudaError_t e1 = launch_update(v, net->uc, net->interval, 1, 0, net->stream);
-    cudaError_t e2 = launch_deliver(v, &net->ctl->pair, &net->ctl->done,
-                                    net->list, 1, net->stream);
+    cudaError_t e2 = launch_deliver_any(net, &net->ctl->pair, &net->ctl->done,
+                                        net->list, 0, 1);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
       cudaStreamEndCapture(net->stream, &g);
       return fail(SNN_E_CUDA, "graph capture failed: %s",
@@ -451,6 +528,8 @@ int snn_create(const snn_params* p, void* stream, snn_net** out) {
       "n_slots must be a power of two in [2, 256]");
   REQ(p->interval >= 0 && p->interval <= p->n_slots, SNN_E_ARG,
       "bad interval");
+  REQ(p->deliver_mode == SNN_DELIVER_TILED || p->deliver_mode == SNN_DELIVER_ATOMIC,
+      SNN_E_ARG, "bad deliver_mode %d", p->deliver_mode);
   snn_net* net = new snn_net();
   net->p = *p;
   net->n = (uint32_t)n;
@@ -548,12 +627,12 @@ int snn_connect_fixed_indegree(snn_net* net, const snn_conn_params* c) {
   cudaStream_t s = net->stream;
   rc = build_store(
       net, deg,
-      [&](const uint64_t* rp, uint32_t* cur, uint64_t* keys) {
-        return build_scatter_fixed(b, rp, cur, keys, s);
-      },
-      &b, nullptr);
+      [&](const uint64_t* rp, uint32_t* cur, uint64_t* keys, uint32_t tw,
+          int lb) { return build_scatter_fixed(b, rp, cur, keys, tw, lb, s); },
+      &b, nullptr, c->d_lo, c->d_hi);
   dfree(deg);
   net->launches += 3;
+  net->k_in_max = c->k_exc + c->k_inh;
   return rc;
 }
 
@@ -591,7 +670,11 @@ int snn_connect_edges(snn_net* net, const uint32_t* src, const uint32_t* tgt,
     pw = hw.data();
   }
   const int dmax = std::min(net->n_slots, 255);
+  int e_lo = 255, e_hi = 1;
+  std::vector<uint32_t> indeg(net->n, 0);
   for (uint64_t e = 0; e < n; ++e) {
+    e_lo = std::min<int>(e_lo, pd[e]);
+    e_hi = std::max<int>(e_hi, pd[e]);
     REQ(ps[e] < net->n && pt[e] < net->n, SNN_E_ARG,
         "edge %llu: index out of range", (unsigned long long)e);
     REQ(pd[e] >= 1 && pd[e] <= dmax, SNN_E_ARG,
@@ -599,7 +682,10 @@ int snn_connect_edges(snn_net* net, const uint32_t* src, const uint32_t* tgt,
         (int)pd[e], dmax);
     REQ(isfinite(pw[e]), SNN_E_ARG, "edge %llu: weight not finite",
         (unsigned long long)e);
+    ++indeg[pt[e]];
   }
+  const uint32_t k_in_max =
+      indeg.empty() ? 0u : *std::max_element(indeg.begin(), indeg.end());
   uint32_t *d_src = nullptr, *d_tgt = nullptr, *deg = nullptr;
   uint8_t* d_del = nullptr;
   double* d_w = nullptr;
@@ -618,16 +704,19 @@ int snn_connect_edges(snn_net* net, const uint32_t* src, const uint32_t* tgt,
   CK(build_count_edges(d_src, n, deg, s));
   rc = build_store(
       net, deg,
-      [&](const uint64_t* rp, uint32_t* cur, uint64_t* keys) {
-        return build_scatter_edges(d_src, d_tgt, d_del, n, rp, cur, keys, s);
+      [&](const uint64_t* rp, uint32_t* cur, uint64_t* keys, uint32_t tw,
+          int lb) {
+        return build_scatter_edges(d_src, d_tgt, d_del, n, rp, cur, keys, tw,
+                                   lb, s);
       },
-      nullptr, d_w);
+      nullptr, d_w, e_lo, e_hi);
   dfree(d_src);
   dfree(d_tgt);
   dfree(d_del);
   dfree(d_w);
   dfree(deg);
   net->launches += 3;
+  net->k_in_max = k_in_max;
   return rc;
 }
 
@@ -663,6 +752,10 @@ int snn_finalize(snn_net* net) {
   REQ(net->dmax <= net->n_slots, SNN_E_ARG, "max delay %d exceeds n_slots %d",
       net->dmax, net->n_slots);
   net->interval = iv;
+  net->window = net->n_syn ? iv + (net->dmax - net->dmin) : iv;
+  // a neuron fires at most once per refractory period plus one step
+  net->spikes_per_iv =
+      (uint32_t)((iv + net->uc.refr_steps) / (net->uc.refr_steps + 1));
   net->list_cap = (uint64_t)net->n * iv;
   CK(dalloc(&net->list, net->list_cap * sizeof(SpikeEntry)));
   (void)deliver_grid_size(net->fmt);
@@ -694,8 +787,8 @@ int snn_deliver_pending(snn_net* net) {
   if (!net->pending) return SNN_OK;
   int rc;
   if ((rc = set_device(net)) != SNN_OK) return rc;
-  CK(launch_deliver(net->view(), &net->ctl->pair, &net->ctl->done, net->list, 1,
-                    net->stream));
+  CK(launch_deliver_any(net, &net->ctl->pair, &net->ctl->done, net->list, 0,
+                        1));
   net->launches += 1;
   net->del_launches += 1;
   net->pending = false;
@@ -756,8 +849,8 @@ int snn_deliver(snn_net* net, const uint32_t* src, const int32_t* t_emit,
   CK(launch_prepare_external(v, d_src, d_t, n_spikes, net->ext_list,
                              &net->ctl->ext_pair, s));
   if (e0) CK(cudaEventRecord(e0, s));
-  CK(launch_deliver(v, &net->ctl->ext_pair, &net->ctl->ext_done, net->ext_list,
-                    0, s));
+  CK(launch_deliver_any(net, &net->ctl->ext_pair, &net->ctl->ext_done,
+                        net->ext_list, 1, 0));
   if (e1) CK(cudaEventRecord(e1, s));
   net->launches += 2;
   net->del_launches += 1;
@@ -832,7 +925,8 @@ int snn_simulate(snn_net* net, int64_t n_steps) {
       CK(cudaEventRecord(a, s));
       CK(launch_update(v, net->uc, steps, 1, 0, s));
       CK(cudaEventRecord(b, s));
-      CK(launch_deliver(v, &net->ctl->pair, &net->ctl->done, net->list, 1, s));
+      CK(launch_deliver_any(net, &net->ctl->pair, &net->ctl->done, net->list, 0,
+                            1));
       CK(cudaEventRecord(c, s));
       net->launches += 2;
       net->upd_launches += 1;
@@ -1070,6 +1164,10 @@ int snn_get_stats(snn_net* net, snn_stats* out) {
   out->ms_deliver = net->ms_deliver;
   out->bytes_per_record = net->fmt == SNN_W_FP32_12B ? 12 : 8;
   out->store_bytes = net->recs_bytes;
+  out->n_tiles = net->n_tiles;
+  out->tile_width = net->tile_w;
+  out->window = net->window;
+  out->deliver_mode = use_tiled(net) ? SNN_DELIVER_TILED : SNN_DELIVER_ATOMIC;
   return SNN_OK;
 }
 
@@ -1099,7 +1197,7 @@ int snn_destroy(snn_net* net) {
   void* bufs[] = {net->V,        net->I,        net->J,       net->refr,
                   net->rb,       net->counts,   net->ctl,     net->row_ptr,
                   net->recs,     net->list,     net->ext_list, net->ext_src,
-                  net->ext_t,    net->log_src,  net->log_t};
+                  net->ext_t,    net->log_src,  net->log_t,   net->tile_off};
   for (void* b : bufs) dfree(b);
   if (net->own_stream) cudaStreamDestroy(net->stream);
   delete net;

@@ -5,12 +5,20 @@
 //
 // Pipeline: (1) count out-degrees with one generator call per synapse,
 // (2) the host turns them into row offsets, (3) scatter one 64-bit sort key
-// per synapse into its row -- key = delay << 56 | target << 32 | tie, where
-// tie is the draw index k (fixed in-degree rule) or the edge index -- (4) sort
-// every row by key in shared memory (bitonic network; rows longer than the
-// shared-memory capacity are sorted in a global scratch buffer) and pack the
-// records, regenerating the weight from the tie.  Sorting by the full key
-// makes the store independent of the scatter's atomic order.
+// per synapse into its row, (4) sort every row by key in shared memory
+// (bitonic network; rows longer than the shared-memory capacity are sorted
+// in a global scratch buffer), pack the records (regenerating the weight from
+// the key's tie field) and write the row's target-tile index.
+//
+// Sort key, for target tiles of TW neurons (tile = target / TW, position in
+// the tile lo = target - tile TW < 2^B with B = lo_bits):
+//   tile (24 - B bits) | delay (8) | lo (B) | tie (32)
+// so a row is ordered by (target tile, delay, target, tie), where tie is the
+// draw index k (fixed in-degree rule) or the edge index.  Sorting by the full
+// key makes the store independent of the scatter's atomic order.  Within a
+// tile a row is sorted by (delay, target); the tile index tile_off[row][tau]
+// is the offset (relative to the row) of the first record of tile tau, for
+// tau = 0 .. n_tiles (the last entry is the row length).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -20,9 +28,23 @@
 namespace snn {
 namespace {
 
+struct TileGeom {
+  uint32_t tw;  // targets per tile
+  int lb;       // bits of the position within a tile
+};
+
 __device__ __forceinline__ uint64_t make_key(uint32_t d, uint32_t tgt,
-                                             uint32_t tie) {
-  return ((uint64_t)d << 56) | ((uint64_t)tgt << 32) | tie;
+                                             uint32_t tie, TileGeom g) {
+  const uint32_t tile = tgt / g.tw, lo = tgt - tile * g.tw;
+  return ((uint64_t)tile << (40 + g.lb)) | ((uint64_t)(d & 0xFFu) << (32 + g.lb)) |
+         ((uint64_t)lo << 32) | tie;
+}
+__device__ __forceinline__ uint32_t key_target(uint64_t key, TileGeom g) {
+  return (uint32_t)(key >> (40 + g.lb)) * g.tw +
+         ((uint32_t)(key >> 32) & ((1u << g.lb) - 1u));
+}
+__device__ __forceinline__ uint32_t key_delay(uint64_t key, TileGeom g) {
+  return (uint32_t)(key >> (32 + g.lb)) & 0xFFu;
 }
 
 __device__ __forceinline__ uint32_t fixed_source(const BuildFixed& b,
@@ -40,7 +62,7 @@ __global__ void k_count_fixed(BuildFixed b, uint32_t* deg) {
 }
 
 __global__ void k_scatter_fixed(BuildFixed b, const uint64_t* row_ptr,
-                                uint32_t* cursor, uint64_t* keys) {
+                                uint32_t* cursor, uint64_t* keys, TileGeom g) {
   const uint32_t tgt = blockIdx.x;
   const uint32_t kk = b.k_e + b.k_i;
   const uint32_t span = (uint32_t)(b.d_hi - b.d_lo + 1);
@@ -49,7 +71,7 @@ __global__ void k_scatter_fixed(BuildFixed b, const uint64_t* row_ptr,
     uint32_t src = fixed_source(b, k, r.x);
     uint32_t d = (uint32_t)b.d_lo + scale_u32(r.y, span);
     uint32_t pos = atomicAdd(&cursor[src], 1u);
-    keys[row_ptr[src] + pos] = make_key(d, tgt, k);
+    keys[row_ptr[src] + pos] = make_key(d, tgt, k, g);
   }
 }
 
@@ -62,12 +84,12 @@ __global__ void k_count_edges(const uint32_t* src, uint64_t n, uint32_t* deg) {
 __global__ void k_scatter_edges(const uint32_t* src, const uint32_t* tgt,
                                 const uint8_t* delay, uint64_t n,
                                 const uint64_t* row_ptr, uint32_t* cursor,
-                                uint64_t* keys) {
+                                uint64_t* keys, TileGeom g) {
   for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n;
        e += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s = src[e];
     uint32_t pos = atomicAdd(&cursor[s], 1u);
-    keys[row_ptr[s] + pos] = make_key(delay[e], tgt[e], (uint32_t)e);
+    keys[row_ptr[s] + pos] = make_key(delay[e], tgt[e], (uint32_t)e, g);
   }
 }
 
@@ -91,34 +113,71 @@ __device__ double weight_of(const BuildFixed& b, const double* edge_w,
   return x;
 }
 
+// Writes a record; returns |stored weight| (as stored, widened to float).
 template <int FMT>
-__device__ __forceinline__ void store_rec(void* recs, uint64_t idx,
-                                          uint32_t tgt, uint32_t d, double w) {
+__device__ __forceinline__ float store_rec(void* recs, uint64_t idx,
+                                           uint32_t tgt, uint32_t d, double w) {
   if (FMT == SNN_W_FP32_12B) {
     uint32_t* p = reinterpret_cast<uint32_t*>(recs) + idx * 3u;
+    const float wf = __double2float_rn(w);
     p[0] = tgt;
-    p[1] = __float_as_uint(__double2float_rn(w));
+    p[1] = __float_as_uint(wf);
     p[2] = d & 0xFFu;
+    return fabsf(wf);
   } else {
     uint2 r;
+    const uint16_t bits = bf16_bits_rne(w);
     r.x = tgt;
-    r.y = (d & 0xFFu) | ((uint32_t)bf16_bits_rne(w) << 16);
+    r.y = (d & 0xFFu) | ((uint32_t)bits << 16);
     reinterpret_cast<uint2*>(recs)[idx] = r;
+    return fabsf(bf16_to_f32(bits));
   }
 }
 
 template <int FMT, int WMODE>
 __device__ void pack_row(const uint64_t* sorted, uint32_t len, uint32_t row,
                          uint64_t beg, void* recs, const BuildFixed& b,
-                         const double* edge_w) {
+                         const double* edge_w, TileGeom g, uint32_t n_tiles,
+                         uint32_t* tile_off, uint32_t* stats) {
   const bool exc = row < b.n_e;
+  float wmax = 0.f;
+  uint32_t run_max = 0;
   for (uint32_t p = threadIdx.x; p < len; p += blockDim.x) {
     uint64_t key = sorted[p];
-    uint32_t d = (uint32_t)(key >> 56);
-    uint32_t tgt = (uint32_t)(key >> 32) & 0xFFFFFFu;
+    uint32_t d = key_delay(key, g);
+    uint32_t tgt = key_target(key, g);
     uint32_t tie = (uint32_t)key;
-    store_rec<FMT>(recs, beg + p, tgt, d,
-                   weight_of<WMODE>(b, edge_w, exc, tgt, tie));
+    wmax = fmaxf(wmax, store_rec<FMT>(recs, beg + p, tgt, d,
+                                      weight_of<WMODE>(b, edge_w, exc, tgt, tie)));
+    // multiplicity of (target, delay): length of the run of equal keys
+    // (ignoring the tie field) that starts here
+    if (p == 0 || (sorted[p - 1] >> 32) != (key >> 32)) {
+      uint32_t r = 1;
+      while (p + r < len && (sorted[p + r] >> 32) == (key >> 32)) ++r;
+      run_max = max(run_max, r);
+    }
+  }
+  // |w| >= 0 orders like its bit pattern as an unsigned integer
+  const uint32_t wbits = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(wmax));
+  run_max = __reduce_max_sync(0xFFFFFFFFu, run_max);
+  if ((threadIdx.x & 31u) == 0) {
+    if (run_max) atomicMax(&stats[0], run_max);
+    if (wbits) atomicMax(&stats[1], wbits);
+  }
+  // tile index: first position whose tile is >= tau (lower bound)
+  uint32_t* out = tile_off + (uint64_t)row * (n_tiles + 1);
+  for (uint32_t tau = threadIdx.x; tau <= n_tiles; tau += blockDim.x) {
+    if (tau == n_tiles) {  // every key's tile is below n_tiles
+      out[tau] = len;
+      continue;
+    }
+    const uint64_t probe = (uint64_t)tau << (40 + g.lb);
+    uint32_t lo = 0, hi = len;
+    while (lo < hi) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (sorted[mid] < probe) lo = mid + 1; else hi = mid;
+    }
+    out[tau] = lo;
   }
 }
 
@@ -151,18 +210,21 @@ __device__ __forceinline__ uint32_t pow2_ceil(uint32_t x) {
 template <int FMT, int WMODE>
 __global__ void k_sort_pack(uint32_t n, const uint64_t* row_ptr,
                             uint64_t* keys, void* recs, BuildFixed b,
-                            const double* edge_w, uint32_t cap) {
+                            const double* edge_w, uint32_t cap, TileGeom g,
+                            uint32_t n_tiles, uint32_t* tile_off,
+                            uint32_t* stats) {
   extern __shared__ uint64_t sk[];
   for (uint32_t row = blockIdx.x; row < n; row += gridDim.x) {
     const uint64_t beg = row_ptr[row];
     const uint32_t len = (uint32_t)(row_ptr[row + 1] - beg);
-    if (len == 0 || len > cap) continue;     // uniform per block
+    if (len > cap) continue;                 // uniform per block
     const uint32_t P = pow2_ceil(len);
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
       sk[i] = i < len ? keys[beg + i] : ~0ull;
     __syncthreads();
-    bitonic(sk, P);
-    pack_row<FMT, WMODE>(sk, len, row, beg, recs, b, edge_w);
+    if (P > 1) bitonic(sk, P);
+    pack_row<FMT, WMODE>(sk, len, row, beg, recs, b, edge_w, g, n_tiles,
+                         tile_off, stats);
     __syncthreads();
   }
 }
@@ -171,7 +233,9 @@ template <int FMT, int WMODE>
 __global__ void k_sort_long(const uint32_t* rows, const uint64_t* row_ptr,
                             uint64_t* keys, void* recs, BuildFixed b,
                             const double* edge_w, uint64_t* scratch,
-                            const uint64_t* scratch_off) {
+                            const uint64_t* scratch_off, TileGeom g,
+                            uint32_t n_tiles, uint32_t* tile_off,
+                            uint32_t* stats) {
   const uint32_t row = rows[blockIdx.x];
   const uint64_t beg = row_ptr[row];
   const uint32_t len = (uint32_t)(row_ptr[row + 1] - beg);
@@ -181,7 +245,8 @@ __global__ void k_sort_long(const uint32_t* rows, const uint64_t* row_ptr,
     a[i] = i < len ? keys[beg + i] : ~0ull;
   __syncthreads();
   bitonic(a, P);
-  pack_row<FMT, WMODE>(a, len, row, beg, recs, b, edge_w);
+  pack_row<FMT, WMODE>(a, len, row, beg, recs, b, edge_w, g, n_tiles,
+                       tile_off, stats);
 }
 
 template <int FMT>
@@ -240,10 +305,10 @@ cudaError_t sort_pack_t(uint32_t n, const uint64_t* row_ptr, uint64_t* keys,
                         void* recs, const BuildFixed* b, const double* edge_w,
                         uint32_t max_row, const uint32_t* long_rows,
                         uint32_t n_long, uint64_t* long_scratch,
-                        const uint64_t* long_off, cudaStream_t s) {
-  constexpr uint32_t kCap = 16384;   // keys sorted in shared memory (128 KiB)
+                        const uint64_t* long_off, TileGeom g, uint32_t n_tiles,
+                        uint32_t* tile_off, uint32_t* stats, cudaStream_t s) {
   BuildFixed bb = b ? *b : BuildFixed{};
-  uint32_t cap = max_row < kCap ? max_row : kCap;
+  uint32_t cap = max_row < kSortCap ? max_row : kSortCap;
   uint32_t P = 1;
   while (P < cap) P <<= 1;
   size_t smem = (size_t)P * sizeof(uint64_t);
@@ -253,14 +318,15 @@ cudaError_t sort_pack_t(uint32_t n, const uint64_t* row_ptr, uint64_t* keys,
   if (e != cudaSuccess) return e;
   unsigned threads = P >= 1024 ? 1024 : (P >= 128 ? P : 128);
   unsigned blocks = n < (1u << 20) ? n : (1u << 20);
-  if (blocks && max_row > 0)
-    k_sort_pack<FMT, WMODE><<<blocks, threads, smem, s>>>(n, row_ptr, keys, recs,
-                                                          bb, edge_w, kCap);
+  if (blocks)
+    k_sort_pack<FMT, WMODE><<<blocks, threads, smem, s>>>(
+        n, row_ptr, keys, recs, bb, edge_w, kSortCap, g, n_tiles, tile_off,
+        stats);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (n_long)
-    k_sort_long<FMT, WMODE><<<n_long, 1024, 0, s>>>(long_rows, row_ptr, keys,
-                                                     recs, bb, edge_w,
-                                                     long_scratch, long_off);
+    k_sort_long<FMT, WMODE><<<n_long, 1024, 0, s>>>(
+        long_rows, row_ptr, keys, recs, bb, edge_w, long_scratch, long_off, g,
+        n_tiles, tile_off, stats);
   return cudaGetLastError();
 }
 
@@ -276,10 +342,11 @@ cudaError_t build_count_fixed(const BuildFixed& b, uint32_t* deg,
 
 cudaError_t build_scatter_fixed(const BuildFixed& b, const uint64_t* row_ptr,
                                 uint32_t* cursor, uint64_t* keys,
-                                cudaStream_t s) {
+                                uint32_t tile_w, int lo_bits, cudaStream_t s) {
   uint32_t n = b.n_e + b.n_i;
   if (n == 0 || b.k_e + b.k_i == 0) return cudaSuccess;
-  k_scatter_fixed<<<n, 256, 0, s>>>(b, row_ptr, cursor, keys);
+  k_scatter_fixed<<<n, 256, 0, s>>>(b, row_ptr, cursor, keys,
+                                    TileGeom{tile_w, lo_bits});
   return cudaGetLastError();
 }
 
@@ -293,10 +360,11 @@ cudaError_t build_count_edges(const uint32_t* src, uint64_t n, uint32_t* deg,
 cudaError_t build_scatter_edges(const uint32_t* src, const uint32_t* tgt,
                                 const uint8_t* delay, uint64_t n,
                                 const uint64_t* row_ptr, uint32_t* cursor,
-                                uint64_t* keys, cudaStream_t s) {
+                                uint64_t* keys, uint32_t tile_w, int lo_bits,
+                                cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_scatter_edges<<<grid_for(n, 256), 256, 0, s>>>(src, tgt, delay, n, row_ptr,
-                                                   cursor, keys);
+  k_scatter_edges<<<grid_for(n, 256), 256, 0, s>>>(
+      src, tgt, delay, n, row_ptr, cursor, keys, TileGeom{tile_w, lo_bits});
   return cudaGetLastError();
 }
 
@@ -305,23 +373,19 @@ cudaError_t build_sort_pack(int fmt, uint32_t n, const uint64_t* row_ptr,
                             const double* edge_w, uint32_t max_row,
                             const uint32_t* long_rows, uint32_t n_long,
                             uint64_t* long_scratch,
-                            const uint64_t* long_scratch_off,
-                            cudaStream_t s) {
+                            const uint64_t* long_scratch_off, uint32_t tile_w,
+                            int lo_bits, uint32_t n_tiles, uint32_t* tile_off,
+                            uint32_t* stats, cudaStream_t s) {
+  const TileGeom g{tile_w, lo_bits};
+#define SNN_SORT_ARGS                                                       \
+  n, row_ptr, keys, recs, b, edge_w, max_row, long_rows, n_long,           \
+      long_scratch, long_scratch_off, g, n_tiles, tile_off, stats, s
   if (fmt == SNN_W_FP32_12B)
-    return edge_w ? sort_pack_t<SNN_W_FP32_12B, 1>(
-                        n, row_ptr, keys, recs, b, edge_w, max_row, long_rows,
-                        n_long, long_scratch, long_scratch_off, s)
-                  : sort_pack_t<SNN_W_FP32_12B, 0>(
-                        n, row_ptr, keys, recs, b, edge_w, max_row, long_rows,
-                        n_long, long_scratch, long_scratch_off, s);
-  return edge_w ? sort_pack_t<SNN_W_BF16_8B, 1>(n, row_ptr, keys, recs, b,
-                                                 edge_w, max_row, long_rows,
-                                                 n_long, long_scratch,
-                                                 long_scratch_off, s)
-                : sort_pack_t<SNN_W_BF16_8B, 0>(n, row_ptr, keys, recs, b,
-                                                 edge_w, max_row, long_rows,
-                                                 n_long, long_scratch,
-                                                 long_scratch_off, s);
+    return edge_w ? sort_pack_t<SNN_W_FP32_12B, 1>(SNN_SORT_ARGS)
+                  : sort_pack_t<SNN_W_FP32_12B, 0>(SNN_SORT_ARGS);
+  return edge_w ? sort_pack_t<SNN_W_BF16_8B, 1>(SNN_SORT_ARGS)
+                : sort_pack_t<SNN_W_BF16_8B, 0>(SNN_SORT_ARGS);
+#undef SNN_SORT_ARGS
 }
 
 cudaError_t unpack_store(int fmt, const void* recs, uint64_t n_syn,

@@ -76,6 +76,7 @@ struct Ctl {
   int iv_steps;                 // steps of the pending interval
   unsigned int ext_done;        // CTAs finished delivering an external list
   unsigned long long ext_pair;  // (spikes << 32) | chunks of an external list
+  int ext_tmin, ext_tmax;       // emission-step range of an external list
 };
 
 // ---------------------------------------------------------------------------
@@ -176,6 +177,16 @@ struct NetView {
   uint32_t* counts;         // [n_slots][pitch] or null
   const uint64_t* row_ptr;  // [n+1]
   const void* recs;
+  const uint32_t* tile_off; // [n][n_tiles + 1] row-relative tile starts
+  uint32_t tile_w;          // targets per tile (tile tau: [tau tile_w, ...))
+  uint32_t n_tiles;
+  int d_min, d_max;         // delay range of the store
+  int window;               // ring steps one interval's spikes can reach
+  // bounds for the exact fixed-point accumulation of k_deliver_tiled
+  uint32_t mult_max;        // most synapses sharing (source, target, delay)
+  uint32_t k_in_max;        // largest in-degree
+  uint32_t spikes_per_iv;   // most spikes one neuron emits per interval
+  float max_abs_w;          // largest |stored weight|
   SpikeEntry* list;         // interval list, capacity list_cap
   uint64_t list_cap;
   uint32_t* log_src;        // spike log, capacity log_cap
@@ -202,6 +213,14 @@ cudaError_t launch_prepare_external(const NetView& v, const uint32_t* src,
                                     SpikeEntry* list,
                                     unsigned long long* pair, cudaStream_t s);
 int deliver_grid_size(int fmt);
+// Tile-binned delivery (see k_deliver_tiled).  from_list_range: the window
+// starts at the external list's minimum emission step (ctl->ext_tmin) rather
+// than at the interval start ctl->t_now.
+cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
+                                 unsigned int* done, const SpikeEntry* list,
+                                 int from_list_range, int advance_time,
+                                 cudaStream_t s);
+size_t tiled_smem_bytes(const NetView& v);
 cudaError_t launch_deliver_noalloc(const NetView& v, const uint32_t* src,
                                    const int32_t* t, uint32_t n,
                                    cudaStream_t s);
@@ -218,22 +237,29 @@ cudaError_t build_count_fixed(const BuildFixed& b, uint32_t* deg,
                               cudaStream_t s);
 cudaError_t build_scatter_fixed(const BuildFixed& b, const uint64_t* row_ptr,
                                 uint32_t* cursor, uint64_t* keys,
-                                cudaStream_t s);
+                                uint32_t tile_w, int lo_bits, cudaStream_t s);
 cudaError_t build_count_edges(const uint32_t* src, uint64_t n, uint32_t* deg,
                               cudaStream_t s);
 cudaError_t build_scatter_edges(const uint32_t* src, const uint32_t* tgt,
                                 const uint8_t* delay, uint64_t n,
                                 const uint64_t* row_ptr, uint32_t* cursor,
-                                uint64_t* keys, cudaStream_t s);
-// Sort every row's keys by value and pack records.  weights: either the
+                                uint64_t* keys, uint32_t tile_w, int lo_bits,
+                                cudaStream_t s);
+// Sort every row's keys by value, pack records and write the tile index
+// (n rows of n_tiles + 1 entries).  weights: either the
 // fixed-rule parameters (edge_w == null) or per-edge FP64 weights.
+constexpr uint32_t kSortCap = 16384;  // keys sorted in shared memory (128 KiB)
+// stats (device, 2 words, zeroed by the caller): [0] = largest number of
+// synapses sharing (source, target, delay); [1] = bits of the largest
+// |stored weight| (a non-negative float, ordered as an unsigned integer).
 cudaError_t build_sort_pack(int fmt, uint32_t n, const uint64_t* row_ptr,
                             uint64_t* keys, void* recs, const BuildFixed* b,
                             const double* edge_w, uint32_t max_row,
                             const uint32_t* long_rows, uint32_t n_long,
                             uint64_t* long_scratch,
-                            const uint64_t* long_scratch_off,
-                            cudaStream_t s);
+                            const uint64_t* long_scratch_off, uint32_t tile_w,
+                            int lo_bits, uint32_t n_tiles, uint32_t* tile_off,
+                            uint32_t* stats, cudaStream_t s);
 cudaError_t unpack_store(int fmt, const void* recs, uint64_t n_syn,
                          uint32_t* tgt, uint8_t* delay, float* w,
                          cudaStream_t s);

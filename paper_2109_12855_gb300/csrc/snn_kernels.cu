@@ -62,10 +62,87 @@ __global__ void k_init_state(NetView v, float v_reset, float v_span,
 
 // ---------------------------------------------------------------------------
 // Fused update.
+//
+// One thread per neuron integrates its state for the interval's steps.  The
+// ring-buffer values of a step are loaded in groups of eight independent
+// loads ahead of use (one memory round trip per eight steps instead of one
+// per step).  Spikes are kept as a per-thread bit mask of step indices and
+// compacted once per block for up to 32 steps: a block scan of the per-thread
+// counts, then one set of global atomics per block reserves the block's list
+// entries and chunk ranges.
 // ---------------------------------------------------------------------------
+constexpr int kPrefetch = 8;
+
+// Exclusive block scan of two 32-bit counts and a block sum of a 64-bit one;
+// returns the block totals through *tot_* (all threads).
+__device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b,
+                                            unsigned long long c,
+                                            uint32_t* ex_a, uint32_t* ex_b,
+                                            uint32_t* tot_a, uint32_t* tot_b,
+                                            unsigned long long* tot_c) {
+  __shared__ uint32_t sa[32], sb[32];
+  __shared__ unsigned long long sc[32];
+  __shared__ uint32_t s_ta, s_tb;
+  __shared__ unsigned long long s_tc;
+  const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  const unsigned nw = (blockDim.x + 31) >> 5;
+  uint32_t ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t ya = __shfl_up_sync(kFull, ia, o);
+    uint32_t yb = __shfl_up_sync(kFull, ib, o);
+    if (lane >= (unsigned)o) {
+      ia += ya;
+      ib += yb;
+    }
+  }
+  unsigned long long rc = c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rc += __shfl_xor_sync(kFull, rc, o);
+  if (lane == 31) {
+    sa[wid] = ia;
+    sb[wid] = ib;
+  }
+  if (lane == 0) sc[wid] = rc;
+  __syncthreads();
+  if (wid == 0) {
+    const uint32_t xa = lane < nw ? sa[lane] : 0u;
+    const uint32_t xb = lane < nw ? sb[lane] : 0u;
+    unsigned long long xc = lane < nw ? sc[lane] : 0ull;
+    uint32_t pa = xa, pb = xb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t ya = __shfl_up_sync(kFull, pa, o);
+      uint32_t yb = __shfl_up_sync(kFull, pb, o);
+      if (lane >= (unsigned)o) {
+        pa += ya;
+        pb += yb;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) xc += __shfl_xor_sync(kFull, xc, o);
+    __syncwarp();
+    sa[lane] = pa - xa;  // exclusive prefix over warps
+    sb[lane] = pb - xb;
+    if (lane == 31) {
+      s_ta = pa;
+      s_tb = pb;
+    }
+    if (lane == 0) s_tc = xc;
+  }
+  __syncthreads();
+  *ex_a = sa[wid] + ia - a;
+  *ex_b = sb[wid] + ib - b;
+  *tot_a = s_ta;
+  *tot_b = s_tb;
+  *tot_c = s_tc;
+  __syncthreads();  // the shared arrays are reused by the next call
+}
+
 __global__ void __launch_bounds__(kUpdThreads)
 k_update(NetView v, UpdConst c, int n_steps, int from_ctl, long long t0_arg) {
   __shared__ uint32_t s_thr[kMaxPoisson];
+  __shared__ unsigned long long s_base[2];
   for (int k = threadIdx.x; k < c.n_thr; k += blockDim.x) s_thr[k] = c.thr[k];
   const long long t0 = from_ctl ? v.ctl->t_now : t0_arg;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -76,7 +153,6 @@ k_update(NetView v, UpdConst c, int n_steps, int from_ctl, long long t0_arg) {
 
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = i < v.n;
-  const unsigned lane = threadIdx.x & 31u;
   float V = 0.f, I = 0.f, J = 0.f;
   int refr = 0;
   uint32_t nch = 0;
@@ -90,86 +166,101 @@ k_update(NetView v, UpdConst c, int n_steps, int from_ctl, long long t0_arg) {
     nch = row_chunks(beg, end, v.chunk);
     deg = end - beg;
   }
-  // warp-constant prefix data of the chunk reservation, recomputed on use
   U4 rnd{0, 0, 0, 0};
   long long rnd_block = -1;
 
-  for (int s = 0; s < n_steps; ++s) {
-    const long long t = t0 + s;
-    bool spike = false;
-    if (live) {
-      // (1) membrane, unless refractory
-      if (refr == 0) V = c.p31 * J + c.p32 * I + c.p33 * V;
-      else refr -= 1;
-      // (2) synaptic current and its derivative
-      I = c.p21 * J + c.p22 * I;
-      J = c.p11 * J;
-      // (3) ring-buffer slot of this step (read and clear) and drive
-      float* cell = v.rb + (size_t)((uint32_t)t & v.slot_mask) * v.pitch + i;
-      float in = *cell;
-      *cell = 0.0f;
-      if (c.n_thr > 0) {
-        long long blk = t >> 2;
-        if (blk != rnd_block) {
-          rnd = draw(c.seed, i, (uint64_t)blk, 2u);
-          rnd_block = blk;
-        }
-        uint32_t w = (t & 3) == 0 ? rnd.x : (t & 3) == 1 ? rnd.y
-                   : (t & 3) == 2 ? rnd.z : rnd.w;
-        int k = 0;
-        while (k < c.n_thr - 1 && w >= s_thr[k]) ++k;
-        in += c.w_ext * (float)k;
+  for (int s0 = 0; s0 < n_steps; s0 += 32) {
+    const int ns = n_steps - s0 < 32 ? n_steps - s0 : 32;
+    uint32_t mask = 0;
+    for (int sb = 0; sb < ns; sb += kPrefetch) {
+      // ring-buffer values and drive counts of up to eight steps, computed
+      // before the (sequential) integration so they do not lengthen it
+      float buf[kPrefetch];
+#pragma unroll
+      for (int q = 0; q < kPrefetch; ++q) {
+        buf[q] = 0.f;
+        if (live && sb + q < ns)
+          buf[q] = v.rb[(size_t)((uint32_t)(t0 + s0 + sb + q) & v.slot_mask) *
+                            v.pitch + i];
       }
-      J += c.psc * in;
-      // (4) threshold
-      if (V >= c.v_th) {
-        V = c.v_reset;
-        refr = c.refr_steps;
-        spike = true;
+      if (c.n_thr > 0 && live) {
+#pragma unroll
+        for (int q = 0; q < kPrefetch; ++q) {
+          if (sb + q >= ns) continue;
+          const long long t = t0 + s0 + sb + q;
+          const long long blk = t >> 2;
+          if (blk != rnd_block) {
+            rnd = draw(c.seed, i, (uint64_t)blk, 2u);
+            rnd_block = blk;
+          }
+          const uint32_t w = (t & 3) == 0 ? rnd.x : (t & 3) == 1 ? rnd.y
+                           : (t & 3) == 2 ? rnd.z : rnd.w;
+          int k = 0;
+          while (k < c.n_thr - 1 && w >= s_thr[k]) ++k;
+          buf[q] += c.w_ext * (float)k;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kPrefetch; ++q) {
+        if (!live || sb + q >= ns) continue;
+        const long long t = t0 + s0 + sb + q;
+        // (1) membrane, unless refractory
+        if (refr == 0) V = c.p31 * J + c.p32 * I + c.p33 * V;
+        else refr -= 1;
+        // (2) synaptic current and its derivative
+        I = c.p21 * J + c.p22 * I;
+        J = c.p11 * J;
+        // (3) this step's ring-buffer input (read above; the slot is
+        // cleared here) plus drive
+        v.rb[(size_t)((uint32_t)t & v.slot_mask) * v.pitch + i] = 0.0f;
+        J += c.psc * buf[q];
+        // (4) threshold
+        if (V >= c.v_th) {
+          V = c.v_reset;
+          refr = c.refr_steps;
+          mask |= 1u << (sb + q);
+        }
       }
     }
-    const unsigned m = __ballot_sync(kFull, spike);
-    if (m) {
-      // warp-inclusive scan of chunk counts of the spiking lanes
-      uint32_t my = spike ? nch : 0u;
-      uint32_t incl = my;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= (unsigned)o) incl += y;
-      }
-      const uint32_t tot = __shfl_sync(kFull, incl, 31);
-      unsigned long long dsum = spike ? deg : 0ull;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
-      const int leader = __ffs(m) - 1;
-      const unsigned cnt = __popc(m);
-      unsigned long long old = 0, logb = 0;
-      if ((int)lane == leader) {
-        old = atomicAdd(&v.ctl->pair, ((unsigned long long)cnt << 32) | tot);
-        atomicAdd(&v.ctl->events, dsum);
-        atomicAdd(&v.ctl->spikes, (unsigned long long)cnt);
-        if (v.log_cap) logb = atomicAdd(&v.ctl->log_count, (unsigned long long)cnt);
-        if ((uint32_t)old + (unsigned long long)tot > 0xFFFFFFFFull)
+    // block compaction of this chunk's spikes
+    const uint32_t cnt = __popc(mask);
+    if (__syncthreads_or(cnt != 0)) {
+      uint32_t ex_cnt, ex_ch, tot_cnt, tot_ch;
+      unsigned long long tot_deg;
+      block_scan2(cnt, cnt * nch, (unsigned long long)cnt * deg, &ex_cnt,
+                  &ex_ch, &tot_cnt, &tot_ch, &tot_deg);
+      if (threadIdx.x == 0) {
+        unsigned long long old =
+            atomicAdd(&v.ctl->pair, ((unsigned long long)tot_cnt << 32) | tot_ch);
+        if ((uint32_t)old + (unsigned long long)tot_ch > 0xFFFFFFFFull)
           atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_CHUNKS);
+        atomicAdd(&v.ctl->events, tot_deg);
+        atomicAdd(&v.ctl->spikes, (unsigned long long)tot_cnt);
+        s_base[0] = old;
+        s_base[1] = v.log_cap
+                        ? atomicAdd(&v.ctl->log_count, (unsigned long long)tot_cnt)
+                        : 0ull;
       }
-      old = __shfl_sync(kFull, old, leader);
-      logb = __shfl_sync(kFull, logb, leader);
-      if (spike) {
-        const unsigned rank = __popc(m & ((1u << lane) - 1u));
-        const unsigned long long idx = (old >> 32) + rank;
+      __syncthreads();
+      const unsigned long long old = s_base[0], logb = s_base[1];
+      uint32_t m = mask, k = 0;
+      while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1u;
+        const long long t = t0 + s0 + b;
+        const unsigned long long idx = (old >> 32) + ex_cnt + k;
         if (idx < v.list_cap) {
           SpikeEntry e;
           e.src = i;
           e.t = (int32_t)t;
-          e.choff = (uint32_t)old + incl - my;
+          e.choff = (uint32_t)old + ex_ch + k * nch;
           e.pad = 0;
           v.list[idx] = e;
         } else {
           atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_SPIKE_LIST);
         }
         if (v.log_cap) {
-          const unsigned long long li = logb + rank;
+          const unsigned long long li = logb + ex_cnt + k;
           if (li < v.log_cap) {
             v.log_src[li] = i;
             v.log_t[li] = (int32_t)t;
@@ -177,7 +268,9 @@ k_update(NetView v, UpdConst c, int n_steps, int from_ctl, long long t0_arg) {
             atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_SPIKE_LOG);
           }
         }
+        ++k;
       }
+      __syncthreads();  // s_base is rewritten by the next chunk
     }
   }
   if (live) {
@@ -338,6 +431,288 @@ k_deliver(NetView v, unsigned long long* pair_p, unsigned int* done_p,
 }
 
 // ---------------------------------------------------------------------------
+// Tile-binned delivery.
+//
+// CTA tau owns the targets [tau TW, (tau+1) TW) and accumulates, in shared
+// memory, every event of the list aimed at them for the ring steps
+// base .. base + window - 1 that one interval can reach (base = interval
+// start + min delay).  Rows are sorted by target tile, so the records of
+// spike j for tile tau are one contiguous run, located by the row's tile
+// index.  (A) the CTA describes a batch of runs in shared memory; (B) each
+// of its 32 warps takes U runs per pass and loads up to PER records per lane
+// of each before adding any (independent loads in flight).  (Staging the
+// runs into shared memory with bulk copies was measured slower: the runs are
+// short, about 74 records, so per-run synchronisation dominates.)
+//
+// Accumulation is exact fixed point: a weight w becomes x = w 2^(q-s),
+// split into hi = floor(x) and lo = round((x - hi) 2^s) in [0, 2^s]; hi and
+// lo are summed in two int32 arrays with shared-memory integer atomics, so
+// the sum is order-independent and the cell value is (H 2^s + L) 2^-q.
+// The scales come from bounds on one launch: a cell receives at most
+// E = min(spikes x max synapse multiplicity, max in-degree x spikes per
+// neuron per interval) events of magnitude <= max|w|; s makes E 2^s < 2^31
+// and q makes E max|w| 2^(q-s) + E < 2^31, so neither sum can overflow, and
+// the rounding error (<= 2^-(q+1) per event) is below that of FP32
+// accumulation.  If no such scales exist the CTA falls back to FP32
+// shared-memory atomics.  The CTA then adds its cells into the ring buffer
+// with plain coalesced read-modify-writes: no other CTA touches them.
+// An external list whose emission steps span more than the window is
+// delivered by the same CTAs with global atomics instead.
+// ---------------------------------------------------------------------------
+constexpr int kTileThreads = 1024;
+constexpr int kTileWarps = kTileThreads / 32;
+constexpr int kDescBatch = 1024;   // spike runs described per pass
+
+template <int FMT> struct Rec1;
+template <> struct Rec1<SNN_W_FP32_12B> { uint32_t a, b, c; };
+template <> struct Rec1<SNN_W_BF16_8B> { uint32_t a, b; };
+
+template <int FMT>
+__device__ __forceinline__ Rec1<FMT> load_rec(const void* recs, uint64_t r);
+template <>
+__device__ __forceinline__ Rec1<SNN_W_FP32_12B> load_rec<SNN_W_FP32_12B>(
+    const void* recs, uint64_t r) {
+  const uint32_t* p = reinterpret_cast<const uint32_t*>(recs) + r * 3u;
+  Rec1<SNN_W_FP32_12B> x;
+  x.a = __ldcs(p);
+  x.b = __ldcs(p + 1);
+  x.c = __ldcs(p + 2);
+  return x;
+}
+template <>
+__device__ __forceinline__ Rec1<SNN_W_BF16_8B> load_rec<SNN_W_BF16_8B>(
+    const void* recs, uint64_t r) {
+  const uint2 u = __ldcs(reinterpret_cast<const uint2*>(recs) + r);
+  Rec1<SNN_W_BF16_8B> x;
+  x.a = u.x;
+  x.b = u.y;
+  return x;
+}
+__device__ __forceinline__ void rec_fields(const Rec1<SNN_W_FP32_12B>& x,
+                                           uint32_t& tgt, uint32_t& d,
+                                           float& w) {
+  tgt = x.a;
+  w = __uint_as_float(x.b);
+  d = x.c & 0xFFu;
+}
+__device__ __forceinline__ void rec_fields(const Rec1<SNN_W_BF16_8B>& x,
+                                           uint32_t& tgt, uint32_t& d,
+                                           float& w) {
+  tgt = x.a;
+  d = x.b & 0xFFu;
+  w = __uint_as_float(x.b & 0xFFFF0000u);
+}
+
+// Per-spike run of records for this CTA's tile.
+struct SegDesc {
+  uint64_t beg;
+  uint32_t len;
+  int32_t t;
+};
+
+// Fixed-point scales of one launch (see above); fixed = 0: use FP32.
+struct FixScale {
+  int fixed;
+  int sh;          // s
+  float scale_hs;  // 2^(q - s)
+  float scale_s;   // 2^s
+  double inv_q;    // 2^-q
+};
+
+__device__ FixScale fix_scale(const NetView& v, uint64_t n_sp,
+                              bool per_interval) {
+  FixScale f{0, 0, 1.f, 1.f, 1.0};
+  uint64_t e = n_sp * (uint64_t)(v.mult_max ? v.mult_max : 1u);
+  if (per_interval) {
+    const uint64_t e2 = (uint64_t)v.k_in_max * (v.spikes_per_iv ? v.spikes_per_iv : 1u);
+    if (e2 < e) e = e2;
+  }
+  if (e == 0 || e >= (1ull << 30) || !(v.max_abs_w > 0.f)) return f;
+  const int lg = 63 - __clzll((long long)e);  // 2^lg <= e < 2^(lg+1)
+  const int sh = 30 - lg;                     // e 2^sh < 2^31
+  const double lim = (2147483647.0 - (double)e) / ((double)e * v.max_abs_w);
+  if (!(lim >= 1.0)) return f;
+  int qs = (int)floor(log2(lim));             // 2^(q - s) <= lim
+  // keep max|w| 2^q below 2^62 and the scales inside float's range
+  const int wexp = (int)ceil(log2((double)v.max_abs_w));
+  int q = sh + qs;
+  if (q > 62 - wexp) q = 62 - wexp;
+  if (q - sh > 100) q = sh + 100;
+  if (q - sh < -100) return f;
+  f.fixed = 1;
+  f.sh = sh;
+  f.scale_hs = (float)ldexp(1.0, q - sh);
+  f.scale_s = (float)ldexp(1.0, sh);
+  f.inv_q = ldexp(1.0, -q);
+  return f;
+}
+
+template <int FMT, bool COUNT>
+__global__ void __launch_bounds__(kTileThreads, 1)
+k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
+                const SpikeEntry* __restrict__ list, int from_list_range,
+                int advance_time) {
+  // U runs per warp pass, PER records per lane of each loaded before use
+  constexpr int U = FMT == SNN_W_FP32_12B ? 2 : 4;
+  constexpr int PER = 3;
+  extern __shared__ __align__(16) int acc_mem[];
+  __shared__ SegDesc s_desc[kDescBatch];
+  __shared__ unsigned long long s_pair;
+  __shared__ long long s_base;
+  __shared__ int s_inwin;
+  __shared__ FixScale s_fx;
+  const uint32_t TW = v.tile_w;
+  const uint32_t W = (uint32_t)v.window;
+  const uint32_t cells = W * TW;
+  const uint32_t tile = blockIdx.x;
+  const uint32_t tgt_lo = tile * TW;
+  const unsigned lane = threadIdx.x & 31u;
+  const uint32_t warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    const unsigned long long pr =
+        *reinterpret_cast<volatile unsigned long long*>(pair_p);
+    s_pair = pr;
+    if (from_list_range) {
+      const long long tmin = v.ctl->ext_tmin, tmax = v.ctl->ext_tmax;
+      s_base = tmin + v.d_min;
+      s_inwin = (tmax - tmin) + (v.d_max - v.d_min) + 1 <= (long long)W;
+    } else {
+      s_base = v.ctl->t_now + v.d_min;
+      s_inwin = 1;
+    }
+    s_fx = fix_scale(v, pr >> 32, !from_list_range);
+  }
+  __syncthreads();
+  const FixScale fx = s_fx;
+  int* accH = acc_mem;                                // fixed: hi parts
+  int* accL = acc_mem + cells;                        // fixed: lo parts
+  float* accF = reinterpret_cast<float*>(acc_mem);    // FP32 fallback
+  for (uint32_t x = threadIdx.x; x < 2 * cells; x += blockDim.x) acc_mem[x] = 0;
+  __syncthreads();
+  const uint32_t n_sp = (uint32_t)(s_pair >> 32);
+  const long long base = s_base;
+  const bool inwin = s_inwin != 0;
+  const uint32_t row_stride = v.n_tiles + 1;
+
+  // one event: cell = d TW + tgt + off, off = (t - base) TW - tgt_lo per run
+  auto add = [&](uint32_t tgt, int32_t t, int32_t off, uint32_t d, float w) {
+    if (inwin) {
+      const uint32_t cell = d * TW + tgt + (uint32_t)off;
+      if (fx.fixed) {
+        const float xw = w * fx.scale_hs;
+        const float hf = floorf(xw);
+        atomicAdd(&accH[cell], (int)hf);
+        atomicAdd(&accL[cell], __float2int_rn((xw - hf) * fx.scale_s));
+      } else {
+        atomicAdd(&accF[cell], w);
+      }
+    } else {
+      const uint32_t step = (uint32_t)t + d;
+      red_add_f32(v.rb + (size_t)(step & v.slot_mask) * v.pitch + tgt, w);
+    }
+    if (COUNT)
+      atomicAdd(v.counts + (size_t)(((uint32_t)t + d) & v.slot_mask) * v.pitch + tgt,
+                1u);
+  };
+
+  auto load_pass = [&](Rec1<FMT> (&r)[U][PER], uint32_t k0, uint32_t nb) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool ok = k0 + u < nb;
+      const uint64_t beg = ok ? s_desc[k0 + u].beg : 0ull;
+      const uint32_t len = ok ? s_desc[k0 + u].len : 0u;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const uint32_t idx = lane + 32u * q;
+        if (idx < len) r[u][q] = load_rec<FMT>(v.recs, beg + idx);
+      }
+    }
+  };
+  auto add_pass = [&](const Rec1<FMT> (&r)[U][PER], uint32_t k0, uint32_t nb) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0 + u >= nb) break;
+      const SegDesc sd = s_desc[k0 + u];
+      const int32_t off =
+          (int32_t)(((long long)sd.t - base) * (long long)TW) - (int32_t)tgt_lo;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const uint32_t idx = lane + 32u * q;
+        if (idx < sd.len) {
+          uint32_t tgt, d;
+          float w;
+          rec_fields(r[u][q], tgt, d, w);
+          add(tgt, sd.t, off, d, w);
+        }
+      }
+      for (uint32_t idx = 32u * PER + lane; idx < sd.len; idx += 32u) {
+        uint32_t tgt, d;
+        float w;
+        rec_fields(load_rec<FMT>(v.recs, sd.beg + idx), tgt, d, w);
+        add(tgt, sd.t, off, d, w);
+      }
+    }
+  };
+
+  for (uint32_t j0 = 0; j0 < n_sp; j0 += kDescBatch) {
+    const uint32_t nb = n_sp - j0 < (uint32_t)kDescBatch ? n_sp - j0
+                                                         : (uint32_t)kDescBatch;
+    // (A) describe this batch's runs: independent loads across threads
+    for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) {
+      const SpikeEntry e = list[j0 + k];
+      SegDesc sd{0, 0u, e.t};
+      if (e.src < v.n) {
+        const uint32_t* to = v.tile_off + (uint64_t)e.src * row_stride + tile;
+        const uint32_t a = to[0], b = to[1];
+        sd.beg = v.row_ptr[e.src] + a;
+        sd.len = b - a;
+      }
+      s_desc[k] = sd;
+    }
+    __syncthreads();
+    // (B) each warp takes U runs per pass: all loads first, then the adds
+    for (uint32_t k = warp * U; k < nb; k += kTileWarps * U) {
+      Rec1<FMT> r[U][PER];
+      load_pass(r, k, nb);
+      add_pass(r, k, nb);
+    }
+    __syncthreads();  // s_desc is rewritten by the next batch
+  }
+  if (inwin) {
+    for (uint32_t sl = 0; sl < W; ++sl) {
+      const uint32_t slot = (uint32_t)(base + sl) & v.slot_mask;
+      float* row = v.rb + (size_t)slot * v.pitch + tgt_lo;
+      for (uint32_t x = threadIdx.x; x < TW; x += blockDim.x) {
+        if (tgt_lo + x >= v.n) continue;
+        const uint32_t c = sl * TW + x;
+        float a;
+        if (fx.fixed) {
+          const int H = accH[c], L = accL[c];
+          if ((H | L) == 0) continue;
+          const long long T = ((long long)H << fx.sh) + (long long)L;
+          a = (float)((double)T * fx.inv_q);
+        } else {
+          a = accF[c];
+          if (a == 0.f) continue;
+        }
+        row[x] += a;
+      }
+    }
+  }
+  // The last CTA to finish clears the list counters and advances the clock.
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned prev = atomicAdd(done_p, 1u);
+    if (prev == gridDim.x - 1) {
+      *pair_p = 0ull;
+      *done_p = 0u;
+      if (advance_time) v.ctl->t_now += v.ctl->iv_steps;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Caller's spike list -> entries with chunk prefix sums (one CTA).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
@@ -346,9 +721,15 @@ k_prepare_external(NetView v, const uint32_t* __restrict__ src,
                    SpikeEntry* out, unsigned long long* pair_p) {
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_carry;
+  __shared__ int s_tmin, s_tmax;
   const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_carry = 0;
+  if (threadIdx.x == 0) {
+    s_carry = 0;
+    s_tmin = 0x7FFFFFFF;
+    s_tmax = -0x7FFFFFFF - 1;
+  }
   unsigned long long deg_sum = 0;
+  int tmin = 0x7FFFFFFF, tmax = -0x7FFFFFFF - 1;
   bool bad = false;
   __syncthreads();
   for (uint32_t base = 0; base < n; base += blockDim.x) {
@@ -358,6 +739,8 @@ k_prepare_external(NetView v, const uint32_t* __restrict__ src,
     if (i < n) {
       s = src[i];
       t = tt[i];
+      tmin = min(tmin, t);
+      tmax = max(tmax, t);
       if (s < v.n) {
         uint64_t b = v.row_ptr[s], e = v.row_ptr[s + 1];
         nch = row_chunks(b, e, v.chunk);
@@ -402,10 +785,15 @@ k_prepare_external(NetView v, const uint32_t* __restrict__ src,
   // block reduction of deg_sum
   for (int o = 16; o > 0; o >>= 1) deg_sum += __shfl_xor_sync(kFull, deg_sum, o);
   if (lane == 0 && deg_sum) atomicAdd(&v.ctl->events, deg_sum);
+  atomicMin(&s_tmin, tmin);
+  atomicMax(&s_tmax, tmax);
   if (__syncthreads_or(bad) && threadIdx.x == 0)
     atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_BAD_SOURCE);
-  if (threadIdx.x == 0)
+  if (threadIdx.x == 0) {
     *pair_p = ((unsigned long long)n << 32) | (unsigned long long)s_carry;
+    v.ctl->ext_tmin = s_tmin;
+    v.ctl->ext_tmax = s_tmax;
+  }
 }
 
 int g_deliver_blocks[2] = {0, 0};
@@ -469,6 +857,44 @@ cudaError_t launch_deliver(const NetView& v, unsigned long long* pair,
           <<<blocks, kDelThreads, 0, s>>>(v, pair, done, list, advance_time);
   }
   return cudaGetLastError();
+}
+
+size_t tiled_smem_bytes(const NetView& v) {
+  return 2 * (size_t)v.window * v.tile_w * sizeof(int);
+}
+
+template <int FMT, bool COUNT>
+cudaError_t launch_tiled_t(const NetView& v, unsigned long long* pair,
+                           unsigned int* done, const SpikeEntry* list,
+                           int from_list_range, int advance_time,
+                           cudaStream_t s) {
+  const size_t smem = tiled_smem_bytes(v);
+  static int configured = 0;   // per-process attribute, set once
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(
+        k_deliver_tiled<FMT, COUNT>,
+        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = 1;
+  }
+  k_deliver_tiled<FMT, COUNT><<<v.n_tiles, kTileThreads, smem, s>>>(
+      v, pair, done, list, from_list_range, advance_time);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
+                                 unsigned int* done, const SpikeEntry* list,
+                                 int from_list_range, int advance_time,
+                                 cudaStream_t s) {
+  if (v.fmt == SNN_W_FP32_12B)
+    return v.counts ? launch_tiled_t<SNN_W_FP32_12B, true>(
+                          v, pair, done, list, from_list_range, advance_time, s)
+                    : launch_tiled_t<SNN_W_FP32_12B, false>(
+                          v, pair, done, list, from_list_range, advance_time, s);
+  return v.counts ? launch_tiled_t<SNN_W_BF16_8B, true>(
+                        v, pair, done, list, from_list_range, advance_time, s)
+                  : launch_tiled_t<SNN_W_BF16_8B, false>(
+                        v, pair, done, list, from_list_range, advance_time, s);
 }
 
 cudaError_t launch_prepare_external(const NetView& v, const uint32_t* src,

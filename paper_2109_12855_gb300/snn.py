@@ -19,8 +19,10 @@ SNN_E_OOM, SNN_E_ARG, SNN_E_STATE, SNN_E_TIMEOUT, SNN_E_OVERFLOW, SNN_E_CUDA = \
     -1, -2, -3, -4, -5, -6
 SNN_MEM_HOST, SNN_MEM_DEVICE = 0, 1
 SNN_W_FP32_12B, SNN_W_BF16_8B = 0, 1
+SNN_DELIVER_TILED, SNN_DELIVER_ATOMIC = 0, 1
 SNN_ERRF_SPIKE_LIST, SNN_ERRF_SPIKE_LOG, SNN_ERRF_BAD_SOURCE, SNN_ERRF_CHUNKS = \
     1, 2, 4, 8
+SNN_ERRF_TIMEOUT = 16
 
 EXPORTS = [
     "snn_abi_version", "snn_last_error", "snn_default_params",
@@ -51,7 +53,7 @@ class snn_params(C.Structure):
                 ("seed", C.c_uint64), ("weight_format", C.c_int32),
                 ("n_slots", C.c_int32), ("interval", C.c_int32),
                 ("init_v_random", C.c_int32), ("count_events", C.c_int32),
-                ("pad_", C.c_int32), ("spike_log_capacity", C.c_uint64)]
+                ("deliver_mode", C.c_int32), ("spike_log_capacity", C.c_uint64)]
 
 
 class snn_conn_params(C.Structure):
@@ -71,7 +73,9 @@ class snn_stats(C.Structure):
                 ("update_launches", C.c_uint64),
                 ("deliver_launches", C.c_uint64), ("ms_update", C.c_double),
                 ("ms_deliver", C.c_double), ("bytes_per_record", C.c_uint64),
-                ("store_bytes", C.c_uint64)]
+                ("store_bytes", C.c_uint64), ("n_tiles", C.c_uint32),
+                ("tile_width", C.c_uint32), ("window", C.c_int32),
+                ("deliver_mode", C.c_int32)]
 
 
 _P = C.c_void_p

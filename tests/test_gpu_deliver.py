@@ -17,10 +17,12 @@ def _gpu():
     need_gpu()
 
 
-@pytest.fixture(scope="module", params=[0, 1], ids=["fp32", "bf16"])
+@pytest.fixture(scope="module", params=[(0, 0), (1, 0), (0, 1), (1, 1)],
+                ids=["fp32-tiled", "bf16-tiled", "fp32-atomic", "bf16-atomic"])
 def small(request):
+    fmt, mode = request.param
     net, cp = fixed_net(400, 100, 40, 10, 22.4, -112.0, 10, 20, seed=3,
-                        fmt=request.param)
+                        fmt=fmt, deliver_mode=mode)
     store = O.build_fixed_indegree(cp)
     yield net, store
     net.close()
@@ -76,8 +78,10 @@ def test_deliveries_accumulate(small):
     assert np.all(np.abs(rb - rb_o) <= 1e-5 * (absw + absw2))
 
 
-def test_bernoulli_interval_lists_medium():
-    net, cp = fixed_net(16000, 4000, 1600, 400, 22.4, -112.0, 15, 15, seed=8)
+@pytest.mark.parametrize("mode", [0, 1], ids=["tiled", "atomic"])
+def test_bernoulli_interval_lists_medium(mode):
+    net, cp = fixed_net(16000, 4000, 1600, 400, 22.4, -112.0, 15, 15, seed=8,
+                        deliver_mode=mode)
     with net:
         store = O.build_fixed_indegree(cp)
         for k, rate in enumerate((8.0, 40.0, 400.0)):
@@ -85,14 +89,15 @@ def test_bernoulli_interval_lists_medium():
             check_delivery(net, store, src, t)
 
 
+@pytest.mark.parametrize("mode", [0, 1], ids=["tiled", "atomic"])
 @pytest.mark.parametrize("fmt", [0, 1])
-def test_edge_net_long_and_short_segments(fmt):
+def test_edge_net_long_and_short_segments(fmt, mode):
     # hub row of 20,000 synapses; many sources with one synapse; sources
     # with none; delays over the whole ring
     n = 3000
     src, tgt, d, w = W.random_edges(n, 3000, 1, 32, seed=12, hub=5,
                                     hub_edges=20000)
-    net, store = edge_net(n, (src, tgt, d, w), fmt)
+    net, store = edge_net(n, (src, tgt, d, w), fmt, deliver_mode=mode)
     with net:
         deg = np.diff(store.row_ptr.astype(np.int64))
         assert (deg == 0).sum() > 100 and (deg == 1).sum() > 100
@@ -127,3 +132,44 @@ def test_device_resident_spike_list(small):
     rb_o, cnt, absw, ev_o = O.deliver_ref(store, S, src, t)
     assert ev == ev_o
     assert np.all(np.abs(rb_dev.cpu().numpy() - rb_o) <= 1e-5 * absw)
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["tiled", "atomic"])
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_update_then_deliver_pending_matches_oracle(fmt, mode):
+    """The interval path: snn_update compacts the spikes of one interval,
+    snn_deliver_pending delivers them.  The oracle updates the same state
+    (its spike list must equal the GPU's) and delivers its own list with
+    Algorithm REF onto its own ring buffer."""
+    from paper_2109_12855_gb300 import snn
+    n = 5000
+    net, cp = fixed_net(4000, 1000, 400, 100, 22.4, -112.0, 10, 20, seed=31,
+                        fmt=fmt, deliver_mode=mode, init_v_random=0,
+                        spike_log_capacity=1 << 20)
+    store = O.build_fixed_indegree(cp)
+    V, I, J, refr = W.random_state(n, seed=77 + fmt)
+    V[::7] = 100.0                       # these fire at the first step
+    g = W.rng(5)
+    rb = g.normal(0, 30.0, (S, n)).astype(np.float32)
+    with net:
+        V32, I32, J32 = (x.astype(np.float32) for x in (V, I, J))
+        net.write_state(V32, I32, J32, refr)
+        snn.snn_write_rb(net.h, rb)
+        t0 = 4321
+        snn.snn_update(net.h, t0, 10)
+        gsrc, gt = net.read_spikes()
+        snn.snn_deliver_pending(net.h)
+        grb = net.read_rb()
+        assert net.stats().t_now == t0 + 10
+    st = O.State(V32.astype(np.float64), I32.astype(np.float64),
+                 J32.astype(np.float64), refr.copy())
+    orb = rb.astype(np.float64)
+    osrc, ot = O.update(O.Neuron(), st, orb, t0, 10, 0.0, 0.0, 1)
+    assert len(osrc) > 500
+    assert sorted(zip(gsrc.tolist(), gt.tolist())) == \
+        sorted(zip(osrc.tolist(), ot.tolist()))
+    rb_del, cnt, absw, ev = O.deliver_ref(store, S, osrc, ot)
+    want = orb + rb_del
+    # values: the random ring-buffer contents plus the delivered sums
+    tol = 1e-5 * absw + 1e-6 * np.abs(orb)
+    assert np.all(np.abs(grb - want) <= tol)

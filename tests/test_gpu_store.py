@@ -15,22 +15,40 @@ def _gpu():
     need_gpu()
 
 
+def _canonical(tg, dl, w, a, b):
+    """Row [a, b) sorted by (delay, target, weight)."""
+    order = np.lexsort((w[a:b], tg[a:b], dl[a:b]))
+    return tg[a:b][order], dl[a:b][order], w[a:b][order]
+
+
 def _compare(net, store, exact_w=True, fmt=0):
+    """Same rows as the oracle's store (order within a row may differ: the
+    GPU store is sorted by target tile first); each GPU row is sorted by
+    (tile, delay, target)."""
     rp, tg, dl, w = net.read_store()
+    st = net.stats()
     assert np.array_equal(rp, store.row_ptr)
-    assert np.array_equal(tg, store.tgt)
-    assert np.array_equal(dl.astype(np.int32), store.delay)
+    tw = st.tile_width
     wo = store.w.astype(np.float32)
-    if exact_w:
-        assert np.array_equal(w, wo)
-    else:
-        # FP64 normals come from CUDA's and the host's log/cos, which may
-        # differ in the last FP64 bit; after rounding to the stored format
-        # at most a one-ulp difference can remain, and rarely
-        ulp = np.spacing(np.abs(wo)) * (65536.0 if fmt == 1 else 1.0)
-        diff = np.abs(w - wo)
-        assert np.all(diff <= ulp)
-        assert (diff == 0).mean() > 0.999
+    dlo = store.delay.astype(np.uint8)
+    for i in range(len(rp) - 1):
+        a, b = int(rp[i]), int(rp[i + 1])
+        if a == b:
+            continue
+        key = ((tg[a:b] // tw).astype(np.int64) << 40) | \
+            (dl[a:b].astype(np.int64) << 32) | tg[a:b]
+        assert np.all(np.diff(key) >= 0), i
+        gt, gd, gw = _canonical(tg, dl, w, a, b)
+        ot, od, ow = _canonical(store.tgt, dlo, wo, a, b)
+        assert np.array_equal(gt, ot) and np.array_equal(gd, od), i
+        if exact_w:
+            assert np.array_equal(gw, ow), i
+        else:
+            # FP64 normals come from CUDA's and the host's log/cos, which may
+            # differ in the last FP64 bit; after rounding to the stored
+            # format at most a one-ulp difference can remain, and rarely
+            ulp = np.spacing(np.abs(ow)) * (65536.0 if fmt == 1 else 1.0)
+            assert np.all(np.abs(gw - ow) <= ulp), i
 
 
 @pytest.mark.parametrize("fmt", [0, 1])
@@ -42,6 +60,7 @@ def test_fixed_indegree_store_small(fmt):
         st = net.stats()
         assert st.min_delay == 10 and st.max_delay == 20 and st.interval == 10
         assert st.n_synapses == 500 * 50
+        assert st.window == 20 and st.n_tiles * st.tile_width >= 500
 
 
 @pytest.mark.parametrize("fmt", [0, 1])
