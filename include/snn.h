@@ -294,6 +294,19 @@ int snn_read_store(snn_net* net, uint64_t* row_ptr, uint32_t* tgt,
  * spike) from the next update on.  Errors: SNN_E_ARG (negative rate, or a
  * rate whose inversion table exceeds 128 outcomes). */
 int snn_set_drive(snn_net* net, double nu_ext, double w_ext);
+/* Checkpoint / restore of the dynamic state: V, I, J, refractory counts,
+ * the ring buffer and the clock.  Every random draw is a Philox call keyed by
+ * (neuron, step) and the seed, so no generator state exists beyond the
+ * clock.  The connection store and parameters are not included: restore into
+ * a net built with the same parameters and connections.  The image is a
+ * little-endian byte string: 64-byte header (magic "SNNSTATE", version, N,
+ * n_slots, t_now), then float32 V, I, J, int32 refr (N each) and float32
+ * rb[n_slots][N].  snn_state_size gives its length; save synchronises;
+ * load requires no pending spikes and checks the header (SNN_E_ARG on a
+ * mismatch). */
+int snn_state_size(snn_net* net, uint64_t* bytes);
+int snn_save_state(snn_net* net, void* host_buf, uint64_t cap);
+int snn_load_state(snn_net* net, const void* host_buf, uint64_t size);
 /* Set the step counter (next step to update). */
 int snn_set_time(snn_net* net, int64_t t);
 /* Profiling on: every update and deliver launch is bracketed by CUDA events

@@ -1101,6 +1101,86 @@ int snn_read_store(snn_net* net, uint64_t* row_ptr, uint32_t* tgt,
   return SNN_OK;
 }
 
+namespace {
+struct StateHeader {
+  char magic[8];     // "SNNSTATE"
+  uint32_t version;  // 1
+  uint32_t n;
+  int32_t n_slots;
+  int32_t pad_;
+  int64_t t_now;
+  char reserved[32];
+};
+static_assert(sizeof(StateHeader) == 64, "state header is 64 bytes");
+
+uint64_t state_bytes(const snn_net* net) {
+  return sizeof(StateHeader) + 4ull * net->n * 4 +
+         4ull * net->n * (uint64_t)net->n_slots;
+}
+}  // namespace
+
+int snn_state_size(snn_net* net, uint64_t* bytes) {
+  REQ(net && bytes, SNN_E_ARG, "null argument");
+  *bytes = state_bytes(net);
+  return SNN_OK;
+}
+
+int snn_save_state(snn_net* net, void* host_buf, uint64_t cap) {
+  REQ(net && host_buf, SNN_E_ARG, "null argument");
+  REQ(cap >= state_bytes(net), SNN_E_OVERFLOW, "state needs %llu bytes",
+      (unsigned long long)state_bytes(net));
+  REQ(!net->pending, SNN_E_STATE, "spikes of an update are pending");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  long long t_now = 0;
+  CK(cudaMemcpyAsync(&t_now, &net->ctl->t_now, sizeof t_now,
+                     cudaMemcpyDeviceToHost, net->stream));
+  CK(cudaStreamSynchronize(net->stream));
+  StateHeader h{};
+  memcpy(h.magic, "SNNSTATE", 8);
+  h.version = 1;
+  h.n = net->n;
+  h.n_slots = net->n_slots;
+  h.t_now = t_now;
+  char* out = static_cast<char*>(host_buf);
+  memcpy(out, &h, sizeof h);
+  char* p = out + sizeof h;
+  const size_t b = (size_t)net->n * 4;
+  if ((rc = snn_read_state(net, reinterpret_cast<float*>(p),
+                           reinterpret_cast<float*>(p + b),
+                           reinterpret_cast<float*>(p + 2 * b),
+                           reinterpret_cast<int32_t*>(p + 3 * b),
+                           SNN_MEM_HOST)) != SNN_OK)
+    return rc;
+  return snn_read_rb(net, reinterpret_cast<float*>(p + 4 * b), SNN_MEM_HOST);
+}
+
+int snn_load_state(snn_net* net, const void* host_buf, uint64_t size) {
+  REQ(net && host_buf, SNN_E_ARG, "null argument");
+  REQ(size >= state_bytes(net), SNN_E_ARG, "state image too short");
+  REQ(!net->pending, SNN_E_STATE, "spikes of an update are pending");
+  StateHeader h;
+  memcpy(&h, host_buf, sizeof h);
+  REQ(memcmp(h.magic, "SNNSTATE", 8) == 0 && h.version == 1, SNN_E_ARG,
+      "not a state image");
+  REQ(h.n == net->n && h.n_slots == net->n_slots, SNN_E_ARG,
+      "state image of a different net (N %u, slots %d)", h.n, h.n_slots);
+  REQ(h.t_now >= 0 && h.t_now < (1ll << 31), SNN_E_ARG, "bad clock");
+  const char* p = static_cast<const char*>(host_buf) + sizeof h;
+  const size_t b = (size_t)net->n * 4;
+  int rc;
+  if ((rc = snn_write_state(net, reinterpret_cast<const float*>(p),
+                            reinterpret_cast<const float*>(p + b),
+                            reinterpret_cast<const float*>(p + 2 * b),
+                            reinterpret_cast<const int32_t*>(p + 3 * b),
+                            SNN_MEM_HOST)) != SNN_OK)
+    return rc;
+  if ((rc = snn_write_rb(net, reinterpret_cast<const float*>(p + 4 * b),
+                         SNN_MEM_HOST)) != SNN_OK)
+    return rc;
+  return snn_set_time(net, h.t_now);
+}
+
 int snn_set_drive(snn_net* net, double nu_ext, double w_ext) {
   REQ(net, SNN_E_ARG, "null net");
   REQ(nu_ext >= 0 && isfinite(nu_ext) && isfinite(w_ext), SNN_E_ARG,

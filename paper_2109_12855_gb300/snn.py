@@ -31,7 +31,8 @@ EXPORTS = [
     "snn_discard_pending", "snn_deliver", "snn_deliver_noalloc",
     "snn_simulate", "snn_read_spikes",
     "snn_read_rb", "snn_write_rb", "snn_read_counts", "snn_clear_rb",
-    "snn_read_state", "snn_write_state", "snn_read_store", "snn_set_drive",
+    "snn_read_state", "snn_write_state", "snn_read_store", "snn_state_size",
+    "snn_save_state", "snn_load_state", "snn_set_drive",
     "snn_set_time",
     "snn_set_profiling", "snn_get_stats", "snn_clear_errors", "snn_sync",
     "snn_destroy",
@@ -120,6 +121,9 @@ def lib():
             "snn_read_state": ([_P, _P, _P, _P, _P, C.c_int], C.c_int),
             "snn_write_state": ([_P, _P, _P, _P, _P, C.c_int], C.c_int),
             "snn_read_store": ([_P, _P, _P, _P, _P, C.c_int], C.c_int),
+            "snn_state_size": ([_P, C.POINTER(C.c_uint64)], C.c_int),
+            "snn_save_state": ([_P, _P, C.c_uint64], C.c_int),
+            "snn_load_state": ([_P, _P, C.c_uint64], C.c_int),
             "snn_set_drive": ([_P, C.c_double, C.c_double], C.c_int),
             "snn_set_time": ([_P, C.c_int64], C.c_int),
             "snn_set_profiling": ([_P, C.c_int], C.c_int),
@@ -283,6 +287,25 @@ def snn_read_store(net, row_ptr=None, tgt=None, delay=None, w=None):
     mem = _mem_of(row_ptr, tgt, delay, w)
     _check(lib().snn_read_store(net, _buf(row_ptr)[0], _buf(tgt)[0],
                                 _buf(delay)[0], _buf(w)[0], mem))
+
+
+def snn_state_size(net) -> int:
+    n = C.c_uint64()
+    _check(lib().snn_state_size(net, C.byref(n)))
+    return n.value
+
+
+def snn_save_state(net) -> bytes:
+    """Checkpoint image of the net's dynamic state (bytes)."""
+    n = snn_state_size(net)
+    buf = (C.c_char * n)()
+    _check(lib().snn_save_state(net, buf, n))
+    return bytes(buf)
+
+
+def snn_load_state(net, image: bytes):
+    buf = C.create_string_buffer(image, len(image))
+    _check(lib().snn_load_state(net, buf, len(image)))
 
 
 def snn_set_drive(net, nu_ext: float, w_ext: float):
