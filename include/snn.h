@@ -121,6 +121,10 @@ typedef struct snn_params {
   int32_t deliver_mode;   /* SNN_DELIVER_TILED (0, default) or
                              SNN_DELIVER_ATOMIC (1); see below */
   uint64_t spike_log_capacity; /* entries kept for snn_read_spikes (0: none) */
+  int32_t tile_width;     /* targets per tile of the tiled delivery; 0 = the
+                             automatic choice (about N / #SMs), otherwise used
+                             as given when its shared-memory window fits */
+  int32_t reserved_;
 } snn_params;
 
 /* Fixed in-degree connection rule (the benchmark model's random
@@ -320,6 +324,94 @@ int snn_clear_errors(snn_net* net);
 int snn_sync(snn_net* net);
 /* Free everything; net may be NULL. */
 int snn_destroy(snn_net* net);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of independent simulation requests.
+ * (The paper has no serving layer; this is the deployment form of the same
+ * update/deliver cycle.)
+ *
+ * A server owns a device-memory budget.  Submitted requests queue in
+ * arrival order; a builder thread admits the head request once its
+ * estimated footprint fits the budget and builds its connection store while
+ * the admitted nets keep running.  Each snn_server_step advances every
+ * admitted net by its next interval in ONE batched update launch and ONE
+ * batched tiled-delivery launch for all nets together (block -> net lookup
+ * table; per-net clock, state, store and interval), graph-captured while the
+ * batch is unchanged; a small autotuner picks how many intervals one step
+ * runs (1, 2, 4 or 8) from measured time per interval.  Nets that reached
+ * their step count are retired: their counters (and spikes, if recorded)
+ * move to the request's result and their memory is released.
+ * Results do not depend on the mix: delivery sums are exact fixed point and
+ * every random draw is keyed by (neuron, step), so a request's spikes are
+ * bit-identical alone and batched.
+ * ---------------------------------------------------------------------- */
+typedef struct snn_server snn_server;
+
+typedef struct snn_request {
+  snn_params params;      /* model and seed; weight_format must equal the
+                             server's; spike_log_capacity is set by the
+                             server when record_spikes is 1 */
+  snn_conn_params conn;   /* fixed in-degree connectivity (k_exc + k_inh >= 1) */
+  int64_t n_steps;        /* biological time to simulate, in steps (>= 1) */
+  uint64_t user_tag;      /* returned in the result */
+  int32_t record_spikes;  /* 1: keep the spike list (snn_server_spikes) */
+  int32_t pad_;
+} snn_request;
+
+enum {
+  SNN_REQ_QUEUED = 0,
+  SNN_REQ_BUILDING = 1,
+  SNN_REQ_RUNNING = 2,
+  SNN_REQ_DONE = 3,
+  SNN_REQ_FAILED = -1
+};
+
+typedef struct snn_result {
+  uint64_t id, user_tag;
+  int32_t state;          /* SNN_REQ_* */
+  int32_t error;          /* status code of a failed request */
+  uint64_t n_neurons, n_synapses;
+  uint64_t spikes, events; /* counters of the finished simulation */
+  int64_t n_steps;
+  double t_submit, t_admit, t_start, t_done; /* seconds on the server clock:
+                             submitted, admitted (build begins), first batch
+                             step, result ready */
+  uint64_t bytes;         /* device bytes reserved for it */
+} snn_result;
+
+typedef struct snn_server_stats {
+  uint64_t submitted, done, failed, active, queued;
+  uint64_t steps, intervals, kernel_launches;
+  uint64_t events, spikes;  /* of finished requests */
+  uint64_t mem_budget, mem_used;
+  int32_t intervals_per_step; /* current choice of the autotuner */
+  int32_t tuned;              /* 1 once the autotuner settled */
+  double gpu_ms;              /* CUDA-event time of the batched launches */
+} snn_server_stats;
+
+/* Create a server with a device-memory budget (bytes), one weight format
+ * for all its requests, on the current device; stream: cudaStream_t as
+ * void* for the batched launches (NULL: an internal blocking stream). */
+int snn_server_create(uint64_t mem_budget, int32_t weight_format,
+                      void* stream, snn_server** out);
+/* Queue a request; *id identifies it.  Thread-safe.  SNN_E_ARG for invalid
+ * parameters or a footprint above the whole budget. */
+int snn_server_submit(snn_server* sv, const snn_request* req, uint64_t* id);
+/* Admit built nets, advance all running nets by one step (the autotuned
+ * number of intervals), retire finished ones.  *n_active (optional): nets
+ * running after the step.  Returns immediately when nothing is running. */
+int snn_server_step(snn_server* sv, int32_t* n_active);
+/* State and counters of a request (thread-safe). */
+int snn_server_poll(snn_server* sv, uint64_t id, snn_result* out);
+/* Spikes (source, step) of a finished request that recorded them; *n is
+ * the number recorded (SNN_E_OVERFLOW if above cap). */
+int snn_server_spikes(snn_server* sv, uint64_t id, uint32_t* src, int32_t* t,
+                      uint64_t cap, uint64_t* n);
+/* Forget a finished request's result. */
+int snn_server_release(snn_server* sv, uint64_t id);
+int snn_server_get_stats(snn_server* sv, snn_server_stats* out);
+/* Stop the builder, free all nets; sv may be NULL. */
+int snn_server_destroy(snn_server* sv);
 
 #ifdef __cplusplus
 }

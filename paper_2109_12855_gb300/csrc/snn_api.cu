@@ -145,83 +145,9 @@ bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 }  // namespace
 
-// ---------------------------------------------------------------------------
-// The net.
-// ---------------------------------------------------------------------------
-struct snn_net {
-  snn_params p{};
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int device = 0;
-  uint32_t n = 0, pitch = 0;
-  int fmt = 0, n_slots = 0;
-  UpdConst uc{};
-  float *V = nullptr, *I = nullptr, *J = nullptr;
-  int32_t* refr = nullptr;
-  float* rb = nullptr;
-  uint32_t* counts = nullptr;
-  Ctl* ctl = nullptr;
-  uint64_t* row_ptr = nullptr;
-  void* recs = nullptr;
-  uint64_t n_syn = 0, recs_bytes = 0;
-  uint32_t* tile_off = nullptr;  // [n][n_tiles + 1]
-  uint32_t tile_w = 0, n_tiles = 0;
-  int lo_bits = 0;
-  int window = 0;
-  uint32_t mult_max = 0, k_in_max = 0, spikes_per_iv = 1;
-  float max_abs_w = 0.f;
-  SpikeEntry* list = nullptr;
-  uint64_t list_cap = 0;
-  SpikeEntry* ext_list = nullptr;
-  uint32_t* ext_src = nullptr;
-  int32_t* ext_t = nullptr;
-  uint64_t ext_cap = 0;
-  uint32_t* log_src = nullptr;
-  int32_t* log_t = nullptr;
-  uint64_t log_cap = 0;
-  bool connected = false, finalized = false, pending = false;
-  int interval = 0, dmin = 0, dmax = 0;
-  long long t_host = 0;
-  bool profiling = false;
-  std::vector<cudaEvent_t> ev;
-  double ms_update = 0, ms_deliver = 0;
-  uint64_t launches = 0, upd_launches = 0, del_launches = 0;
-  cudaGraphExec_t graph = nullptr;
+#include "snn_net.cuh"
 
-  NetView view() const {
-    NetView v;
-    v.n = n;
-    v.pitch = pitch;
-    v.slot_mask = (uint32_t)n_slots - 1u;
-    v.chunk = (uint32_t)chunk_records(fmt);
-    v.fmt = fmt;
-    v.V = V;
-    v.I = I;
-    v.J = J;
-    v.refr = refr;
-    v.rb = rb;
-    v.counts = counts;
-    v.row_ptr = row_ptr;
-    v.recs = recs;
-    v.tile_off = tile_off;
-    v.tile_w = tile_w;
-    v.n_tiles = n_tiles;
-    v.d_min = dmin;
-    v.d_max = dmax;
-    v.window = window;
-    v.mult_max = mult_max;
-    v.k_in_max = k_in_max;
-    v.spikes_per_iv = spikes_per_iv;
-    v.max_abs_w = max_abs_w;
-    v.list = list;
-    v.list_cap = list_cap;
-    v.log_src = log_src;
-    v.log_t = log_t;
-    v.log_cap = log_cap;
-    v.ctl = ctl;
-    return v;
-  }
-};
+void snn::set_last_error(const char* msg) { g_err = msg; }
 
 namespace {
 
@@ -257,8 +183,8 @@ int set_device(snn_net* net) {
 // tile width cells of two int32 accumulators) fits the shared-memory budget.  The sort key holds the
 // tile and the position in it in 24 bits; when a non-power-of-two width
 // would not fit them, the width is rounded up to a power of two.
-void choose_tiles(uint32_t n, int window, uint32_t* tile_w, int* lo_bits,
-                  uint32_t* n_tiles) {
+void choose_tiles(uint32_t n, int window, int32_t hint, uint32_t* tile_w,
+                  int* lo_bits, uint32_t* n_tiles) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -270,7 +196,9 @@ void choose_tiles(uint32_t n, int window, uint32_t* tile_w, int* lo_bits,
     tw = (n + k * sms - 1) / (k * sms);
     if (tw <= tw_max) break;
   }
+  if (hint > 0) tw = std::min<uint64_t>((uint64_t)hint, tw_max);
   tw = std::max<uint64_t>(tw, std::min<uint64_t>(64, n));
+  tw = std::min<uint64_t>(tw, n);
   int lb = 1;
   while ((1ull << lb) < tw) ++lb;
   uint64_t nt = (n + tw - 1) / tw;
@@ -282,6 +210,15 @@ void choose_tiles(uint32_t n, int window, uint32_t* tile_w, int* lo_bits,
   *lo_bits = lb;
   *n_tiles = (uint32_t)nt;
 }
+
+}  // namespace
+
+void snn::tile_geometry(uint32_t n, int window, int32_t hint, uint32_t* tile_w,
+                        int* lo_bits, uint32_t* n_tiles) {
+  choose_tiles(n, window, hint, tile_w, lo_bits, n_tiles);
+}
+
+namespace {
 
 bool use_tiled(const snn_net* net) {
   return net->p.deliver_mode == SNN_DELIVER_TILED && net->n_syn > 0 &&
@@ -335,8 +272,8 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
                      cudaMemcpyHostToDevice, s));
   // tiles sized for the widest window the interval can reach
   const int iv = net->p.interval ? net->p.interval : d_lo;
-  choose_tiles(n, iv + (d_hi - d_lo), &net->tile_w, &net->lo_bits,
-               &net->n_tiles);
+  choose_tiles(n, iv + (d_hi - d_lo), net->p.tile_width, &net->tile_w,
+               &net->lo_bits, &net->n_tiles);
   CK(dalloc(&net->tile_off, (uint64_t)n * (net->n_tiles + 1) * sizeof(uint32_t)));
   // keys; for 8-byte records the key array becomes the record array
   uint64_t* keys = nullptr;
@@ -530,6 +467,7 @@ int snn_create(const snn_params* p, void* stream, snn_net** out) {
       "bad interval");
   REQ(p->deliver_mode == SNN_DELIVER_TILED || p->deliver_mode == SNN_DELIVER_ATOMIC,
       SNN_E_ARG, "bad deliver_mode %d", p->deliver_mode);
+  REQ(p->tile_width >= 0, SNN_E_ARG, "bad tile_width %d", p->tile_width);
   snn_net* net = new snn_net();
   net->p = *p;
   net->n = (uint32_t)n;

@@ -195,6 +195,14 @@ struct NetView {
   Ctl* ctl;
 };
 
+// One net of a batch advanced by the batched kernels (device table entry).
+struct BatchNet {
+  NetView v;
+  UpdConst c;
+  int n_steps;   // steps of this net's next interval
+  int pad_;
+};
+
 __device__ inline unsigned lane_id() { return threadIdx.x & 31u; }
 
 }  // namespace snn
@@ -221,6 +229,13 @@ cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
                                  int from_list_range, int advance_time,
                                  cudaStream_t s);
 size_t tiled_smem_bytes(const NetView& v);
+// Batched kernels (serving): bmap entries are (net index, block or tile).
+cudaError_t launch_update_batch(const BatchNet* nets, const uint2* bmap,
+                                uint32_t n_blocks, cudaStream_t s);
+cudaError_t launch_deliver_tiled_batch(int fmt, const BatchNet* nets,
+                                       const uint2* bmap, uint32_t n_ctas,
+                                       size_t smem, cudaStream_t s);
+uint32_t update_threads();
 cudaError_t launch_deliver_noalloc(const NetView& v, const uint32_t* src,
                                    const int32_t* t, uint32_t n,
                                    cudaStream_t s);

@@ -139,19 +139,22 @@ __device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b,
   __syncthreads();  // the shared arrays are reused by the next call
 }
 
-__global__ void __launch_bounds__(kUpdThreads)
-k_update(NetView v, UpdConst c, int n_steps, int from_ctl, long long t0_arg) {
+// Body of the update for neuron block `block` of net v (one thread per
+// neuron); shared by the single-net and the batched kernels.
+__device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
+                                            int n_steps, int from_ctl,
+                                            long long t0_arg, uint32_t block) {
   __shared__ uint32_t s_thr[kMaxPoisson];
   __shared__ unsigned long long s_base[2];
   for (int k = threadIdx.x; k < c.n_thr; k += blockDim.x) s_thr[k] = c.thr[k];
   const long long t0 = from_ctl ? v.ctl->t_now : t0_arg;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (block == 0 && threadIdx.x == 0) {
     v.ctl->iv_steps = n_steps;
     if (!from_ctl) v.ctl->t_now = t0;
   }
   __syncthreads();
 
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t i = block * blockDim.x + threadIdx.x;
   const bool live = i < v.n;
   float V = 0.f, I = 0.f, J = 0.f;
   int refr = 0;
@@ -279,6 +282,28 @@ k_update(NetView v, UpdConst c, int n_steps, int from_ctl, long long t0_arg) {
     v.J[i] = J;
     v.refr[i] = refr;
   }
+}
+
+__global__ void __launch_bounds__(kUpdThreads)
+k_update(NetView v, UpdConst c, int n_steps, int from_ctl, long long t0_arg) {
+  update_body(v, c, n_steps, from_ctl, t0_arg, blockIdx.x);
+}
+
+// All nets of a batch in one launch: block b updates neuron block bmap[b].y
+// of net bmap[b].x, from that net's clock.
+__global__ void __launch_bounds__(kUpdThreads)
+k_update_batch(const BatchNet* __restrict__ nets, const uint2* __restrict__ bmap) {
+  __shared__ UpdConst s_c;
+  const uint2 m = bmap[blockIdx.x];
+  const BatchNet& bn = nets[m.x];
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&bn.c);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&s_c);
+  for (uint32_t k = threadIdx.x; k < sizeof(UpdConst) / 4; k += blockDim.x)
+    dst[k] = src[k];
+  const NetView v = bn.v;
+  const int n_steps = bn.n_steps;
+  __syncthreads();
+  update_body(v, s_c, n_steps, 1, 0, m.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -548,14 +573,13 @@ __device__ FixScale fix_scale(const NetView& v, uint64_t n_sp,
 }
 
 template <int FMT, bool COUNT>
-__global__ void __launch_bounds__(kTileThreads, 1)
-k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
-                const SpikeEntry* __restrict__ list, int from_list_range,
-                int advance_time) {
+__device__ __forceinline__ void deliver_tile_body(
+    const NetView& v, unsigned long long* pair_p, unsigned int* done_p,
+    const SpikeEntry* __restrict__ list, int from_list_range, int advance_time,
+    uint32_t tile, int* acc_mem) {
   // U runs per warp pass, PER records per lane of each loaded before use
   constexpr int U = FMT == SNN_W_FP32_12B ? 2 : 4;
   constexpr int PER = 3;
-  extern __shared__ __align__(16) int acc_mem[];
   __shared__ SegDesc s_desc[kDescBatch];
   __shared__ unsigned long long s_pair;
   __shared__ long long s_base;
@@ -564,7 +588,6 @@ k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
   const uint32_t TW = v.tile_w;
   const uint32_t W = (uint32_t)v.window;
   const uint32_t cells = W * TW;
-  const uint32_t tile = blockIdx.x;
   const uint32_t tgt_lo = tile * TW;
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
@@ -704,12 +727,35 @@ k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
   if (threadIdx.x == 0) {
     __threadfence();
     unsigned prev = atomicAdd(done_p, 1u);
-    if (prev == gridDim.x - 1) {
+    if (prev == v.n_tiles - 1) {
       *pair_p = 0ull;
       *done_p = 0u;
       if (advance_time) v.ctl->t_now += v.ctl->iv_steps;
     }
   }
+}
+
+template <int FMT, bool COUNT>
+__global__ void __launch_bounds__(kTileThreads, 1)
+k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
+                const SpikeEntry* __restrict__ list, int from_list_range,
+                int advance_time) {
+  extern __shared__ __align__(16) int acc_mem[];
+  deliver_tile_body<FMT, COUNT>(v, pair_p, done_p, list, from_list_range,
+                                advance_time, blockIdx.x, acc_mem);
+}
+
+// All nets of a batch in one launch: CTA b delivers tile bmap[b].y of net
+// bmap[b].x (its pending interval list, advancing that net's clock).
+template <int FMT>
+__global__ void __launch_bounds__(kTileThreads, 1)
+k_deliver_tiled_batch(const BatchNet* __restrict__ nets,
+                      const uint2* __restrict__ bmap) {
+  extern __shared__ __align__(16) int acc_mem[];
+  const uint2 m = bmap[blockIdx.x];
+  const NetView v = nets[m.x].v;
+  deliver_tile_body<FMT, false>(v, &v.ctl->pair, &v.ctl->done, v.list, 0, 1,
+                                m.y, acc_mem);
 }
 
 // ---------------------------------------------------------------------------
@@ -896,6 +942,39 @@ cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
                   : launch_tiled_t<SNN_W_BF16_8B, false>(
                         v, pair, done, list, from_list_range, advance_time, s);
 }
+
+cudaError_t launch_update_batch(const BatchNet* nets, const uint2* bmap,
+                                uint32_t n_blocks, cudaStream_t s) {
+  if (n_blocks == 0) return cudaSuccess;
+  k_update_batch<<<n_blocks, kUpdThreads, 0, s>>>(nets, bmap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deliver_tiled_batch(int fmt, const BatchNet* nets,
+                                       const uint2* bmap, uint32_t n_ctas,
+                                       size_t smem, cudaStream_t s) {
+  if (n_ctas == 0) return cudaSuccess;
+  static int configured[2] = {0, 0};
+  const int k = fmt == SNN_W_FP32_12B ? 0 : 1;
+  if (!configured[k]) {
+    cudaError_t e = k == 0
+        ? cudaFuncSetAttribute(k_deliver_tiled_batch<SNN_W_FP32_12B>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024)
+        : cudaFuncSetAttribute(k_deliver_tiled_batch<SNN_W_BF16_8B>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured[k] = 1;
+  }
+  if (k == 0)
+    k_deliver_tiled_batch<SNN_W_FP32_12B><<<n_ctas, kTileThreads, smem, s>>>(nets, bmap);
+  else
+    k_deliver_tiled_batch<SNN_W_BF16_8B><<<n_ctas, kTileThreads, smem, s>>>(nets, bmap);
+  return cudaGetLastError();
+}
+
+uint32_t update_threads() { return kUpdThreads; }
 
 cudaError_t launch_prepare_external(const NetView& v, const uint32_t* src,
                                     const int32_t* t, uint32_t n,

@@ -1,0 +1,97 @@
+// snn_net.cuh -- host-side definition of a net (shared by the C ABI and the
+// serving loop).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "snn_internal.cuh"
+
+using namespace snn;
+
+namespace snn {
+// Message returned by snn_last_error() on this thread.
+void set_last_error(const char* msg);
+// Tile geometry the store builder uses for n targets (see snn_api.cu).
+void tile_geometry(uint32_t n, int window, int32_t hint, uint32_t* tile_w,
+                   int* lo_bits, uint32_t* n_tiles);
+}  // namespace snn
+
+// The net: parameters, device buffers and host bookkeeping.
+struct snn_net {
+  snn_params p{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  uint32_t n = 0, pitch = 0;
+  int fmt = 0, n_slots = 0;
+  UpdConst uc{};
+  float *V = nullptr, *I = nullptr, *J = nullptr;
+  int32_t* refr = nullptr;
+  float* rb = nullptr;
+  uint32_t* counts = nullptr;
+  Ctl* ctl = nullptr;
+  uint64_t* row_ptr = nullptr;
+  void* recs = nullptr;
+  uint64_t n_syn = 0, recs_bytes = 0;
+  uint32_t* tile_off = nullptr;  // [n][n_tiles + 1]
+  uint32_t tile_w = 0, n_tiles = 0;
+  int lo_bits = 0;
+  int window = 0;
+  uint32_t mult_max = 0, k_in_max = 0, spikes_per_iv = 1;
+  float max_abs_w = 0.f;
+  SpikeEntry* list = nullptr;
+  uint64_t list_cap = 0;
+  SpikeEntry* ext_list = nullptr;
+  uint32_t* ext_src = nullptr;
+  int32_t* ext_t = nullptr;
+  uint64_t ext_cap = 0;
+  uint32_t* log_src = nullptr;
+  int32_t* log_t = nullptr;
+  uint64_t log_cap = 0;
+  bool connected = false, finalized = false, pending = false;
+  int interval = 0, dmin = 0, dmax = 0;
+  long long t_host = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;
+  double ms_update = 0, ms_deliver = 0;
+  uint64_t launches = 0, upd_launches = 0, del_launches = 0;
+  cudaGraphExec_t graph = nullptr;
+
+  NetView view() const {
+    NetView v;
+    v.n = n;
+    v.pitch = pitch;
+    v.slot_mask = (uint32_t)n_slots - 1u;
+    v.chunk = (uint32_t)chunk_records(fmt);
+    v.fmt = fmt;
+    v.V = V;
+    v.I = I;
+    v.J = J;
+    v.refr = refr;
+    v.rb = rb;
+    v.counts = counts;
+    v.row_ptr = row_ptr;
+    v.recs = recs;
+    v.tile_off = tile_off;
+    v.tile_w = tile_w;
+    v.n_tiles = n_tiles;
+    v.d_min = dmin;
+    v.d_max = dmax;
+    v.window = window;
+    v.mult_max = mult_max;
+    v.k_in_max = k_in_max;
+    v.spikes_per_iv = spikes_per_iv;
+    v.max_abs_w = max_abs_w;
+    v.list = list;
+    v.list_cap = list_cap;
+    v.log_src = log_src;
+    v.log_t = log_t;
+    v.log_cap = log_cap;
+    v.ctl = ctl;
+    return v;
+  }
+};
+

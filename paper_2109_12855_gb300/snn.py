@@ -35,8 +35,12 @@ EXPORTS = [
     "snn_save_state", "snn_load_state", "snn_set_drive",
     "snn_set_time",
     "snn_set_profiling", "snn_get_stats", "snn_clear_errors", "snn_sync",
-    "snn_destroy",
+    "snn_destroy", "snn_server_create", "snn_server_submit", "snn_server_step",
+    "snn_server_poll", "snn_server_spikes", "snn_server_release",
+    "snn_server_get_stats", "snn_server_destroy",
 ]
+SNN_REQ_QUEUED, SNN_REQ_BUILDING, SNN_REQ_RUNNING, SNN_REQ_DONE = 0, 1, 2, 3
+SNN_REQ_FAILED = -1
 
 
 class SnnError(RuntimeError):
@@ -54,7 +58,8 @@ class snn_params(C.Structure):
                 ("seed", C.c_uint64), ("weight_format", C.c_int32),
                 ("n_slots", C.c_int32), ("interval", C.c_int32),
                 ("init_v_random", C.c_int32), ("count_events", C.c_int32),
-                ("deliver_mode", C.c_int32), ("spike_log_capacity", C.c_uint64)]
+                ("deliver_mode", C.c_int32), ("spike_log_capacity", C.c_uint64),
+                ("tile_width", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class snn_conn_params(C.Structure):
@@ -77,6 +82,33 @@ class snn_stats(C.Structure):
                 ("store_bytes", C.c_uint64), ("n_tiles", C.c_uint32),
                 ("tile_width", C.c_uint32), ("window", C.c_int32),
                 ("deliver_mode", C.c_int32)]
+
+
+class snn_request(C.Structure):
+    _fields_ = [("params", snn_params), ("conn", snn_conn_params),
+                ("n_steps", C.c_int64), ("user_tag", C.c_uint64),
+                ("record_spikes", C.c_int32), ("pad_", C.c_int32)]
+
+
+class snn_result(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("user_tag", C.c_uint64),
+                ("state", C.c_int32), ("error", C.c_int32),
+                ("n_neurons", C.c_uint64), ("n_synapses", C.c_uint64),
+                ("spikes", C.c_uint64), ("events", C.c_uint64),
+                ("n_steps", C.c_int64), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double), ("bytes", C.c_uint64)]
+
+
+class snn_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("done", C.c_uint64),
+                ("failed", C.c_uint64), ("active", C.c_uint64),
+                ("queued", C.c_uint64), ("steps", C.c_uint64),
+                ("intervals", C.c_uint64), ("kernel_launches", C.c_uint64),
+                ("events", C.c_uint64), ("spikes", C.c_uint64),
+                ("mem_budget", C.c_uint64), ("mem_used", C.c_uint64),
+                ("intervals_per_step", C.c_int32), ("tuned", C.c_int32),
+                ("gpu_ms", C.c_double)]
 
 
 _P = C.c_void_p
@@ -131,6 +163,17 @@ def lib():
             "snn_clear_errors": ([_P], C.c_int),
             "snn_sync": ([_P], C.c_int),
             "snn_destroy": ([_P], C.c_int),
+            "snn_server_create": ([C.c_uint64, C.c_int32, _P, C.POINTER(_P)],
+                                  C.c_int),
+            "snn_server_submit": ([_P, C.POINTER(snn_request),
+                                   C.POINTER(C.c_uint64)], C.c_int),
+            "snn_server_step": ([_P, C.POINTER(C.c_int32)], C.c_int),
+            "snn_server_poll": ([_P, C.c_uint64, C.POINTER(snn_result)], C.c_int),
+            "snn_server_spikes": ([_P, C.c_uint64, _P, _P, C.c_uint64,
+                                   C.POINTER(C.c_uint64)], C.c_int),
+            "snn_server_release": ([_P, C.c_uint64], C.c_int),
+            "snn_server_get_stats": ([_P, C.POINTER(snn_server_stats)], C.c_int),
+            "snn_server_destroy": ([_P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -445,3 +488,66 @@ class Net:
         n = snn_read_spikes(self.h, src, t)
         k = min(n, cap)
         return src[:k], t[:k]
+
+
+# --- serving ----------------------------------------------------------------
+def snn_server_create(mem_budget: int, weight_format: int, stream=None):
+    h = _P()
+    _check(lib().snn_server_create(mem_budget, weight_format, stream or None,
+                                   C.byref(h)))
+    return h
+
+
+def snn_server_submit(sv, req: snn_request) -> int:
+    i = C.c_uint64()
+    _check(lib().snn_server_submit(sv, C.byref(req), C.byref(i)))
+    return i.value
+
+
+def snn_server_step(sv) -> int:
+    n = C.c_int32()
+    _check(lib().snn_server_step(sv, C.byref(n)))
+    return n.value
+
+
+def snn_server_poll(sv, rid: int) -> snn_result:
+    r = snn_result()
+    _check(lib().snn_server_poll(sv, rid, C.byref(r)))
+    return r
+
+
+def snn_server_spikes(sv, rid: int):
+    n = C.c_uint64()
+    rc = lib().snn_server_spikes(sv, rid, None, None, 0, C.byref(n))
+    if rc not in (SNN_OK, SNN_E_OVERFLOW):
+        _check(rc)
+    src = np.zeros(max(n.value, 1), np.uint32)
+    t = np.zeros(max(n.value, 1), np.int32)
+    _check(lib().snn_server_spikes(sv, rid, src.ctypes.data, t.ctypes.data,
+                                   n.value, C.byref(n)))
+    return src[:n.value], t[:n.value]
+
+
+def snn_server_release(sv, rid: int):
+    _check(lib().snn_server_release(sv, rid))
+
+
+def snn_server_get_stats(sv) -> snn_server_stats:
+    st = snn_server_stats()
+    _check(lib().snn_server_get_stats(sv, C.byref(st)))
+    return st
+
+
+def snn_server_destroy(sv):
+    _check(lib().snn_server_destroy(sv))
+
+
+def request(params: snn_params, conn: snn_conn_params, n_steps: int,
+            user_tag: int = 0, record_spikes: bool = False) -> snn_request:
+    r = snn_request()
+    r.params = params
+    r.conn = conn
+    r.n_steps = n_steps
+    r.user_tag = user_tag
+    r.record_spikes = int(record_spikes)
+    return r
