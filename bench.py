@@ -59,6 +59,9 @@ WORKLOADS = {
                            0, 150.0, "deliver"),
 }
 DEFAULT = "balanced-112500-fp32"
+# serving: a Poisson stream of independent balanced nets (BF16 records,
+# N log-uniform in [1,250, 112,500], 100 ms - 1 s each), mean rate in req/s
+SERVE_WORKLOADS = {"serve-poisson-20": 20.0}
 
 
 # ---------------------------------------------------------------------------
@@ -447,13 +450,249 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+def serve_requests(snn, stream_reqs, fmt, nu_ext, record, seed_offset=0):
+    out = []
+    for i, r in enumerate(stream_reqs):
+        wl = r.net
+        p = snn.params(n_exc=wl.n_e, n_inh=wl.n_i, weight_format=fmt,
+                       seed=r.seed + seed_offset, nu_ext=nu_ext)
+        w_e = snn.snn_psc_weight_for_psp(p, wl.psp_mv)
+        p.w_ext = w_e
+        c = snn.conn_params(k_exc=wl.k_e, k_inh=wl.k_i, w_exc=w_e,
+                            w_inh=-wl.g * w_e, sd_exc=wl.sd_rel * w_e,
+                            sd_inh=wl.sd_rel * wl.g * w_e, d_lo=wl.d_lo,
+                            d_hi=wl.d_hi, seed=r.seed + seed_offset + 1000,
+                            clip_exc=1, clip_inh=0)
+        out.append(snn.request(p, c, int(round(wl.bio_ms / 0.1)), user_tag=i,
+                               record_spikes=record))
+    return out
+
+
+def _lat_stats(lat):
+    a = np.sort(np.asarray(lat)) * 1e3
+    return {"p50_ms": float(np.percentile(a, 50)),
+            "p99_ms": float(np.percentile(a, 99)),
+            "max_ms": float(a[-1]), "mean_ms": float(a.mean())}
+
+
+def serve_batched(snn, reqs, arrivals, budget, stream, clocks=None):
+    """Continuous batching: submit each request at its arrival time, step the
+    server until every request finished.  Latency = completion - arrival."""
+    sv = snn.snn_server_create(budget, reqs[0].params.weight_format, stream)
+    try:
+        ids, lag = [], []
+        if clocks:
+            clocks.start()
+        t0 = time.perf_counter()
+        nxt, n = 0, len(reqs)
+        while True:
+            now = time.perf_counter() - t0
+            while nxt < n and arrivals[nxt] <= now:
+                ids.append(snn.snn_server_submit(sv, reqs[nxt]))
+                lag.append(time.perf_counter() - t0 - arrivals[nxt])
+                nxt += 1
+            active = snn.snn_server_step(sv)
+            st = snn.snn_server_get_stats(sv)
+            if nxt == n and st.done + st.failed == n:
+                break
+            if active == 0:
+                time.sleep(1e-4)          # nothing on the GPU yet
+        wall = time.perf_counter() - t0
+        clk = clocks.stop() if clocks else None
+        res = [snn.snn_server_poll(sv, i) for i in ids]
+        if any(r.state != snn.SNN_REQ_DONE for r in res):
+            raise RuntimeError("served request failed: " + str(
+                [(r.id, r.error) for r in res if r.state != snn.SNN_REQ_DONE]))
+        lat = [r.t_done - r.t_submit + g for r, g in zip(res, lag)]
+        spikes_read = sum(r.spikes for r in res)
+        return {"wall_s": wall, "events": sum(r.events for r in res),
+                "spikes": spikes_read, "latency": _lat_stats(lat),
+                "server_steps": st.steps, "intervals": st.intervals,
+                "kernel_launches": st.kernel_launches, "gpu_ms": st.gpu_ms,
+                "intervals_per_step": st.intervals_per_step,
+                "tuned": st.tuned, "clocks": clk}
+    finally:
+        snn.snn_server_destroy(sv)
+
+
+def serve_serial(snn, reqs, arrivals, stream):
+    """The plain single-net path, one request at a time in arrival order:
+    build, snn_simulate, read the spikes back, destroy."""
+    t0 = time.perf_counter()
+    lat, events, spikes = [], 0, 0
+    for r, arr in zip(reqs, arrivals):
+        now = time.perf_counter() - t0
+        if now < arr:
+            time.sleep(arr - now)
+        p = snn.snn_params.from_buffer_copy(r.params)
+        with snn.Net(p, stream) as net:
+            net.connect_fixed_indegree(r.conn)
+            net.finalize()
+            snn.snn_simulate(net.h, r.n_steps)
+            if p.spike_log_capacity:
+                net.read_spikes()
+            st = net.stats()
+        events += st.events_delivered
+        spikes += st.spikes
+        lat.append(time.perf_counter() - t0 - arr)
+    wall = time.perf_counter() - t0
+    return {"wall_s": wall, "events": events, "spikes": spikes,
+            "latency": _lat_stats(lat)}
+
+
+def spike_log_bound(r):
+    """Spike-log capacity that holds every spike of a request (each neuron
+    fires at most once per refractory period plus one step)."""
+    n = r.params.n_exc + r.params.n_inh
+    refr = round(r.params.t_ref / r.params.h)
+    return min(n * int((r.n_steps + refr) / (refr + 1)), 1 << 22)
+
+
+def run_serve(args, rate_hz, nu_ext):
+    import torch
+    from paper_2109_12855_gb300 import snn
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    s = torch.cuda.Stream()
+    torch.cuda.set_stream(s)
+    stream = s.cuda_stream
+    stream_reqs = W.serving_stream(args.requests, rate_hz, seed=7)
+    arrivals = [r.arrival_s for r in stream_reqs]
+    zero = [0.0] * len(arrivals)
+    off = 1000000 * rank                  # replicas draw their own nets
+    bf16 = serve_requests(snn, stream_reqs, 1, nu_ext, True, off)
+    fp32 = serve_requests(snn, stream_reqs, 0, nu_ext, True, off)
+    for r in fp32:                        # the single-net path sizes its log
+        r.params.spike_log_capacity = spike_log_bound(r)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+
+    # warm-up: short runs of the first requests through both paths
+    for _ in range(max(args.warmup, 1)):
+        warm = serve_requests(snn, stream_reqs[:3], 1, nu_ext, True, off)
+        for r in warm:
+            r.n_steps = 200
+        serve_batched(snn, warm, [0.0] * 3, budget, stream)
+        warm = serve_requests(snn, stream_reqs[:3], 0, nu_ext, False, off)
+        for r in warm:
+            r.n_steps = 200
+        serve_serial(snn, warm, [0.0] * 3, stream)
+
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    if cvd.isdigit():
+        gpu_index = int(cvd)
+    barrier()
+    batched = serve_batched(snn, bf16, arrivals, budget, stream,
+                            Clocks(gpu_index))
+    serial = serve_serial(snn, fp32, arrivals, stream)
+    sat_batched = serve_batched(snn, bf16, zero, budget, stream)
+    sat_serial_bf16 = serve_serial(snn, [r for r in serve_requests(
+        snn, stream_reqs, 1, nu_ext, False, off)], zero, stream)
+    sat_serial = serve_serial(snn, fp32, zero, stream)
+    barrier()
+
+    wall, events_all, _ = reduce_over_ranks(1e3 * batched["wall_s"],
+                                            batched["events"])
+    value = events_all / (wall * 1e-3)
+    if rank != 0:
+        return
+
+    def rate(x):
+        return x["events"] / x["wall_s"]
+
+    hbm, peak_kind = peaks()
+    gpu_s = batched["gpu_ms"] * 1e-3
+    alg_bytes = 8 * batched["events"] + 32 * batched["spikes"]
+    achieved = alg_bytes / gpu_s / 1e9 if gpu_s else 0.0
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        big = max(stream_reqs, key=lambda r: r.net.n_synapses).net
+        n_t = min(args.oracle_targets, big.n)
+        ctx = oracle_sample(big, nu_ext, n_t)
+        oracle_step(ctx, big, nu_ext, 5)
+        e_c, s_c = oracle_step(ctx, big, nu_ext, args.cpu_intervals)
+        cpu = {"value": e_c / s_c, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "seconds": s_c,
+               "sample": sample_text(big, n_t, args.cpu_intervals)}
+    n_req = len(stream_reqs)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": batched["server_steps"], "warmup": args.warmup,
+        "ms_per_step": wall / max(batched["server_steps"], 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16-store/f32-accumulate", "data": "synthetic",
+        "config": {"workload": args.workload, "requests": n_req,
+                   "arrival_rate_hz": rate_hz,
+                   "neurons": [min(r.net.n for r in stream_reqs),
+                               max(r.net.n for r in stream_reqs)],
+                   "synapses_total": sum(r.net.n_synapses for r in stream_reqs),
+                   "bio_ms_total": sum(r.net.bio_ms for r in stream_reqs),
+                   "nu_ext_hz": nu_ext, "mem_budget_bytes": budget,
+                   "step": "one server step: every running net advances by "
+                           "the autotuned number of intervals",
+                   "l2": "inputs larger than L2 (the resident stores total "
+                         "several GB, streamed every interval)",
+                   "parallelism": f"replicas x{ws}"},
+        "latency": batched["latency"],
+        "serving": {
+            "batched_bf16": {"events_per_s": rate(batched), **batched},
+            "serial_fp32": {"events_per_s": rate(serial), **serial},
+            "saturated": {
+                "batched_bf16": {"events_per_s": rate(sat_batched),
+                                 "wall_s": sat_batched["wall_s"],
+                                 "latency": sat_batched["latency"],
+                                 "intervals_per_step":
+                                     sat_batched["intervals_per_step"]},
+                "serial_bf16": {"events_per_s": rate(sat_serial_bf16),
+                                "wall_s": sat_serial_bf16["wall_s"],
+                                "latency": sat_serial_bf16["latency"]},
+                "serial_fp32": {"events_per_s": rate(sat_serial),
+                                "wall_s": sat_serial["wall_s"],
+                                "latency": sat_serial["latency"]}}},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_source": peak_kind, "traffic": None,
+                     "kernel": "k_update_batch + k_deliver_tiled_batch "
+                               "(GPU time of the server steps)",
+                     "bytes_per_event": 8},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": UNIT,
+                "h2d_bytes_per_step": int(n_req * ctypes_size(snn.snn_request)
+                                          / max(batched["server_steps"], 1)),
+                "d2h_bytes_per_step": int(8 * batched["spikes"]
+                                          / max(batched["server_steps"], 1)),
+                "note": "the serving value is already end to end: requests "
+                        "enter as host structs and every spike train is read "
+                        "back to host memory inside the timed region"},
+        "gpu_launches": batched["kernel_launches"],
+        "clocks": batched["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def ctypes_size(t):
+    import ctypes
+    return ctypes.sizeof(t)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) +
+                    sorted(SERVE_WORKLOADS), default=DEFAULT)
+    ap.add_argument("--requests", type=int, default=40,
+                    help="serving workloads: requests in the stream")
     ap.add_argument("--nu-ext", type=float, default=None)
     ap.add_argument("--oracle-targets", type=int, default=4500)
     ap.add_argument("--oracle-intervals", type=int, default=100,
@@ -467,8 +706,18 @@ def main():
                     help="deliver workloads: Bernoulli lists at this rate "
                          "instead of a recorded run")
     args = ap.parse_args()
-    wl, fmt, bio_ms, kind = WORKLOADS[args.workload]
     nu_ext = args.nu_ext if args.nu_ext is not None else NU_EXT_8HZ
+    if args.workload in SERVE_WORKLOADS:
+        if args.impl == "reference":
+            big = max(W.serving_stream(args.requests), key=lambda r:
+                      r.net.n_synapses).net
+            run_reference(args, big, nu_ext)
+        else:
+            from paper_2109_12855_gb300 import build
+            build()
+            run_serve(args, SERVE_WORKLOADS[args.workload], nu_ext)
+        return
+    wl, fmt, bio_ms, kind = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl, nu_ext)
     else:

@@ -16,6 +16,10 @@ parameters follow the benchmark configurations):
 * ``BALANCED_562500`` N = 562,500 (450,000 E + 112,500 I), K = 11,250,
   delays 10..20 steps, BF16 records with weights N(J, 0.1 J) (E, clipped at 0)
   and N(-5 J, 0.5 J) (I).
+* ``serving_stream``  a Poisson stream of independent balanced nets (mean
+  20 requests/s): N log-uniform in [1,250, 112,500] with 4:1 E:I,
+  K = min(N/10, 11,250) with 4:1 E:I, BF16 records with the spread above,
+  delays 10..20 steps, 100 ms to 1 s of biological time, one seed each.
 """
 from __future__ import annotations
 
@@ -118,3 +122,31 @@ def random_state(n: int, seed: int, v_lo: float = 0.0, v_hi: float = 20.0,
     J = g.normal(0.0, 200.0, n)
     refr = np.where(g.random(n) < 0.2, g.integers(1, refr_max + 1, n), 0)
     return V, I, J, refr.astype(np.int32)
+
+
+@dataclass(frozen=True)
+class ServeRequest:
+    arrival_s: float        # offset from the start of the stream
+    net: Balanced
+    seed: int
+
+
+def serving_stream(n_requests: int, rate_hz: float = 20.0, seed: int = 7,
+                   n_lo: int = 1250, n_hi: int = 112500,
+                   bio_lo_ms: float = 100.0, bio_hi_ms: float = 1000.0):
+    """Poisson arrivals (exponential gaps of mean 1/rate_hz; all at 0 when
+    rate_hz is 0) of balanced nets with log-uniform sizes."""
+    g = rng(seed)
+    out, t = [], 0.0
+    for i in range(n_requests):
+        if rate_hz > 0 and i > 0:
+            t += g.exponential(1.0 / rate_hz)
+        n = int(round(np.exp(g.uniform(np.log(n_lo), np.log(n_hi))) / 5)) * 5
+        n = min(max(n, n_lo), n_hi)
+        k = min(n // 10, 11250)
+        k_e = k * 4 // 5
+        bio = float(round(g.uniform(bio_lo_ms, bio_hi_ms), 1))
+        net = Balanced(f"serve-{i}", n * 4 // 5, n - n * 4 // 5, k_e, k - k_e,
+                       10, 20, "bf16", 0.1, bio)
+        out.append(ServeRequest(t, net, 1000 + i))
+    return out
