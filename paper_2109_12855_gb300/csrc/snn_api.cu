@@ -137,6 +137,12 @@ int make_upd_const(const snn_params& p, UpdConst* c) {
     int n = poisson_thresholds(p.nu_ext * p.h * 1e-3, c->thr, kMaxPoisson);
     if (n < 0) return -1;
     c->n_thr = n;
+    for (int j = 0; j < 256; ++j) {
+      const uint32_t lo = (uint32_t)j << 24;
+      int k = 0;
+      while (k < n - 1 && c->thr[k] <= lo) ++k;
+      c->guide[j] = (uint8_t)k;
+    }
   }
   return 0;
 }

@@ -160,6 +160,10 @@ struct UpdConst {
   uint64_t seed;
   uint32_t thr[kMaxPoisson];  // Poisson inversion thresholds (last = 2^32-1
                               // sentinel handled by n_thr)
+  // guide[j] = number of thresholds thr[m] (m < n_thr - 1) with
+  // thr[m] <= j * 2^24: the inversion of a word in [j 2^24, (j+1) 2^24)
+  // starts its search there (the result is that of the plain search)
+  uint8_t guide[256];
 };
 
 // Device view of one net.

@@ -145,8 +145,10 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
                                             int n_steps, int from_ctl,
                                             long long t0_arg, uint32_t block) {
   __shared__ uint32_t s_thr[kMaxPoisson];
+  __shared__ uint8_t s_guide[256];
   __shared__ unsigned long long s_base[2];
   for (int k = threadIdx.x; k < c.n_thr; k += blockDim.x) s_thr[k] = c.thr[k];
+  for (int k = threadIdx.x; k < 256; k += blockDim.x) s_guide[k] = c.guide[k];
   const long long t0 = from_ctl ? v.ctl->t_now : t0_arg;
   if (block == 0 && threadIdx.x == 0) {
     v.ctl->iv_steps = n_steps;
@@ -171,6 +173,7 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
   }
   U4 rnd{0, 0, 0, 0};
   long long rnd_block = -1;
+  float* const rb_i = v.rb + i;  // slot s of neuron i at rb_i[s * pitch]
 
   for (int s0 = 0; s0 < n_steps; s0 += 32) {
     const int ns = n_steps - s0 < 32 ? n_steps - s0 : 32;
@@ -179,26 +182,35 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
       // ring-buffer values and drive counts of up to eight steps, computed
       // before the (sequential) integration so they do not lengthen it
       float buf[kPrefetch];
+      const long long tf = t0 + s0 + sb;  // first step of this group
+      const int ng = ns - sb < kPrefetch ? ns - sb : kPrefetch;
 #pragma unroll
       for (int q = 0; q < kPrefetch; ++q) {
         buf[q] = 0.f;
-        if (live && sb + q < ns)
-          buf[q] = v.rb[(size_t)((uint32_t)(t0 + s0 + sb + q) & v.slot_mask) *
-                            v.pitch + i];
+        if (live && q < ng)
+          buf[q] = rb_i[((uint32_t)(tf + q) & v.slot_mask) * v.pitch];
       }
       if (c.n_thr > 0 && live) {
+        // the group's steps lie in the 4-step draw blocks b0 .. b0 + 2;
+        // the draws are independent of one another (issued together), and
+        // the block drawn last is kept for the next group
+        const long long b0 = tf >> 2, bl = (tf + ng - 1) >> 2;
+        const U4 r0 = b0 == rnd_block ? rnd : draw(c.seed, i, (uint64_t)b0, 2u);
+        U4 r1 = r0, r2 = r0;
+        if (bl >= b0 + 1) r1 = draw(c.seed, i, (uint64_t)(b0 + 1), 2u);
+        if (bl >= b0 + 2) r2 = draw(c.seed, i, (uint64_t)(b0 + 2), 2u);
+        rnd = bl == b0 ? r0 : bl == b0 + 1 ? r1 : r2;
+        rnd_block = bl;
+        const uint32_t wd[12] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y,
+                                 r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
+        const int a = (int)(tf & 3);
 #pragma unroll
         for (int q = 0; q < kPrefetch; ++q) {
-          if (sb + q >= ns) continue;
-          const long long t = t0 + s0 + sb + q;
-          const long long blk = t >> 2;
-          if (blk != rnd_block) {
-            rnd = draw(c.seed, i, (uint64_t)blk, 2u);
-            rnd_block = blk;
-          }
-          const uint32_t w = (t & 3) == 0 ? rnd.x : (t & 3) == 1 ? rnd.y
-                           : (t & 3) == 2 ? rnd.z : rnd.w;
-          int k = 0;
+          if (q >= ng) continue;
+          // word (tf + q) mod 4 of block (tf + q) / 4: wd[a + q]
+          const uint32_t w = a == 0 ? wd[q] : a == 1 ? wd[q + 1]
+                           : a == 2 ? wd[q + 2] : wd[q + 3];
+          int k = s_guide[w >> 24];
           while (k < c.n_thr - 1 && w >= s_thr[k]) ++k;
           buf[q] += c.w_ext * (float)k;
         }
@@ -215,7 +227,7 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
         J = c.p11 * J;
         // (3) this step's ring-buffer input (read above; the slot is
         // cleared here) plus drive
-        v.rb[(size_t)((uint32_t)t & v.slot_mask) * v.pitch + i] = 0.0f;
+        rb_i[((uint32_t)t & v.slot_mask) * v.pitch] = 0.0f;
         J += c.psc * buf[q];
         // (4) threshold
         if (V >= c.v_th) {
