@@ -395,7 +395,10 @@ typedef struct snn_server_stats {
 int snn_server_create(uint64_t mem_budget, int32_t weight_format,
                       void* stream, snn_server** out);
 /* Queue a request; *id identifies it.  Thread-safe.  SNN_E_ARG for invalid
- * parameters or a footprint above the whole budget. */
+ * parameters or a footprint above the whole budget.  A request with
+ * params.tile_width == 0 gets delivery tiles in proportion to its synapses
+ * (about one per 4.2e6, at most one per SM), since all served nets share
+ * each delivery launch. */
 int snn_server_submit(snn_server* sv, const snn_request* req, uint64_t* id);
 /* Admit built nets, advance all running nets by one step (the autotuned
  * number of intervals), retire finished ones.  *n_active (optional): nets

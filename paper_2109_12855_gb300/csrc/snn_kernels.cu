@@ -714,23 +714,35 @@ __device__ __forceinline__ void deliver_tile_body(
     __syncthreads();  // s_desc is rewritten by the next batch
   }
   if (inwin) {
-    for (uint32_t sl = 0; sl < W; ++sl) {
-      const uint32_t slot = (uint32_t)(base + sl) & v.slot_mask;
-      float* row = v.rb + (size_t)slot * v.pitch + tgt_lo;
-      for (uint32_t x = threadIdx.x; x < TW; x += blockDim.x) {
-        if (tgt_lo + x >= v.n) continue;
-        const uint32_t c = sl * TW + x;
-        float a;
-        if (fx.fixed) {
-          const int H = accH[c], L = accL[c];
-          if ((H | L) == 0) continue;
-          const long long T = ((long long)H << fx.sh) + (long long)L;
-          a = (float)((double)T * fx.inv_q);
-        } else {
-          a = accF[c];
-          if (a == 0.f) continue;
+    // each thread owns whole target columns; the ring-buffer reads of
+    // kFlush slots are issued together, then the sums are written back
+    // (one memory round trip per kFlush slots, not one per slot)
+    constexpr uint32_t kFlush = 8;
+    for (uint32_t x = threadIdx.x; x < TW && tgt_lo + x < v.n; x += blockDim.x) {
+      float* const col = v.rb + tgt_lo + x;
+      for (uint32_t sl0 = 0; sl0 < W; sl0 += kFlush) {
+        float a[kFlush], old[kFlush];
+        uint32_t off[kFlush];
+#pragma unroll
+        for (uint32_t q = 0; q < kFlush; ++q) {
+          a[q] = 0.f;
+          off[q] = ((uint32_t)(base + sl0 + q) & v.slot_mask) * v.pitch;
+          if (sl0 + q < W) {
+            const uint32_t c = (sl0 + q) * TW + x;
+            if (fx.fixed) {
+              const long long T = ((long long)accH[c] << fx.sh) + (long long)accL[c];
+              a[q] = (float)((double)T * fx.inv_q);
+            } else {
+              a[q] = accF[c];
+            }
+          }
         }
-        row[x] += a;
+#pragma unroll
+        for (uint32_t q = 0; q < kFlush; ++q)
+          old[q] = a[q] != 0.f ? col[off[q]] : 0.f;
+#pragma unroll
+        for (uint32_t q = 0; q < kFlush; ++q)
+          if (a[q] != 0.f) col[off[q]] = old[q] + a[q];
       }
     }
   }

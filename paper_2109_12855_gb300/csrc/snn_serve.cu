@@ -59,6 +59,10 @@ int sfail(int code, const char* fmt, ...) {
 constexpr int kTuneCandidates[] = {1, 2, 4, 8};
 constexpr int kTuneStepsPerCandidate = 4;
 constexpr uint64_t kLogCapMax = 1ull << 22;  // recorded spikes per request
+// Served nets share each delivery launch, so a net gets tiles in proportion
+// to its synapses (one per kSynPerTile, at most one per SM) rather than one
+// per SM: small nets then add few CTAs of fixed per-CTA cost to the batch.
+constexpr uint64_t kSynPerTile = 1ull << 22;
 
 double now_s() {
   using namespace std::chrono;
@@ -132,6 +136,17 @@ namespace {
 // Device bytes a request will hold (the store with its build keys, tile
 // index, ring buffer, state, interval list, spike log), plus slack for the
 // allocator's granularity.
+int32_t serve_tile_width(const snn_request& r) {
+  const uint64_t n = (uint64_t)r.params.n_exc + r.params.n_inh;
+  const uint64_t n_syn = n * ((uint64_t)r.conn.k_exc + r.conn.k_inh);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint64_t tiles = (n_syn + kSynPerTile - 1) / kSynPerTile;
+  tiles = std::min<uint64_t>(std::max<uint64_t>(tiles, 1), (uint64_t)std::max(sms, 1));
+  return (int32_t)std::min<uint64_t>((n + tiles - 1) / tiles, 1u << 30);
+}
+
 uint64_t estimate_bytes(const snn_request& r, int fmt) {
   const uint64_t n = (uint64_t)r.params.n_exc + r.params.n_inh;
   const uint64_t k = (uint64_t)r.conn.k_exc + r.conn.k_inh;
@@ -425,6 +440,7 @@ int snn_server_submit(snn_server* sv, const snn_request* req, uint64_t* id) {
   } else {
     q.r.params.spike_log_capacity = 0;
   }
+  if (q.r.params.tile_width == 0) q.r.params.tile_width = serve_tile_width(q.r);
   q.est = estimate_bytes(q.r, sv->fmt);
   SREQ(q.est <= sv->budget, SNN_E_ARG,
        "request needs about %llu bytes, above the server budget",
