@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -157,16 +158,76 @@ void snn::set_last_error(const char* msg) { g_err = msg; }
 
 namespace {
 
-template <class T>
-cudaError_t dalloc(T** p, size_t bytes) {
-  *p = nullptr;
-  if (bytes == 0) bytes = 16;
-  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+// Device memory of the library comes from one stream-ordered pool per
+// device (allocations and frees are ordered on the net's stream, so freeing
+// never synchronises the device); freed blocks stay in the pool for the next
+// net and are returned to the device when the last net is destroyed.
+struct DevicePools {
+  std::mutex mu;
+  cudaMemPool_t pool[64] = {};
+  int live[64] = {};
+};
+DevicePools& pools() {
+  static DevicePools p;
+  return p;
 }
 
-void dfree(void* p) {
-  if (p) cudaFree(p);
+cudaMemPool_t device_pool(int dev) {
+  if (dev < 0 || dev >= 64) return nullptr;
+  DevicePools& P = pools();
+  std::lock_guard<std::mutex> lk(P.mu);
+  if (!P.pool[dev]) {
+    cudaMemPoolProps pr;
+    memset(&pr, 0, sizeof pr);
+    pr.allocType = cudaMemAllocationTypePinned;
+    pr.handleTypes = cudaMemHandleTypeNone;
+    pr.location.type = cudaMemLocationTypeDevice;
+    pr.location.id = dev;
+    cudaMemPool_t mp = nullptr;
+    if (cudaMemPoolCreate(&mp, &pr) != cudaSuccess) return nullptr;
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
+    P.pool[dev] = mp;
+  }
+  return P.pool[dev];
 }
+
+void count_net(int dev, int delta, cudaStream_t s) {
+  if (dev < 0 || dev >= 64) return;
+  DevicePools& P = pools();
+  std::lock_guard<std::mutex> lk(P.mu);
+  P.live[dev] += delta;
+  if (P.live[dev] == 0 && P.pool[dev]) {
+    cudaStreamSynchronize(s);  // its frees are done
+    cudaMemPoolTrimTo(P.pool[dev], 0);
+  }
+}
+
+}  // namespace
+
+cudaError_t snn::pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t mp = device_pool(dev);
+  if (!mp) return cudaErrorMemoryAllocation;
+  return cudaMallocFromPoolAsync(p, bytes, mp, s);
+}
+
+void snn::pool_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(T** p, size_t bytes, cudaStream_t s) {
+  return snn::pool_alloc(reinterpret_cast<void**>(p), bytes, s);
+}
+
+void dfree(void* p, cudaStream_t s) { snn::pool_free(p, s); }
 
 cudaMemcpyKind kind_to(int mem) {
   return mem == SNN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -273,17 +334,17 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
   const uint32_t ch = (uint32_t)chunk_records(net->fmt);
   const uint64_t padded = (n_syn + ch - 1) / ch * ch + ch;
   const int rec_bytes = net->fmt == SNN_W_FP32_12B ? 12 : 8;
-  CK(dalloc(&net->row_ptr, (n + 1) * sizeof(uint64_t)));
+  CK(dalloc(&net->row_ptr, (n + 1) * sizeof(uint64_t), net->stream));
   CK(cudaMemcpyAsync(net->row_ptr, rp.data(), (n + 1) * sizeof(uint64_t),
                      cudaMemcpyHostToDevice, s));
   // tiles sized for the widest window the interval can reach
   const int iv = net->p.interval ? net->p.interval : d_lo;
   choose_tiles(n, iv + (d_hi - d_lo), net->p.tile_width, &net->tile_w,
                &net->lo_bits, &net->n_tiles);
-  CK(dalloc(&net->tile_off, (uint64_t)n * (net->n_tiles + 1) * sizeof(uint32_t)));
+  CK(dalloc(&net->tile_off, (uint64_t)n * (net->n_tiles + 1) * sizeof(uint32_t), net->stream));
   // keys; for 8-byte records the key array becomes the record array
   uint64_t* keys = nullptr;
-  CK(dalloc(&keys, padded * sizeof(uint64_t)));
+  CK(dalloc(&keys, padded * sizeof(uint64_t), net->stream));
   uint32_t* cursor = d_deg;  // reuse as the scatter cursor
   CK(cudaMemsetAsync(cursor, 0, n * sizeof(uint32_t), s));
   CK(scatter(net->row_ptr, cursor, keys, net->tile_w, net->lo_bits));
@@ -291,9 +352,9 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
   if (rec_bytes == 8) {
     recs = keys;
   } else {
-    cudaError_t e = dalloc(&recs, padded * rec_bytes);
+    cudaError_t e = dalloc(&recs, padded * rec_bytes, net->stream);
     if (e != cudaSuccess) {
-      dfree(keys);
+      dfree(keys, net->stream);
       return fail(SNN_E_OOM, "store allocation of %llu bytes failed",
                   (unsigned long long)(padded * rec_bytes));
     }
@@ -304,9 +365,9 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
   uint32_t* d_long = nullptr;
   uint64_t *d_loff = nullptr, *d_scr = nullptr;
   if (!long_rows.empty()) {
-    CK(dalloc(&d_long, long_rows.size() * sizeof(uint32_t)));
-    CK(dalloc(&d_loff, long_off.size() * sizeof(uint64_t)));
-    CK(dalloc(&d_scr, scratch * sizeof(uint64_t)));
+    CK(dalloc(&d_long, long_rows.size() * sizeof(uint32_t), net->stream));
+    CK(dalloc(&d_loff, long_off.size() * sizeof(uint64_t), net->stream));
+    CK(dalloc(&d_scr, scratch * sizeof(uint64_t), net->stream));
     CK(cudaMemcpyAsync(d_long, long_rows.data(),
                        long_rows.size() * sizeof(uint32_t),
                        cudaMemcpyHostToDevice, s));
@@ -315,7 +376,7 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
                        cudaMemcpyHostToDevice, s));
   }
   uint32_t* d_stats = nullptr;
-  CK(dalloc(&d_stats, 2 * sizeof(uint32_t)));
+  CK(dalloc(&d_stats, 2 * sizeof(uint32_t), net->stream));
   CK(cudaMemsetAsync(d_stats, 0, 2 * sizeof(uint32_t), s));
   CK(build_sort_pack(net->fmt, n, net->row_ptr, keys, recs, bf, d_edge_w,
                      max_row, d_long, (uint32_t)long_rows.size(), d_scr,
@@ -324,13 +385,13 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
   uint32_t h_stats[2] = {0, 0};
   CK(cudaMemcpyAsync(h_stats, d_stats, sizeof h_stats, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  dfree(d_stats);
+  dfree(d_stats, net->stream);
   net->mult_max = h_stats[0];
   memcpy(&net->max_abs_w, &h_stats[1], sizeof(float));
-  if (recs != keys) dfree(keys);
-  dfree(d_long);
-  dfree(d_loff);
-  dfree(d_scr);
+  if (recs != keys) dfree(keys, net->stream);
+  dfree(d_long, net->stream);
+  dfree(d_loff, net->stream);
+  dfree(d_scr, net->stream);
   net->recs = recs;
   net->n_syn = n_syn;
   net->recs_bytes = padded * rec_bytes;
@@ -341,16 +402,16 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
 int ensure_ext(snn_net* net, uint64_t n) {
   if (n <= net->ext_cap) return SNN_OK;
   uint64_t cap = std::max<uint64_t>(n, 2 * net->ext_cap);
-  dfree(net->ext_list);
-  dfree(net->ext_src);
-  dfree(net->ext_t);
+  dfree(net->ext_list, net->stream);
+  dfree(net->ext_src, net->stream);
+  dfree(net->ext_t, net->stream);
   net->ext_list = nullptr;
   net->ext_src = nullptr;
   net->ext_t = nullptr;
   net->ext_cap = 0;
-  CK(dalloc(&net->ext_list, cap * sizeof(SpikeEntry)));
-  CK(dalloc(&net->ext_src, cap * sizeof(uint32_t)));
-  CK(dalloc(&net->ext_t, cap * sizeof(int32_t)));
+  CK(dalloc(&net->ext_list, cap * sizeof(SpikeEntry), net->stream));
+  CK(dalloc(&net->ext_src, cap * sizeof(uint32_t), net->stream));
+  CK(dalloc(&net->ext_t, cap * sizeof(int32_t), net->stream));
   net->ext_cap = cap;
   return SNN_OK;
 }
@@ -491,6 +552,8 @@ int snn_create(const snn_params* p, void* stream, snn_net** out) {
   };
   if (cudaGetDevice(&net->device) != cudaSuccess)
     return bail(fail(SNN_E_CUDA, "no CUDA device"));
+  count_net(net->device, +1, nullptr);
+  net->counted = true;
   if (stream) {
     net->stream = static_cast<cudaStream_t>(stream);
   } else {
@@ -504,7 +567,7 @@ int snn_create(const snn_params* p, void* stream, snn_net** out) {
   const size_t rb_bytes = (size_t)net->n_slots * net->pitch * sizeof(float);
 #define ALLOC(ptr, bytes)                                                   \
   do {                                                                      \
-    if (dalloc(&(ptr), (bytes)) != cudaSuccess)                             \
+    if (dalloc(&(ptr), (bytes), net->stream) != cudaSuccess)                  \
       return bail(fail(SNN_E_OOM, "allocation of %zu bytes failed",        \
                        (size_t)(bytes)));                                   \
   } while (0)
@@ -561,11 +624,11 @@ int snn_connect_fixed_indegree(snn_net* net, const snn_conn_params* c) {
   b.clip_e = c->clip_exc;
   b.clip_i = c->clip_inh;
   uint32_t* deg = nullptr;
-  CK(dalloc(&deg, net->n * sizeof(uint32_t)));
+  CK(dalloc(&deg, net->n * sizeof(uint32_t), net->stream));
   CK(cudaMemsetAsync(deg, 0, net->n * sizeof(uint32_t), net->stream));
   cudaError_t e = build_count_fixed(b, deg, net->stream);
   if (e != cudaSuccess) {
-    dfree(deg);
+    dfree(deg, net->stream);
     CK(e);
   }
   cudaStream_t s = net->stream;
@@ -574,7 +637,7 @@ int snn_connect_fixed_indegree(snn_net* net, const snn_conn_params* c) {
       [&](const uint64_t* rp, uint32_t* cur, uint64_t* keys, uint32_t tw,
           int lb) { return build_scatter_fixed(b, rp, cur, keys, tw, lb, s); },
       &b, nullptr, c->d_lo, c->d_hi);
-  dfree(deg);
+  dfree(deg, net->stream);
   net->launches += 3;
   net->k_in_max = c->k_exc + c->k_inh;
   return rc;
@@ -633,11 +696,11 @@ int snn_connect_edges(snn_net* net, const uint32_t* src, const uint32_t* tgt,
   uint32_t *d_src = nullptr, *d_tgt = nullptr, *deg = nullptr;
   uint8_t* d_del = nullptr;
   double* d_w = nullptr;
-  CK(dalloc(&d_src, n * 4));
-  CK(dalloc(&d_tgt, n * 4));
-  CK(dalloc(&d_del, n));
-  CK(dalloc(&d_w, n * 8));
-  CK(dalloc(&deg, net->n * sizeof(uint32_t)));
+  CK(dalloc(&d_src, n * 4, net->stream));
+  CK(dalloc(&d_tgt, n * 4, net->stream));
+  CK(dalloc(&d_del, n, net->stream));
+  CK(dalloc(&d_w, n * 8, net->stream));
+  CK(dalloc(&deg, net->n * sizeof(uint32_t), net->stream));
   if (n) {
     CK(cudaMemcpyAsync(d_src, ps, n * 4, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(d_tgt, pt, n * 4, cudaMemcpyHostToDevice, s));
@@ -654,11 +717,11 @@ int snn_connect_edges(snn_net* net, const uint32_t* src, const uint32_t* tgt,
                                    lb, s);
       },
       nullptr, d_w, e_lo, e_hi);
-  dfree(d_src);
-  dfree(d_tgt);
-  dfree(d_del);
-  dfree(d_w);
-  dfree(deg);
+  dfree(d_src, net->stream);
+  dfree(d_tgt, net->stream);
+  dfree(d_del, net->stream);
+  dfree(d_w, net->stream);
+  dfree(deg, net->stream);
   net->launches += 3;
   net->k_in_max = k_in_max;
   return rc;
@@ -672,21 +735,21 @@ int snn_finalize(snn_net* net) {
   cudaStream_t s = net->stream;
   if (!net->connected) {
     // a net without synapses: empty store
-    CK(dalloc(&net->row_ptr, (net->n + 1) * sizeof(uint64_t)));
+    CK(dalloc(&net->row_ptr, (net->n + 1) * sizeof(uint64_t), net->stream));
     CK(cudaMemsetAsync(net->row_ptr, 0, (net->n + 1) * sizeof(uint64_t), s));
-    CK(dalloc(&net->recs, 4096));
+    CK(dalloc(&net->recs, 4096, net->stream));
     CK(cudaMemsetAsync(net->recs, 0, 4096, s));
     net->n_syn = 0;
     net->connected = true;
   }
   unsigned* dd = nullptr;
   unsigned h[2] = {0xFFFFFFFFu, 0u};
-  CK(dalloc(&dd, 2 * sizeof(unsigned)));
+  CK(dalloc(&dd, 2 * sizeof(unsigned), net->stream));
   CK(cudaMemcpyAsync(dd, h, sizeof h, cudaMemcpyHostToDevice, s));
   CK(delay_range(net->fmt, net->recs, net->n_syn, dd, s));
   CK(cudaMemcpyAsync(h, dd, sizeof h, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  dfree(dd);
+  dfree(dd, net->stream);
   net->dmin = net->n_syn ? (int)h[0] : 0;
   net->dmax = net->n_syn ? (int)h[1] : 0;
   int iv = net->p.interval;
@@ -701,7 +764,7 @@ int snn_finalize(snn_net* net) {
   net->spikes_per_iv =
       (uint32_t)((iv + net->uc.refr_steps) / (net->uc.refr_steps + 1));
   net->list_cap = (uint64_t)net->n * iv;
-  CK(dalloc(&net->list, net->list_cap * sizeof(SpikeEntry)));
+  CK(dalloc(&net->list, net->list_cap * sizeof(SpikeEntry), net->stream));
   (void)deliver_grid_size(net->fmt);
   CK(cudaGetLastError());
   net->finalized = true;
@@ -1027,17 +1090,17 @@ int snn_read_store(snn_net* net, uint64_t* row_ptr, uint32_t* tgt,
       uint32_t* dt = nullptr;
       uint8_t* dd = nullptr;
       float* dw = nullptr;
-      CK(dalloc(&dt, m * 4));
-      CK(dalloc(&dd, m));
-      CK(dalloc(&dw, m * 4));
+      CK(dalloc(&dt, m * 4, net->stream));
+      CK(dalloc(&dd, m, net->stream));
+      CK(dalloc(&dw, m * 4, net->stream));
       CK(unpack_store(net->fmt, net->recs, m, dt, dd, dw, s));
       if (tgt) CK(cudaMemcpyAsync(tgt, dt, m * 4, cudaMemcpyDeviceToHost, s));
       if (delay) CK(cudaMemcpyAsync(delay, dd, m, cudaMemcpyDeviceToHost, s));
       if (w) CK(cudaMemcpyAsync(w, dw, m * 4, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      dfree(dt);
-      dfree(dd);
-      dfree(dw);
+      dfree(dt, net->stream);
+      dfree(dd, net->stream);
+      dfree(dw, net->stream);
     }
     net->launches += 1;
   }
@@ -1222,7 +1285,8 @@ int snn_destroy(snn_net* net) {
                   net->rb,       net->counts,   net->ctl,     net->row_ptr,
                   net->recs,     net->list,     net->ext_list, net->ext_src,
                   net->ext_t,    net->log_src,  net->log_t,   net->tile_off};
-  for (void* b : bufs) dfree(b);
+  for (void* b : bufs) dfree(b, net->stream);
+  if (net->counted) count_net(net->device, -1, net->stream);
   if (net->own_stream) cudaStreamDestroy(net->stream);
   delete net;
   return SNN_OK;

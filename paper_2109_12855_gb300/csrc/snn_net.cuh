@@ -17,12 +17,18 @@ void set_last_error(const char* msg);
 // Tile geometry the store builder uses for n targets (see snn_api.cu).
 void tile_geometry(uint32_t n, int window, int32_t hint, uint32_t* tile_w,
                    int* lo_bits, uint32_t* n_tiles);
+// Device memory from the library's stream-ordered pool of the current
+// device (see snn_api.cu); free with pool_free on a stream ordered after
+// the last use.
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
+void pool_free(void* p, cudaStream_t s);
 }  // namespace snn
 
 // The net: parameters, device buffers and host bookkeeping.
 struct snn_net {
   snn_params p{};
   cudaStream_t stream = nullptr;
+  bool counted = false;  // counted among the device's live nets
   bool own_stream = false;
   int device = 0;
   uint32_t n = 0, pitch = 0;

@@ -215,12 +215,13 @@ void builder_main(snn_server* sv) {
 }
 
 template <class T>
-int ensure_dev(T** p, size_t* cap, size_t n) {
+int ensure_dev(T** p, size_t* cap, size_t n, cudaStream_t s) {
   if (n <= *cap) return SNN_OK;
-  if (*p) cudaFree(*p);
+  const size_t c = std::max<size_t>(n, 2 * *cap);
+  pool_free(*p, s);
   *p = nullptr;
-  size_t c = std::max<size_t>(n, 2 * *cap);
-  SCK(cudaMalloc(reinterpret_cast<void**>(p), c * sizeof(T)));
+  *cap = 0;
+  SCK(pool_alloc(reinterpret_cast<void**>(p), c * sizeof(T), s));
   *cap = c;
   return SNN_OK;
 }
@@ -246,9 +247,9 @@ int rebuild_tables(snn_server* sv) {
     smem = std::max(smem, tiled_smem_bytes(nets[k].v));
   }
   int rc;
-  if ((rc = ensure_dev(&sv->d_nets, &sv->cap_nets, nets.size())) != SNN_OK) return rc;
-  if ((rc = ensure_dev(&sv->d_umap, &sv->cap_umap, umap.size())) != SNN_OK) return rc;
-  if ((rc = ensure_dev(&sv->d_dmap, &sv->cap_dmap, dmap.size())) != SNN_OK) return rc;
+  if ((rc = ensure_dev(&sv->d_nets, &sv->cap_nets, nets.size(), sv->stream)) != SNN_OK) return rc;
+  if ((rc = ensure_dev(&sv->d_umap, &sv->cap_umap, umap.size(), sv->stream)) != SNN_OK) return rc;
+  if ((rc = ensure_dev(&sv->d_dmap, &sv->cap_dmap, dmap.size(), sv->stream)) != SNN_OK) return rc;
   SCK(cudaMemcpyAsync(sv->d_nets, nets.data(), nets.size() * sizeof(BatchNet),
                       cudaMemcpyHostToDevice, sv->stream));
   SCK(cudaMemcpyAsync(sv->d_umap, umap.data(), umap.size() * sizeof(uint2),
@@ -622,9 +623,10 @@ int snn_server_destroy(snn_server* sv) {
   for (auto& pair : sv->ev)
     for (cudaEvent_t e : pair)
       if (e) cudaEventDestroy(e);
-  if (sv->d_nets) cudaFree(sv->d_nets);
-  if (sv->d_umap) cudaFree(sv->d_umap);
-  if (sv->d_dmap) cudaFree(sv->d_dmap);
+  pool_free(sv->d_nets, sv->stream);
+  pool_free(sv->d_umap, sv->stream);
+  pool_free(sv->d_dmap, sv->stream);
+  if (sv->stream) cudaStreamSynchronize(sv->stream);
   if (sv->own_stream) cudaStreamDestroy(sv->stream);
   delete sv;
   return SNN_OK;
