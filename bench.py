@@ -59,6 +59,14 @@ WORKLOADS = {
                            0, 150.0, "deliver"),
 }
 DEFAULT = "balanced-112500-fp32"
+# DRAM bytes (read + write) per synaptic event of k_deliver_tiled, summed by
+# ncu over all 667 launches of one timed step of the workload and divided by
+# that step's events (profiles/dram_k_deliver_tiled_balanced-112500-fp32.md).
+# It stands for the kernel it was measured on: the entry is used only while
+# the kernel sources hash to the recorded prefix.
+TRAFFIC_B_PER_EVENT = {
+    "balanced-112500-fp32": (12.550, "9acc9eb59ec9b11d", "d40e515e507ce391"),
+}
 # serving: a Poisson stream of independent balanced nets (BF16 records,
 # N log-uniform in [1,250, 112,500], 100 ms - 1 s each), mean rate in req/s
 SERVE_WORKLOADS = {"serve-poisson-20": 20.0}
@@ -250,6 +258,22 @@ def build_net(wl, fmt, nu_ext, seed, stream, log_cap=0, deliver_mode=0):
     return net, w_e
 
 
+def kernel_sources_hash():
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2109_12855_gb300", "csrc")
+    return tuple(hashlib.sha256(open(os.path.join(csrc, f), "rb").read())
+                 .hexdigest()[:16] for f in ("snn_kernels.cu", "snn_internal.cuh"))
+
+
+def measured_traffic(workload, events_per_launch):
+    """ncu-measured DRAM bytes per launch of the delivery kernel, or None
+    when there is no capture for this workload or the kernel has changed."""
+    ent = TRAFFIC_B_PER_EVENT.get(workload)
+    if ent is None or kernel_sources_hash() != ent[1:]:
+        return None
+    return ent[0] * events_per_launch
+
+
 def timed(torch, stream, fn, k):
     """Run fn k times between events on the library's stream; ms total."""
     barrier()
@@ -424,6 +448,7 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
                    "bio_ms_per_step": bio_ms, "nu_ext_hz": nu_ext,
                    "mean_rate_hz": spikes_all / ws / wl.n / (
                        args.steps * bio_ms * 1e-3),
+                   "events_timed": events_all, "spikes_timed": int(spikes_all),
                    "build_s": t_build,
                    "l2": "inputs larger than L2 (the record store is "
                          f"{wl.n_synapses * rec_bytes / 1e9:.1f} GB, streamed "
@@ -432,7 +457,12 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm,
                      "peak_source": peak_kind,
-                     "traffic": None, "kernel": "k_deliver",
+                     "traffic": measured_traffic(args.workload,
+                                                 ev_prof / max(n_del, 1)),
+                     "traffic_unit": "bytes per launch (ncu dram read+write)",
+                     "algorithmic_bytes_per_launch": per_launch_bytes,
+                     "kernel": "k_deliver_tiled" if args.deliver_mode == "tiled"
+                               else "k_deliver",
                      "launches": n_del, "avg_launch_us": 1e3 * ms_del / max(n_del, 1),
                      "deliver_mode": args.deliver_mode,
                      "tiles": [st_tiles.n_tiles, st_tiles.tile_width,
