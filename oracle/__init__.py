@@ -16,6 +16,9 @@ names the passage of the paper it follows:
 * ``update`` / ``simulate``  -- Section 1 and Section 2.1 (time-driven
   cycle: update for one min-delay interval, then deliver; exact
   integration of the linear subthreshold dynamics).
+* ``deliver_stdp`` / ``simulate_stdp`` -- Section 6 (plasticity as an update
+  scheme driven by presynaptic spikes, weights computed at delivery; the
+  cited pair-based power-law rule), with the readings stated in the C source.
 
 Parity unpinned: none of these has a worked example in the paper; all are
 pinned in ``tests/test_oracle_pins.py`` by closed forms, library routines,
@@ -133,6 +136,28 @@ def _declare(lib):
                                  C.c_int64, C.c_double, C.c_double, C.c_uint64,
                                  _P, _P, C.c_uint64, C.POINTER(C.c_uint64)]
     lib.orc_simulate.restype = C.c_uint64
+    _declare_stdp(lib)
+
+
+class StdpC(C.Structure):
+    _fields_ = [("h", C.c_double), ("tau_plus", C.c_double),
+                ("tau_minus", C.c_double), ("lam", C.c_double),
+                ("alpha", C.c_double), ("mu", C.c_double), ("w0", C.c_double),
+                ("w_max", C.c_double), ("n_exc", C.c_uint32)]
+
+
+class HistC(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("cap", C.c_uint32), ("t", C.c_void_p),
+                ("count", C.c_void_p)]
+
+
+def _declare_stdp(lib):
+    lib.orc_hist_add.argtypes = [C.POINTER(HistC), C.c_uint64, _P, _P]
+    lib.orc_hist_add.restype = C.c_int
+    lib.orc_deliver_stdp.argtypes = [C.POINTER(StoreC), _P, C.POINTER(StdpC),
+                                     C.POINTER(HistC), C.c_uint64, _P, _P, _P,
+                                     _P]
+    lib.orc_deliver_stdp.restype = C.c_uint64
 
 
 def _ptr(a: np.ndarray):
@@ -417,3 +442,82 @@ def simulate(nm: Neuron, store: Store, n_slots: int, interval: int, st: State,
                               C.byref(ev))
     ns = min(int(ns), cap)
     return src[:ns].copy(), tt[:ns].copy(), int(ev.value)
+
+
+# --------------------------------------------------------------------------
+# Plasticity (Section 6; readings in the C source)
+# --------------------------------------------------------------------------
+@dataclass
+class Stdp:
+    """Pair-based power-law STDP of E->E synapses."""
+    n_exc: int
+    tau_plus: float = 20.0   # ms
+    tau_minus: float = 20.0  # ms
+    lam: float = 0.1
+    alpha: float = 0.0513
+    mu: float = 0.4
+    w0: float = 1.0          # pA
+    w_max: float = 100.0     # pA
+    h: float = 0.1           # ms
+
+    def c(self) -> StdpC:
+        return StdpC(self.h, self.tau_plus, self.tau_minus, self.lam,
+                     self.alpha, self.mu, self.w0, self.w_max, self.n_exc)
+
+
+class History:
+    """Every spike of every neuron so far (``cap`` per neuron)."""
+
+    def __init__(self, n: int, cap: int = 4096):
+        self.n, self.cap = n, cap
+        self.t = np.zeros((n, cap), np.int64)
+        self.count = np.zeros(n, np.uint32)
+
+    def c(self) -> HistC:
+        return HistC(self.n, self.cap, self.t.ctypes.data, self.count.ctypes.data)
+
+    def add(self, src, t):
+        src, t = _spikes(src, t)
+        h = self.c()
+        if _load().orc_hist_add(C.byref(h), len(src), _ptr(src), _ptr(t)) != 0:
+            raise ValueError("spike history full")
+
+    def spikes(self, i: int) -> np.ndarray:
+        return self.t[i, :self.count[i]].copy()
+
+
+def deliver_stdp(st: Store, w: np.ndarray, p: Stdp, hist: History,
+                 n_slots: int, src, t, rb=None):
+    """Delivery with plastic E->E weights (``w`` updated in place; the
+    history must hold every spike up to the list's steps).  Returns
+    (rb, absw, events)."""
+    src, t = _spikes(src, t)
+    assert w.dtype == np.float64 and len(w) == len(st.tgt)
+    if rb is None:
+        rb = np.zeros((n_slots, st.n))
+    absw = np.zeros((n_slots, st.n))
+    ev = _load().orc_deliver_stdp(C.byref(st.c(n_slots)), _ptr(w),
+                                  C.byref(p.c()), C.byref(hist.c()), len(src),
+                                  _ptr(src), _ptr(t), _ptr(rb), _ptr(absw))
+    return rb, absw, int(ev)
+
+
+def simulate_stdp(nm: Neuron, store: Store, w: np.ndarray, p: Stdp,
+                  n_slots: int, interval: int, st: State, rb: np.ndarray,
+                  t0: int, n_steps: int, nu_ext_hz: float, w_ext: float,
+                  seed: int, hist: History):
+    """Time-driven cycle with plastic delivery: update one interval, record
+    its spikes, deliver them (weights in ``w`` change).  In place.  Returns
+    (spike sources, spike steps, events)."""
+    out_s, out_t, events = [], [], 0
+    t = t0
+    while t < t0 + n_steps:
+        m = min(interval, t0 + n_steps - t)
+        s_i, s_t = update(nm, st, rb, t, m, nu_ext_hz, w_ext, seed)
+        hist.add(s_i, s_t)
+        _, _, ev = deliver_stdp(store, w, p, hist, n_slots, s_i, s_t, rb)
+        events += ev
+        out_s.append(s_i)
+        out_t.append(s_t)
+        t += m
+    return np.concatenate(out_s), np.concatenate(out_t), events

@@ -676,3 +676,105 @@ uint64_t orc_simulate(const orc_neuron* nm, const orc_store* st,
   if (events_out) *events_out = events;
   return total;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Spike-timing dependent plasticity of E->E synapses, evaluated at          */
+/* delivery.  The paper's discussion (Section 6) describes the class of      */
+/* plasticity rules it has in view: an update scheme driven by presynaptic   */
+/* spikes in which a weight is computed only when the spike becomes visible  */
+/* at the target, so the weight arithmetic becomes part of delivery; it      */
+/* cites the pair-based power-law rule of Morrison, Aertsen & Diesmann       */
+/* (2007).  Readings (the paper gives no formulas):                          */
+/*  - a synapse i->j with delay d sees a presynaptic spike of i at its       */
+/*    emission step t_e and a postsynaptic spike of j at t_p + d (the whole  */
+/*    delay is dendritic);                                                   */
+/*  - every pre/post pair interacts (all-to-all) with                        */
+/*    D = (t_p + d - t_e) h:  D > 0 potentiates by                           */
+/*    lambda w0^(1-mu) w^mu exp(-D / tau_plus),  D <= 0 depresses by         */
+/*    lambda alpha w exp(D / tau_minus);                                     */
+/*  - at a presynaptic spike t_e the synapse first applies, in time order,   */
+/*    the potentiation owed to the post spikes seen since the previous pre   */
+/*    spike (t_prev < t_p + d <= t_e; each against all earlier pre spikes),  */
+/*    then the depression of the pairs (t_e, t_p) with t_p + d <= t_e, and   */
+/*    delivers the resulting weight; weights stay in [0, w_max].             */
+/* The traces are summed here directly over the full spike history.         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double h, tau_plus, tau_minus, lambda, alpha, mu, w0, w_max;
+  uint32_t n_exc;  /* synapse i->j is plastic iff i < n_exc and j < n_exc */
+} orc_stdp;
+
+typedef struct {
+  uint32_t n, cap;  /* neurons, spike times kept per neuron */
+  int64_t* t;       /* [n][cap], increasing per neuron */
+  uint32_t* count;  /* [n] */
+} orc_hist;
+
+/* Append spikes (in any neuron order, increasing time per neuron).  Returns
+ * -1 if a neuron's history is full. */
+int orc_hist_add(orc_hist* hs, uint64_t n_sp, const uint32_t* src,
+                 const int64_t* t) {
+  for (uint64_t s = 0; s < n_sp; ++s) {
+    uint32_t i = src[s];
+    if (i >= hs->n || hs->count[i] >= hs->cap) return -1;
+    hs->t[(size_t)i * hs->cap + hs->count[i]] = t[s];
+    hs->count[i] += 1;
+  }
+  return 0;
+}
+
+/* sum over spikes t' of neuron i with t' < before of exp(-(at - t') h / tau) */
+static double orc_trace_before(const orc_hist* hs, uint32_t i, int64_t before,
+                               int64_t at, double h, double tau) {
+  double k = 0.0;
+  const int64_t* ts = hs->t + (size_t)i * hs->cap;
+  for (uint32_t q = 0; q < hs->count[i]; ++q)
+    if (ts[q] < before) k += exp(-(double)(at - ts[q]) * h / tau);
+  return k;
+}
+
+uint64_t orc_deliver_stdp(const orc_store* st, double* w, const orc_stdp* p,
+                          const orc_hist* hs, uint64_t n_sp,
+                          const uint32_t* sp_src, const int64_t* sp_t,
+                          double* rb, double* absw) {
+  uint64_t events = 0;
+  const double c_pot = p->lambda * pow(p->w0, 1.0 - p->mu);
+  const double c_dep = p->lambda * p->alpha;
+  for (uint64_t s = 0; s < n_sp; ++s) {
+    const uint32_t i = sp_src[s];
+    const int64_t te = sp_t[s];
+    /* latest presynaptic spike before t_e */
+    int has_prev = 0;
+    int64_t tprev = 0;
+    const int64_t* ti = hs->t + (size_t)i * hs->cap;
+    for (uint32_t q = 0; q < hs->count[i]; ++q)
+      if (ti[q] < te && (!has_prev || ti[q] > tprev)) { tprev = ti[q]; has_prev = 1; }
+    for (uint64_t lcid = st->row_ptr[i]; lcid < st->row_ptr[i + 1]; ++lcid) {
+      const uint32_t j = st->tgt[lcid];
+      const int64_t d = st->delay[lcid];
+      double wt = w[lcid];
+      if (i < p->n_exc && j < p->n_exc) {
+        const int64_t* tj = hs->t + (size_t)j * hs->cap;
+        if (has_prev) {
+          for (uint32_t q = 0; q < hs->count[j]; ++q) {
+            const int64_t tp = tj[q];
+            if (tp + d > tprev && tp + d <= te) {
+              /* pre trace at t_p + d over all pre spikes before t_e */
+              double kp = orc_trace_before(hs, i, te, tp + d, p->h, p->tau_plus);
+              wt += c_pot * pow(wt, p->mu) * kp;
+              if (wt > p->w_max) wt = p->w_max;
+            }
+          }
+        }
+        /* post trace at t_e over post spikes seen at t_p + d <= t_e */
+        double km = orc_trace_before(hs, j, te - d + 1, te - d, p->h, p->tau_minus);
+        wt -= c_dep * wt * km;
+        if (wt < 0.0) wt = 0.0;
+        w[lcid] = wt;
+      }
+      orc_add_value(st, rb, NULL, absw, j, te + d, wt);
+      ++events;
+    }
+  }
+  return events;
+}
