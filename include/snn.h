@@ -165,7 +165,33 @@ typedef struct snn_stats {
   uint32_t n_tiles, tile_width; /* target tiles of the store */
   int32_t window;               /* ring steps one interval reaches */
   int32_t deliver_mode;         /* kernel used by update/simulate */
+  uint64_t plastic_events;      /* plastic weight updates (STDP nets) */
+  uint64_t stdp_truncated;      /* of which the post-spike window reached
+                                   past the kept history (see snn_set_stdp) */
 } snn_stats;
+
+/* Pair-based power-law STDP of the excitatory-to-excitatory synapses
+ * (arXiv 2109.12855, Section 6: plasticity as an update scheme driven by
+ * presynaptic spikes, weights computed when a spike becomes visible at the
+ * target; the cited Morrison et al. 2007 rule).  A synapse i->j with delay d
+ * sees a pre spike at its emission step t_e and a post spike of j at t_p + d;
+ * every pair interacts with D = (t_p + d - t_e) h: D > 0 potentiates by
+ * lambda w0^(1-mu) w^mu exp(-D/tau_plus), D <= 0 depresses by
+ * lambda alpha w exp(D/tau_minus).  At each delivered pre spike the weight
+ * first takes, in time order, the potentiation owed to the post spikes seen
+ * since the previous pre spike, then the depression, and is kept in
+ * [0, w_max]; the delivered value is the new weight. */
+typedef struct snn_stdp_params {
+  double tau_plus, tau_minus;  /* ms */
+  double lambda, alpha, mu;
+  double w0;                   /* pA: weight scale of the power law */
+  double w_max;                /* pA: upper bound (also bounds the exact
+                                  accumulation of the delivery kernel) */
+  int32_t history;             /* post spikes kept per neuron, 2..32; a
+                                  window that reaches past them is counted
+                                  in snn_stats.stdp_truncated */
+  int32_t reserved_;           /* 0 */
+} snn_stdp_params;
 
 typedef struct snn_net snn_net;
 
@@ -287,6 +313,22 @@ int snn_read_state(snn_net* net, float* V, float* I, float* J, int32_t* refr,
                    int mem);
 int snn_write_state(snn_net* net, const float* V, const float* I,
                     const float* J, const int32_t* refr, int mem);
+
+/* Enable STDP (see snn_stdp_params) on the E->E synapses; call after
+ * snn_create and before connecting.  Plastic nets need the tiled delivery
+ * (deliver_mode SNN_DELIVER_TILED) and at most one spike per neuron per
+ * interval (round(t_ref/h) + 1 >= interval, checked at snn_finalize).  The
+ * traces are kept by snn_update, so caller spike lists (snn_deliver,
+ * snn_deliver_noalloc) and checkpoints are refused with SNN_E_STATE.
+ * Weights start at the stored weights and change as plastic deliveries run;
+ * read them with snn_read_weights.  SNN_E_ARG for bad parameters,
+ * SNN_E_STATE if the net is already connected. */
+int snn_set_stdp(snn_net* net, const snn_stdp_params* p);
+
+/* Current weight of every synapse in store order (the order of
+ * snn_read_store): n_synapses floats into w (host or device memory per
+ * mem).  Static synapses return their stored weight. */
+int snn_read_weights(snn_net* net, float* w, int32_t mem);
 
 /* The finalized store: row_ptr uint64 [N+1]; per synapse target uint32,
  * delay uint8 and weight widened to float32 (n_synapses entries each).

@@ -250,14 +250,16 @@ int set_device(snn_net* net) {
 // tile width cells of two int32 accumulators) fits the shared-memory budget.  The sort key holds the
 // tile and the position in it in 24 bits; when a non-power-of-two width
 // would not fit them, the width is rounded up to a power of two.
-void choose_tiles(uint32_t n, int window, int32_t hint, uint32_t* tile_w,
-                  int* lo_bits, uint32_t* n_tiles) {
+// per_target: shared-memory bytes a tile needs per target beyond its
+// accumulator (the post-spike rings of a plastic net)
+void choose_tiles(uint32_t n, int window, int32_t hint, size_t per_target,
+                  uint32_t* tile_w, int* lo_bits, uint32_t* n_tiles) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms < 1) sms = 1;
-  const uint64_t tw_max =
-      std::max<uint64_t>(32, kTileSmemBudget / (8ull * std::max(window, 1)));
+  const uint64_t tw_max = std::max<uint64_t>(
+      32, kTileSmemBudget / (8ull * std::max(window, 1) + per_target));
   uint64_t tw = n;
   for (uint64_t k = 1; k <= 4096; ++k) {
     tw = (n + k * sms - 1) / (k * sms);
@@ -282,14 +284,20 @@ void choose_tiles(uint32_t n, int window, int32_t hint, uint32_t* tile_w,
 
 void snn::tile_geometry(uint32_t n, int window, int32_t hint, uint32_t* tile_w,
                         int* lo_bits, uint32_t* n_tiles) {
-  choose_tiles(n, window, hint, tile_w, lo_bits, n_tiles);
+  choose_tiles(n, window, hint, 0, tile_w, lo_bits, n_tiles);
 }
 
 namespace {
 
+size_t stdp_bytes_per_target(const snn_net* net) {
+  return net->stdp_on ? (size_t)net->stdp.history * 8 + 4 : 0;
+}
+
 bool use_tiled(const snn_net* net) {
   return net->p.deliver_mode == SNN_DELIVER_TILED && net->n_syn > 0 &&
-         net->tile_off && (size_t)net->window * net->tile_w * 8 <= kTileSmemBudget;
+         net->tile_off &&
+         (size_t)net->tile_w * ((size_t)net->window * 8 + stdp_bytes_per_target(net)) <=
+             kTileSmemBudget;
 }
 
 cudaError_t launch_deliver_any(snn_net* net, unsigned long long* pair,
@@ -339,8 +347,9 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
                      cudaMemcpyHostToDevice, s));
   // tiles sized for the widest window the interval can reach
   const int iv = net->p.interval ? net->p.interval : d_lo;
-  choose_tiles(n, iv + (d_hi - d_lo), net->p.tile_width, &net->tile_w,
-               &net->lo_bits, &net->n_tiles);
+  choose_tiles(n, iv + (d_hi - d_lo), net->p.tile_width,
+               stdp_bytes_per_target(net), &net->tile_w, &net->lo_bits,
+               &net->n_tiles);
   CK(dalloc(&net->tile_off, (uint64_t)n * (net->n_tiles + 1) * sizeof(uint32_t), net->stream));
   // keys; for 8-byte records the key array becomes the record array
   uint64_t* keys = nullptr;
@@ -727,6 +736,51 @@ int snn_connect_edges(snn_net* net, const uint32_t* src, const uint32_t* tgt,
   return rc;
 }
 
+// Plasticity state of a finalized store (snn_set_stdp): plastic weights
+// start at the stored weights; traces and post-spike rings start empty.
+int setup_stdp(snn_net* net) {
+  REQ(use_tiled(net), SNN_E_ARG,
+      "STDP needs the tiled delivery (deliver_mode SNN_DELIVER_TILED, and a "
+      "tile that fits shared memory)");
+  REQ(net->uc.refr_steps + 1 >= net->interval, SNN_E_ARG,
+      "STDP needs at most one spike per neuron per interval: refractory "
+      "steps + 1 = %d < interval %d", net->uc.refr_steps + 1, net->interval);
+  cudaStream_t s = net->stream;
+  const snn_stdp_params& q = net->stdp;
+  StdpView& sp = net->sp;
+  const uint64_t n = net->n, H = (uint64_t)q.history;
+  const uint64_t n_rec = net->recs_bytes / (net->fmt == SNN_W_FP32_12B ? 12 : 8);
+  CK(dalloc(&sp.wp, std::max<uint64_t>(n_rec, 1) * sizeof(float), s));
+  CK(cudaMemsetAsync(sp.wp, 0, std::max<uint64_t>(n_rec, 1) * sizeof(float), s));
+  CK(unpack_store(net->fmt, net->recs, net->n_syn, nullptr, nullptr, sp.wp, s));
+  CK(dalloc(&sp.pre_t, n * sizeof(int32_t), s));
+  CK(dalloc(&sp.prev_t, n * sizeof(int32_t), s));
+  CK(dalloc(&sp.pre_k, n * sizeof(float), s));
+  CK(dalloc(&sp.prev_k, n * sizeof(float), s));
+  CK(dalloc(&sp.ring_t, H * net->pitch * sizeof(int32_t), s));
+  CK(dalloc(&sp.ring_k, H * net->pitch * sizeof(float), s));
+  CK(dalloc(&sp.ring_n, n * sizeof(uint32_t), s));
+  CK(launch_fill_i32(sp.pre_t, kNoSpike, n, s));
+  CK(launch_fill_i32(sp.prev_t, kNoSpike, n, s));
+  CK(cudaMemsetAsync(sp.pre_k, 0, n * sizeof(float), s));
+  CK(cudaMemsetAsync(sp.prev_k, 0, n * sizeof(float), s));
+  CK(cudaMemsetAsync(sp.ring_n, 0, n * sizeof(uint32_t), s));
+  CK(cudaMemsetAsync(sp.ring_t, 0, H * net->pitch * sizeof(int32_t), s));
+  CK(cudaMemsetAsync(sp.ring_k, 0, H * net->pitch * sizeof(float), s));
+  sp.n_exc = net->p.n_exc;
+  sp.hist = (uint32_t)H;
+  sp.dt_plus = (float)(net->p.h / q.tau_plus);
+  sp.dt_minus = (float)(net->p.h / q.tau_minus);
+  sp.c_pot = (float)(q.lambda * pow(q.w0, 1.0 - q.mu));
+  sp.c_dep = (float)(q.lambda * q.alpha);
+  sp.mu = (float)q.mu;
+  sp.w_max = (float)q.w_max;
+  // the exact accumulation bounds every delivered weight by max|w|
+  net->max_abs_w = std::max(net->max_abs_w, sp.w_max);
+  net->launches += 3;
+  return SNN_OK;
+}
+
 int snn_finalize(snn_net* net) {
   REQ(net, SNN_E_ARG, "null net");
   REQ(!net->finalized, SNN_E_STATE, "already finalized");
@@ -765,6 +819,10 @@ int snn_finalize(snn_net* net) {
       (uint32_t)((iv + net->uc.refr_steps) / (net->uc.refr_steps + 1));
   net->list_cap = (uint64_t)net->n * iv;
   CK(dalloc(&net->list, net->list_cap * sizeof(SpikeEntry), net->stream));
+  if (net->stdp_on) {
+    int rc2;
+    if ((rc2 = setup_stdp(net)) != SNN_OK) return rc2;
+  }
   (void)deliver_grid_size(net->fmt);
   CK(cudaGetLastError());
   net->finalized = true;
@@ -820,6 +878,8 @@ int snn_deliver(snn_net* net, const uint32_t* src, const int32_t* t_emit,
                 uint32_t n_spikes, int mem, uint64_t* n_events_out) {
   REQ(net, SNN_E_ARG, "null net");
   REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  REQ(!net->stdp_on, SNN_E_STATE,
+      "plastic nets deliver only their own spikes (traces kept by the update)");
   REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
   REQ(n_spikes == 0 || (src && t_emit), SNN_E_ARG, "null spike arrays");
   int rc;
@@ -880,6 +940,8 @@ int snn_deliver_noalloc(snn_net* net, const uint32_t* src,
                         uint64_t* n_events_out) {
   REQ(net, SNN_E_ARG, "null net");
   REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  REQ(!net->stdp_on, SNN_E_STATE,
+      "plastic nets deliver only their own spikes (traces kept by the update)");
   REQ(n_spikes <= SNN_NOALLOC_MAX_SPIKES, SNN_E_ARG,
       "%u spikes exceed the allocation-free scratch of %u spikes", n_spikes,
       (unsigned)SNN_NOALLOC_MAX_SPIKES);
@@ -1136,6 +1198,7 @@ int snn_save_state(snn_net* net, void* host_buf, uint64_t cap) {
   REQ(net && host_buf, SNN_E_ARG, "null argument");
   REQ(cap >= state_bytes(net), SNN_E_OVERFLOW, "state needs %llu bytes",
       (unsigned long long)state_bytes(net));
+  REQ(!net->stdp_on, SNN_E_STATE, "checkpoints of plastic nets are not supported");
   REQ(!net->pending, SNN_E_STATE, "spikes of an update are pending");
   int rc;
   if ((rc = set_device(net)) != SNN_OK) return rc;
@@ -1165,6 +1228,7 @@ int snn_save_state(snn_net* net, void* host_buf, uint64_t cap) {
 int snn_load_state(snn_net* net, const void* host_buf, uint64_t size) {
   REQ(net && host_buf, SNN_E_ARG, "null argument");
   REQ(size >= state_bytes(net), SNN_E_ARG, "state image too short");
+  REQ(!net->stdp_on, SNN_E_STATE, "checkpoints of plastic nets are not supported");
   REQ(!net->pending, SNN_E_STATE, "spikes of an update are pending");
   StateHeader h;
   memcpy(&h, host_buf, sizeof h);
@@ -1255,6 +1319,50 @@ int snn_get_stats(snn_net* net, snn_stats* out) {
   out->tile_width = net->tile_w;
   out->window = net->window;
   out->deliver_mode = use_tiled(net) ? SNN_DELIVER_TILED : SNN_DELIVER_ATOMIC;
+  out->plastic_events = c.plastic_events;
+  out->stdp_truncated = c.stdp_truncated;
+  return SNN_OK;
+}
+
+int snn_set_stdp(snn_net* net, const snn_stdp_params* q) {
+  REQ(net && q, SNN_E_ARG, "null argument");
+  REQ(!net->connected && !net->finalized, SNN_E_STATE,
+      "snn_set_stdp must come before connecting");
+  REQ(q->tau_plus > 0 && q->tau_minus > 0 && q->lambda >= 0 && q->alpha >= 0 &&
+          q->mu >= 0 && q->mu <= 1 && q->w0 > 0 && q->w_max > 0 &&
+          isfinite(q->lambda) && isfinite(q->alpha) && isfinite(q->w_max),
+      SNN_E_ARG, "bad STDP parameters");
+  REQ(q->history >= 2 && q->history <= kMaxStdpHistory, SNN_E_ARG,
+      "STDP history %d outside [2, %d]", q->history, kMaxStdpHistory);
+  REQ(net->p.deliver_mode == SNN_DELIVER_TILED, SNN_E_ARG,
+      "STDP needs deliver_mode SNN_DELIVER_TILED");
+  net->stdp = *q;
+  net->stdp_on = true;
+  return SNN_OK;
+}
+
+int snn_read_weights(snn_net* net, float* w, int32_t mem) {
+  REQ(net && w, SNN_E_ARG, "null argument");
+  REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  const uint64_t m = net->n_syn;
+  if (m == 0) return SNN_OK;
+  if (net->sp.wp) {
+    CK(cudaMemcpyAsync(w, net->sp.wp, m * sizeof(float), kind_to(mem), s));
+  } else if (mem == SNN_MEM_DEVICE) {
+    CK(unpack_store(net->fmt, net->recs, m, nullptr, nullptr, w, s));
+  } else {
+    float* dw = nullptr;
+    CK(dalloc(&dw, m * sizeof(float), s));
+    CK(unpack_store(net->fmt, net->recs, m, nullptr, nullptr, dw, s));
+    CK(cudaMemcpyAsync(w, dw, m * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    dfree(dw, s);
+  }
+  if (mem == SNN_MEM_HOST) CK(cudaStreamSynchronize(s));
   return SNN_OK;
 }
 
@@ -1286,6 +1394,10 @@ int snn_destroy(snn_net* net) {
                   net->recs,     net->list,     net->ext_list, net->ext_src,
                   net->ext_t,    net->log_src,  net->log_t,   net->tile_off};
   for (void* b : bufs) dfree(b, net->stream);
+  void* sbufs[] = {net->sp.wp,     net->sp.pre_t,  net->sp.prev_t,
+                   net->sp.pre_k,  net->sp.prev_k, net->sp.ring_t,
+                   net->sp.ring_k, net->sp.ring_n};
+  for (void* b : sbufs) dfree(b, net->stream);
   if (net->counted) count_net(net->device, -1, net->stream);
   if (net->own_stream) cudaStreamDestroy(net->stream);
   delete net;

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <limits.h>
 #include <string.h>
 
 #include "../../include/snn.h"
@@ -77,6 +78,32 @@ struct Ctl {
   unsigned int ext_done;        // CTAs finished delivering an external list
   unsigned long long ext_pair;  // (spikes << 32) | chunks of an external list
   int ext_tmin, ext_tmax;       // emission-step range of an external list
+  unsigned long long plastic_events;  // plastic synapse updates (accumulated)
+  unsigned long long stdp_truncated;  // updates whose post-spike window
+                                      // reached past the kept history
+};
+
+// "No spike yet" for the spike-time fields of the plasticity state.
+constexpr int32_t kNoSpike = INT32_MIN;
+constexpr int kMaxStdpHistory = 32;
+
+// Plasticity state of a net with STDP on its E->E synapses (see
+// snn_kernels.cu); all pointers null for a static net.
+struct StdpView {
+  float* wp;            // plastic weight of every record (store order)
+  int32_t* pre_t;       // [n] latest spike step (kNoSpike if none)
+  float* pre_k;         // [n] presynaptic trace right after it
+  int32_t* prev_t;      // [n] the two values before the latest spike
+  float* prev_k;
+  int32_t* ring_t;      // [hist][pitch] steps of the last hist spikes
+  float* ring_k;        // [hist][pitch] postsynaptic trace right after each
+  uint32_t* ring_n;     // [n] spikes so far (ring position = count mod hist)
+  uint32_t n_exc;       // plastic: source < n_exc and target < n_exc
+  uint32_t hist;
+  float dt_plus, dt_minus;  // h / tau_plus, h / tau_minus
+  float c_pot;              // lambda w0^(1 - mu)
+  float c_dep;              // lambda alpha
+  float mu, w_max;
 };
 
 // ---------------------------------------------------------------------------
@@ -197,6 +224,8 @@ struct NetView {
   int32_t* log_t;
   uint64_t log_cap;
   Ctl* ctl;
+  int plastic;              // STDP on (state in sp)
+  StdpView sp;
 };
 
 // One net of a batch advanced by the batched kernels (device table entry).
@@ -279,6 +308,8 @@ cudaError_t build_sort_pack(int fmt, uint32_t n, const uint64_t* row_ptr,
                             const uint64_t* long_scratch_off, uint32_t tile_w,
                             int lo_bits, uint32_t n_tiles, uint32_t* tile_off,
                             uint32_t* stats, cudaStream_t s);
+cudaError_t launch_fill_i32(int32_t* p, int32_t value, uint64_t n,
+                            cudaStream_t s);
 cudaError_t unpack_store(int fmt, const void* recs, uint64_t n_syn,
                          uint32_t* tgt, uint8_t* delay, float* w,
                          cudaStream_t s);

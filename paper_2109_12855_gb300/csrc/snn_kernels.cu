@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "snn_internal.cuh"
@@ -58,6 +59,12 @@ __global__ void k_init_state(NetView v, float v_reset, float v_span,
   v.I[i] = 0.0f;
   v.J[i] = 0.0f;
   v.refr[i] = 0;
+}
+
+__global__ void k_fill_i32(int32_t* p, int32_t value, uint64_t n) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
+       k += (uint64_t)gridDim.x * blockDim.x)
+    p[k] = value;
 }
 
 // ---------------------------------------------------------------------------
@@ -139,8 +146,34 @@ __device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b,
   __syncthreads();  // the shared arrays are reused by the next call
 }
 
+// Plasticity state at a spike of excitatory neuron i at step t: the
+// presynaptic trace (kept with the values before this spike, which its own
+// delivery needs) and the postsynaptic ring of the last hist spikes with the
+// trace right after each.  Traces decay by exp(-steps h / tau) and jump by 1.
+__device__ __forceinline__ void stdp_on_spike(const StdpView& sp, uint32_t i,
+                                              int32_t t, uint32_t pitch) {
+  const int32_t tl = sp.pre_t[i];
+  const float kl = sp.pre_k[i];
+  sp.prev_t[i] = tl;
+  sp.prev_k[i] = kl;
+  sp.pre_k[i] =
+      (tl == kNoSpike ? 0.f : kl * expf(-(float)(t - tl) * sp.dt_plus)) + 1.f;
+  sp.pre_t[i] = t;
+  const uint32_t n = sp.ring_n[i];
+  float km = 0.f;
+  if (n) {
+    const size_t last = (size_t)((n - 1u) % sp.hist) * pitch + i;
+    km = sp.ring_k[last] * expf(-(float)(t - sp.ring_t[last]) * sp.dt_minus);
+  }
+  const size_t slot = (size_t)(n % sp.hist) * pitch + i;
+  sp.ring_t[slot] = t;
+  sp.ring_k[slot] = km + 1.f;
+  sp.ring_n[i] = n + 1u;
+}
+
 // Body of the update for neuron block `block` of net v (one thread per
 // neuron); shared by the single-net and the batched kernels.
+template <bool PL>
 __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
                                             int n_steps, int from_ctl,
                                             long long t0_arg, uint32_t block) {
@@ -283,6 +316,8 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
             atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_SPIKE_LOG);
           }
         }
+        if (PL && v.plastic && i < v.sp.n_exc)
+          stdp_on_spike(v.sp, i, (int32_t)t, v.pitch);
         ++k;
       }
       __syncthreads();  // s_base is rewritten by the next chunk
@@ -298,7 +333,7 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
 
 __global__ void __launch_bounds__(kUpdThreads)
 k_update(NetView v, UpdConst c, int n_steps, int from_ctl, long long t0_arg) {
-  update_body(v, c, n_steps, from_ctl, t0_arg, blockIdx.x);
+  update_body<true>(v, c, n_steps, from_ctl, t0_arg, blockIdx.x);
 }
 
 // All nets of a batch in one launch: block b updates neuron block bmap[b].y
@@ -315,7 +350,7 @@ k_update_batch(const BatchNet* __restrict__ nets, const uint2* __restrict__ bmap
   const NetView v = bn.v;
   const int n_steps = bn.n_steps;
   __syncthreads();
-  update_body(v, s_c, n_steps, 1, 0, m.y);
+  update_body<false>(v, s_c, n_steps, 1, 0, m.y);  // served nets are static
 }
 
 // ---------------------------------------------------------------------------
@@ -584,15 +619,62 @@ __device__ FixScale fix_scale(const NetView& v, uint64_t n_sp,
   return f;
 }
 
-template <int FMT, bool COUNT>
+// Plastic weight of an E->E synapse at its presynaptic spike t with delay
+// d (pair-based power-law STDP, all pairs, the whole delay dendritic): the
+// potentiation owed to the post spikes seen since the previous pre spike,
+// in time order, then the depression by the post trace at t; weights stay in
+// [0, w_max].  tprev / kprev: the previous pre spike and the presynaptic
+// trace right after it.  Post spikes of target j come from the CTA's copy
+// of the last hist spikes (rt, rk: [hist][TW]; rn: spikes so far).  *trunc
+// counts updates whose window reached past the kept spikes.
+__device__ __forceinline__ float stdp_weight(
+    const StdpView& sp, float w, int32_t t, uint32_t d, int32_t tprev,
+    float kprev, uint32_t j, uint32_t TW, const int32_t* rt, const float* rk,
+    const uint32_t* rn, uint32_t* trunc) {
+  const uint32_t H = sp.hist;
+  const uint32_t n = rn[j];
+  const int32_t horizon = t - (int32_t)d;  // post spikes seen by step t
+  const bool has_prev = tprev != kNoSpike;
+  const int32_t after = has_prev ? tprev - (int32_t)d : 0;
+  const int32_t k_min = n > H ? (int32_t)(n - H) : 0;
+  int32_t k_dep = -1, k_lo = -1, k = (int32_t)n - 1;
+  for (; k >= k_min; --k) {
+    const int32_t tp = rt[(uint32_t)k % H * TW + j];
+    if (tp > horizon) continue;
+    if (k_dep < 0) k_dep = k;
+    if (!has_prev || tp <= after) break;
+    k_lo = k;
+  }
+  if (k < k_min && n > H && (has_prev || k_dep < 0)) *trunc += 1u;
+  if (k_lo >= 0) {
+    for (int32_t q = k_lo; q <= k_dep; ++q) {
+      const int32_t tp = rt[(uint32_t)q % H * TW + j];
+      const float kp = kprev * expf(-(float)(tp + (int32_t)d - tprev) * sp.dt_plus);
+      w = fminf(w + sp.c_pot * powf(w, sp.mu) * kp, sp.w_max);
+    }
+  }
+  if (k_dep >= 0) {
+    const uint32_t e = (uint32_t)k_dep % H * TW + j;
+    const float km = rk[e] * expf(-(float)(horizon - rt[e]) * sp.dt_minus);
+    w = fmaxf(w - sp.c_dep * w * km, 0.f);
+  }
+  return w;
+}
+
+template <int FMT, bool COUNT, bool PL>
 __device__ __forceinline__ void deliver_tile_body(
     const NetView& v, unsigned long long* pair_p, unsigned int* done_p,
     const SpikeEntry* __restrict__ list, int from_list_range, int advance_time,
     uint32_t tile, int* acc_mem) {
   // U runs per warp pass, PER records per lane of each loaded before use
-  constexpr int U = FMT == SNN_W_FP32_12B ? 2 : 4;
+  // (plastic nets also hold each record's plastic weight: fewer runs)
+  constexpr int U = PL ? (FMT == SNN_W_FP32_12B ? 1 : 2)
+                       : (FMT == SNN_W_FP32_12B ? 2 : 4);
   constexpr int PER = 3;
   __shared__ SegDesc s_desc[kDescBatch];
+  __shared__ int32_t s_tprev[PL ? kDescBatch : 1];   // previous pre spike
+  __shared__ float s_kprev[PL ? kDescBatch : 1];     // its trace; < 0: static
+  __shared__ unsigned long long s_pl[2];             // plastic updates, truncations
   __shared__ unsigned long long s_pair;
   __shared__ long long s_base;
   __shared__ int s_inwin;
@@ -623,6 +705,26 @@ __device__ __forceinline__ void deliver_tile_body(
   int* accL = acc_mem + cells;                        // fixed: lo parts
   float* accF = reinterpret_cast<float*>(acc_mem);    // FP32 fallback
   for (uint32_t x = threadIdx.x; x < 2 * cells; x += blockDim.x) acc_mem[x] = 0;
+  // plastic nets: the post-spike rings of this tile's targets
+  int32_t* s_rt = acc_mem + 2 * cells;                           // [hist][TW]
+  float* s_rk = reinterpret_cast<float*>(s_rt + (PL ? v.sp.hist * TW : 0));
+  uint32_t* s_rn = reinterpret_cast<uint32_t*>(s_rk + (PL ? v.sp.hist * TW : 0));
+  const bool tile_plastic = PL && tgt_lo < v.sp.n_exc;
+  uint32_t my_pl = 0, my_trunc = 0;
+  if (PL) {
+    if (threadIdx.x < 2) s_pl[threadIdx.x] = 0ull;
+    if (tile_plastic) {
+      for (uint32_t x = threadIdx.x; x < TW; x += blockDim.x)
+        s_rn[x] = tgt_lo + x < v.n ? v.sp.ring_n[tgt_lo + x] : 0u;
+      for (uint32_t x = threadIdx.x; x < v.sp.hist * TW; x += blockDim.x) {
+        const uint32_t q = x / TW, jj = x - q * TW;
+        if (tgt_lo + jj < v.n) {
+          s_rt[x] = v.sp.ring_t[(size_t)q * v.pitch + tgt_lo + jj];
+          s_rk[x] = v.sp.ring_k[(size_t)q * v.pitch + tgt_lo + jj];
+        }
+      }
+    }
+  }
   __syncthreads();
   const uint32_t n_sp = (uint32_t)(s_pair >> 32);
   const long long base = s_base;
@@ -650,26 +752,42 @@ __device__ __forceinline__ void deliver_tile_body(
                 1u);
   };
 
-  auto load_pass = [&](Rec1<FMT> (&r)[U][PER], uint32_t k0, uint32_t nb) {
+  // plastic E->E synapse: update its weight (record index r), store it
+  auto plastic = [&](uint32_t tgt, uint32_t k_run, int32_t t, uint32_t d,
+                     float w, uint64_t r) -> float {
+    w = stdp_weight(v.sp, w, t, d, s_tprev[k_run], s_kprev[k_run], tgt - tgt_lo,
+                    TW, s_rt, s_rk, s_rn, &my_trunc);
+    v.sp.wp[r] = w;
+    ++my_pl;
+    return w;
+  };
+  auto load_pass = [&](Rec1<FMT> (&r)[U][PER], float (&wv)[U][PER], uint32_t k0,
+                       uint32_t nb) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const bool ok = k0 + u < nb;
       const uint64_t beg = ok ? s_desc[k0 + u].beg : 0ull;
       const uint32_t len = ok ? s_desc[k0 + u].len : 0u;
+      const bool pl = PL && tile_plastic && ok && s_kprev[k0 + u] >= 0.f;
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
         const uint32_t idx = lane + 32u * q;
-        if (idx < len) r[u][q] = load_rec<FMT>(v.recs, beg + idx);
+        if (idx < len) {
+          r[u][q] = load_rec<FMT>(v.recs, beg + idx);
+          if (pl) wv[u][q] = __ldcs(v.sp.wp + beg + idx);
+        }
       }
     }
   };
-  auto add_pass = [&](const Rec1<FMT> (&r)[U][PER], uint32_t k0, uint32_t nb) {
+  auto add_pass = [&](const Rec1<FMT> (&r)[U][PER], const float (&wv)[U][PER],
+                      uint32_t k0, uint32_t nb) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (k0 + u >= nb) break;
       const SegDesc sd = s_desc[k0 + u];
       const int32_t off =
           (int32_t)(((long long)sd.t - base) * (long long)TW) - (int32_t)tgt_lo;
+      const bool pl = PL && tile_plastic && s_kprev[k0 + u] >= 0.f;
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
         const uint32_t idx = lane + 32u * q;
@@ -677,6 +795,8 @@ __device__ __forceinline__ void deliver_tile_body(
           uint32_t tgt, d;
           float w;
           rec_fields(r[u][q], tgt, d, w);
+          if (pl && tgt < v.sp.n_exc)
+            w = plastic(tgt, k0 + u, sd.t, d, wv[u][q], sd.beg + idx);
           add(tgt, sd.t, off, d, w);
         }
       }
@@ -684,6 +804,9 @@ __device__ __forceinline__ void deliver_tile_body(
         uint32_t tgt, d;
         float w;
         rec_fields(load_rec<FMT>(v.recs, sd.beg + idx), tgt, d, w);
+        if (pl && tgt < v.sp.n_exc)
+          w = plastic(tgt, k0 + u, sd.t, d, __ldcs(v.sp.wp + sd.beg + idx),
+                      sd.beg + idx);
         add(tgt, sd.t, off, d, w);
       }
     }
@@ -703,13 +826,19 @@ __device__ __forceinline__ void deliver_tile_body(
         sd.len = b - a;
       }
       s_desc[k] = sd;
+      if (PL) {
+        const bool exc = e.src < v.sp.n_exc;
+        s_tprev[k] = exc ? v.sp.prev_t[e.src] : kNoSpike;
+        s_kprev[k] = exc ? v.sp.prev_k[e.src] : -1.f;
+      }
     }
     __syncthreads();
     // (B) each warp takes U runs per pass: all loads first, then the adds
     for (uint32_t k = warp * U; k < nb; k += kTileWarps * U) {
       Rec1<FMT> r[U][PER];
-      load_pass(r, k, nb);
-      add_pass(r, k, nb);
+      float wv[U][PER];
+      load_pass(r, wv, k, nb);
+      add_pass(r, wv, k, nb);
     }
     __syncthreads();  // s_desc is rewritten by the next batch
   }
@@ -746,6 +875,24 @@ __device__ __forceinline__ void deliver_tile_body(
       }
     }
   }
+  if (PL) {
+    // one pair of atomics per warp, one per CTA
+    unsigned long long a = my_pl, b = my_trunc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(kFull, a, o);
+      b += __shfl_xor_sync(kFull, b, o);
+    }
+    if (lane == 0 && (a | b)) {
+      atomicAdd(&s_pl[0], a);
+      atomicAdd(&s_pl[1], b);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (s_pl[0] | s_pl[1])) {
+      atomicAdd(&v.ctl->plastic_events, s_pl[0]);
+      atomicAdd(&v.ctl->stdp_truncated, s_pl[1]);
+    }
+  }
   // The last CTA to finish clears the list counters and advances the clock.
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -759,14 +906,14 @@ __device__ __forceinline__ void deliver_tile_body(
   }
 }
 
-template <int FMT, bool COUNT>
+template <int FMT, bool COUNT, bool PL>
 __global__ void __launch_bounds__(kTileThreads, 1)
 k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
                 const SpikeEntry* __restrict__ list, int from_list_range,
                 int advance_time) {
   extern __shared__ __align__(16) int acc_mem[];
-  deliver_tile_body<FMT, COUNT>(v, pair_p, done_p, list, from_list_range,
-                                advance_time, blockIdx.x, acc_mem);
+  deliver_tile_body<FMT, COUNT, PL>(v, pair_p, done_p, list, from_list_range,
+                                    advance_time, blockIdx.x, acc_mem);
 }
 
 // All nets of a batch in one launch: CTA b delivers tile bmap[b].y of net
@@ -778,8 +925,8 @@ k_deliver_tiled_batch(const BatchNet* __restrict__ nets,
   extern __shared__ __align__(16) int acc_mem[];
   const uint2 m = bmap[blockIdx.x];
   const NetView v = nets[m.x].v;
-  deliver_tile_body<FMT, false>(v, &v.ctl->pair, &v.ctl->done, v.list, 0, 1,
-                                m.y, acc_mem);
+  deliver_tile_body<FMT, false, false>(v, &v.ctl->pair, &v.ctl->done, v.list,
+                                       0, 1, m.y, acc_mem);
 }
 
 // ---------------------------------------------------------------------------
@@ -930,10 +1077,12 @@ cudaError_t launch_deliver(const NetView& v, unsigned long long* pair,
 }
 
 size_t tiled_smem_bytes(const NetView& v) {
-  return 2 * (size_t)v.window * v.tile_w * sizeof(int);
+  return (size_t)v.tile_w *
+         (2 * (size_t)v.window * sizeof(int) +
+          (v.plastic ? (size_t)v.sp.hist * 8 + sizeof(uint32_t) : 0));
 }
 
-template <int FMT, bool COUNT>
+template <int FMT, bool COUNT, bool PL>
 cudaError_t launch_tiled_t(const NetView& v, unsigned long long* pair,
                            unsigned int* done, const SpikeEntry* list,
                            int from_list_range, int advance_time,
@@ -942,12 +1091,12 @@ cudaError_t launch_tiled_t(const NetView& v, unsigned long long* pair,
   static int configured = 0;   // per-process attribute, set once
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(
-        k_deliver_tiled<FMT, COUNT>,
+        k_deliver_tiled<FMT, COUNT, PL>,
         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     configured = 1;
   }
-  k_deliver_tiled<FMT, COUNT><<<v.n_tiles, kTileThreads, smem, s>>>(
+  k_deliver_tiled<FMT, COUNT, PL><<<v.n_tiles, kTileThreads, smem, s>>>(
       v, pair, done, list, from_list_range, advance_time);
   return cudaGetLastError();
 }
@@ -956,15 +1105,29 @@ cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
                                  unsigned int* done, const SpikeEntry* list,
                                  int from_list_range, int advance_time,
                                  cudaStream_t s) {
+#define SNN_TILED(F, C, P) \
+  launch_tiled_t<F, C, P>(v, pair, done, list, from_list_range, advance_time, s)
+  if (v.plastic) {
+    if (v.fmt == SNN_W_FP32_12B)
+      return v.counts ? SNN_TILED(SNN_W_FP32_12B, true, true)
+                      : SNN_TILED(SNN_W_FP32_12B, false, true);
+    return v.counts ? SNN_TILED(SNN_W_BF16_8B, true, true)
+                    : SNN_TILED(SNN_W_BF16_8B, false, true);
+  }
   if (v.fmt == SNN_W_FP32_12B)
-    return v.counts ? launch_tiled_t<SNN_W_FP32_12B, true>(
-                          v, pair, done, list, from_list_range, advance_time, s)
-                    : launch_tiled_t<SNN_W_FP32_12B, false>(
-                          v, pair, done, list, from_list_range, advance_time, s);
-  return v.counts ? launch_tiled_t<SNN_W_BF16_8B, true>(
-                        v, pair, done, list, from_list_range, advance_time, s)
-                  : launch_tiled_t<SNN_W_BF16_8B, false>(
-                        v, pair, done, list, from_list_range, advance_time, s);
+    return v.counts ? SNN_TILED(SNN_W_FP32_12B, true, false)
+                    : SNN_TILED(SNN_W_FP32_12B, false, false);
+  return v.counts ? SNN_TILED(SNN_W_BF16_8B, true, false)
+                  : SNN_TILED(SNN_W_BF16_8B, false, false);
+#undef SNN_TILED
+}
+
+cudaError_t launch_fill_i32(int32_t* p, int32_t value, uint64_t n,
+                            cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 4096);
+  k_fill_i32<<<(unsigned)blocks, 256, 0, s>>>(p, value, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_update_batch(const BatchNet* nets, const uint2* bmap,

@@ -65,6 +65,10 @@ struct snn_net {
   double ms_update = 0, ms_deliver = 0;
   uint64_t launches = 0, upd_launches = 0, del_launches = 0;
   cudaGraphExec_t graph = nullptr;
+  // STDP (snn_set_stdp): parameters and device state (StdpView)
+  bool stdp_on = false;
+  snn_stdp_params stdp{};
+  StdpView sp{};
 
   NetView view() const {
     NetView v;
@@ -97,6 +101,8 @@ struct snn_net {
     v.log_t = log_t;
     v.log_cap = log_cap;
     v.ctl = ctl;
+    v.plastic = stdp_on && sp.wp != nullptr;
+    v.sp = sp;
     return v;
   }
 };

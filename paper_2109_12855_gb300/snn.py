@@ -37,7 +37,8 @@ EXPORTS = [
     "snn_set_profiling", "snn_get_stats", "snn_clear_errors", "snn_sync",
     "snn_destroy", "snn_server_create", "snn_server_submit", "snn_server_step",
     "snn_server_poll", "snn_server_spikes", "snn_server_release",
-    "snn_server_get_stats", "snn_server_destroy",
+    "snn_server_get_stats", "snn_server_destroy", "snn_set_stdp",
+    "snn_read_weights",
 ]
 SNN_REQ_QUEUED, SNN_REQ_BUILDING, SNN_REQ_RUNNING, SNN_REQ_DONE = 0, 1, 2, 3
 SNN_REQ_FAILED = -1
@@ -81,7 +82,15 @@ class snn_stats(C.Structure):
                 ("ms_deliver", C.c_double), ("bytes_per_record", C.c_uint64),
                 ("store_bytes", C.c_uint64), ("n_tiles", C.c_uint32),
                 ("tile_width", C.c_uint32), ("window", C.c_int32),
-                ("deliver_mode", C.c_int32)]
+                ("deliver_mode", C.c_int32), ("plastic_events", C.c_uint64),
+                ("stdp_truncated", C.c_uint64)]
+
+
+class snn_stdp_params(C.Structure):
+    _fields_ = [("tau_plus", C.c_double), ("tau_minus", C.c_double),
+                ("lam", C.c_double), ("alpha", C.c_double), ("mu", C.c_double),
+                ("w0", C.c_double), ("w_max", C.c_double),
+                ("history", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class snn_request(C.Structure):
@@ -163,6 +172,8 @@ def lib():
             "snn_clear_errors": ([_P], C.c_int),
             "snn_sync": ([_P], C.c_int),
             "snn_destroy": ([_P], C.c_int),
+            "snn_set_stdp": ([_P, C.POINTER(snn_stdp_params)], C.c_int),
+            "snn_read_weights": ([_P, _P, C.c_int32], C.c_int),
             "snn_server_create": ([C.c_uint64, C.c_int32, _P, C.POINTER(_P)],
                                   C.c_int),
             "snn_server_submit": ([_P, C.POINTER(snn_request),
@@ -332,6 +343,26 @@ def snn_read_store(net, row_ptr=None, tgt=None, delay=None, w=None):
                                 _buf(delay)[0], _buf(w)[0], mem))
 
 
+def stdp_params(**kw) -> snn_stdp_params:
+    """Power-law STDP defaults (tau 20 ms, lambda 0.1, alpha 0.0513,
+    mu 0.4, w0 1 pA, w_max 100 pA, 16 post spikes kept) with overrides."""
+    q = snn_stdp_params(20.0, 20.0, 0.1, 0.0513, 0.4, 1.0, 100.0, 16, 0)
+    for k, v in kw.items():
+        if not hasattr(q, k):
+            raise AttributeError(k)
+        setattr(q, k, v)
+    return q
+
+
+def snn_set_stdp(net, q: snn_stdp_params):
+    _check(lib().snn_set_stdp(net, C.byref(q)))
+
+
+def snn_read_weights(net, w):
+    mem = _mem_of(w)
+    _check(lib().snn_read_weights(net, _buf(w)[0], mem))
+
+
 def snn_state_size(net) -> int:
     n = C.c_uint64()
     _check(lib().snn_state_size(net, C.byref(n)))
@@ -476,6 +507,12 @@ class Net:
         w = np.zeros(max(m, 1), np.float32)
         snn_read_store(self.h, rp, tg, dl, w)
         return rp, tg[:m], dl[:m], w[:m]
+
+    def read_weights(self):
+        m = self.stats().n_synapses
+        w = np.zeros(max(m, 1), np.float32)
+        snn_read_weights(self.h, w)
+        return w[:m]
 
     def deliver(self, src, t):
         return snn_deliver(self.h, np.ascontiguousarray(src, np.uint32),
