@@ -45,6 +45,9 @@ WORKLOADS = {
     "balanced-112500-bf16": (W.BALANCED_112500, 1, 1000.0, "simulate"),
     "balanced-562500-bf16": (W.BALANCED_562500, 1, 500.0, "simulate"),
     "balanced-1250-fp32": (W.BALANCED_1250, 0, 1000.0, "simulate"),
+    # plastic variant: E->E synapses with power-law STDP (FP32 weights
+    # updated at delivery), the other synapses static BF16
+    "balanced-112500-stdp-bf16": (W.BALANCED_112500, 1, 1000.0, "simulate"),
     "deliver-112500-fp32": (W.BALANCED_112500, 0, 1000.0, "deliver"),
     "deliver-562500-bf16": (W.BALANCED_562500, 1, 500.0, "deliver"),
     # profiling case for the update kernel: all 112,500 neurons, in-degree
@@ -52,6 +55,11 @@ WORKLOADS = {
     "update-112500": (W.Balanced("balanced-112500-k1125", 90000, 22500, 900,
                                  225, 15, 15, "fp32", 0.0, 1000.0),
                       0, 1000.0, "simulate"),
+    # profiling case of the plastic kernel: 20,000 neurons with the
+    # in-degree of the 112,500-neuron network (1.8 GB store)
+    "stdp-20000-bf16": (W.Balanced("balanced-20000", 16000, 4000, 9000,
+                                   2250, 15, 15, "bf16", 0.0, 150.0),
+                        1, 150.0, "simulate"),
     # profiling case: the same segment length and launch size as the
     # 112,500-neuron delivery, with a store of 2.7 GB
     "deliver-20000-fp32": (W.Balanced("balanced-20000", 16000, 4000, 9000,
@@ -59,6 +67,19 @@ WORKLOADS = {
                            0, 150.0, "deliver"),
 }
 DEFAULT = "balanced-112500-fp32"
+PLASTIC = {"balanced-112500-stdp-bf16", "stdp-20000-bf16"}
+# STDP of the plastic workload: tau 20 ms, lambda 0.1, alpha 0.0513, mu 0.4;
+# weights bounded by 100 pA; 16 post spikes kept per neuron.  For
+# uncorrelated firing the rule drifts towards w0 alpha^(-1/(1-mu)); w0 is
+# set so that this equals the initial excitatory weight (w0 = 1 pA would put
+# it at 141 pA, six times the 0.1 mV weight, and the network runs away).
+STDP_ALPHA, STDP_MU = 0.0513, 0.4
+
+
+def stdp_config(w_e):
+    return dict(tau_plus=20.0, tau_minus=20.0, lam=0.1, alpha=STDP_ALPHA,
+                mu=STDP_MU, w0=w_e * STDP_ALPHA ** (1.0 / (1.0 - STDP_MU)),
+                w_max=100.0, history=16)
 # DRAM bytes (read + write) per synaptic event of k_deliver_tiled, summed by
 # ncu over all 667 launches of one timed step of the workload and divided by
 # that step's events (profiles/dram_k_deliver_tiled_balanced-112500-fp32.md).
@@ -163,7 +184,8 @@ def barrier():
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
-def oracle_sample(wl, nu_ext, n_targets, seed=1, n_lists=50, rate_hz=8.0):
+def oracle_sample(wl, nu_ext, n_targets, seed=1, n_lists=50, rate_hz=8.0,
+                  plastic=False):
     """The segments of the targets [0, n_targets) (what one NEST thread that
     owns those targets holds), the oracle's neuron model for them, and a pool
     of interval spike lists of all sources (Bernoulli at rate_hz) that the
@@ -178,9 +200,18 @@ def oracle_sample(wl, nu_ext, n_targets, seed=1, n_lists=50, rate_hz=8.0):
              for k in range(n_lists)]
     st = O.State(O.init_v(nm, n_targets, seed), np.zeros(n_targets),
                  np.zeros(n_targets), np.zeros(n_targets, np.int32))
-    return {"O": O, "nm": nm, "w_e": w_e, "store": store, "n": n_targets,
-            "lists": lists, "state": st, "rb_local": np.zeros((32, n_targets)),
-            "rb": np.zeros((32, wl.n)), "t": 0}
+    ctx = {"O": O, "nm": nm, "w_e": w_e, "store": store, "n": n_targets,
+           "lists": lists, "state": st, "rb_local": np.zeros((32, n_targets)),
+           "rb": np.zeros((32, wl.n)), "t": 0, "plastic": plastic}
+    if plastic:
+        q = stdp_config(w_e)
+        ctx["w"] = store.w.copy()
+        ctx["hist"] = O.History(wl.n, cap=96)
+        ctx["stdp"] = O.Stdp(n_exc=wl.n_e, tau_plus=q["tau_plus"],
+                             tau_minus=q["tau_minus"], lam=q["lam"],
+                             alpha=q["alpha"], mu=q["mu"], w0=q["w0"],
+                             w_max=q["w_max"])
+    return ctx
 
 
 def oracle_step(ctx, wl, nu_ext, n_intervals, seed=1):
@@ -197,19 +228,27 @@ def oracle_step(ctx, wl, nu_ext, n_intervals, seed=1):
         a = time.perf_counter()
         O.update(ctx["nm"], ctx["state"], ctx["rb_local"], t, D, nu_ext,
                  ctx["w_e"], seed)
-        _, _, _, ev = O.deliver_ref(ctx["store"], 32, src, tt + t,
-                                    rb=ctx["rb"], counts=False)
+        if ctx["plastic"]:
+            ctx["hist"].add(src, tt + t)
+            _, _, ev = O.deliver_stdp(ctx["store"], ctx["w"], ctx["stdp"],
+                                      ctx["hist"], 32, src, tt + t,
+                                      rb=ctx["rb"])
+        else:
+            _, _, _, ev = O.deliver_ref(ctx["store"], 32, src, tt + t,
+                                        rb=ctx["rb"], counts=False)
         secs += time.perf_counter() - a
         events += ev
         ctx["t"] = t + D
     return events, secs
 
 
-def sample_text(wl, n_targets, n_intervals):
+def sample_text(wl, n_targets, n_intervals, plastic=False):
+    how = ("plastic delivery (STDP of the E->E synapses against the full "
+           "spike history)" if plastic else "Algorithm REF delivery")
     return (f"targets [0, {n_targets:,}) of {wl.name} "
             f"({n_targets * wl.k:,} synapses), {n_intervals} intervals of "
-            f"{wl.d_lo} steps: oracle update of those neurons + Algorithm REF "
-            f"delivery of 8 Hz Bernoulli spike lists of all {wl.n:,} sources "
+            f"{wl.d_lo} steps: oracle update of those neurons + {how} "
+            f"of 8 Hz Bernoulli spike lists of all {wl.n:,} sources "
             f"onto them (single thread)")
 
 
@@ -219,8 +258,10 @@ def run_reference(args, wl, nu_ext):
     if rank != 0:
         return
     n_targets = args.oracle_targets
-    ctx = oracle_sample(wl, nu_ext, n_targets)
-    per_step = args.oracle_intervals
+    plastic = args.workload in PLASTIC
+    ctx = oracle_sample(wl, nu_ext, n_targets, plastic=plastic)
+    per_step = args.oracle_intervals if not plastic else min(
+        args.oracle_intervals, 20)
     for _ in range(args.warmup):
         oracle_step(ctx, wl, nu_ext, per_step)
     ev, secs = 0, 0.0
@@ -229,7 +270,7 @@ def run_reference(args, wl, nu_ext):
         ev += e
         secs += s_
     value = ev / secs
-    sample = sample_text(wl, n_targets, per_step) + " per step"
+    sample = sample_text(wl, n_targets, per_step, plastic) + " per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
@@ -246,14 +287,18 @@ def run_reference(args, wl, nu_ext):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def build_net(wl, fmt, nu_ext, seed, stream, log_cap=0, deliver_mode=0):
+def build_net(wl, fmt, nu_ext, seed, stream, log_cap=0, deliver_mode=0,
+              plastic=False):
     from paper_2109_12855_gb300.tune import build_balanced
+    from paper_2109_12855_gb300 import snn
+    w_e0 = snn.snn_psc_weight_for_psp(snn.params(), wl.psp_mv)
     net, w_e = build_balanced(wl.n_e, wl.n_i, wl.k_e, wl.k_i, wl.d_lo, wl.d_hi,
                               fmt, wl.sd_rel, seed, stream, psp_mv=wl.psp_mv,
                               g=wl.g, nu_ext=nu_ext,
+                              stdp=snn.stdp_params(**stdp_config(w_e0))
+                              if plastic else None,
                               spike_log_capacity=log_cap,
                               deliver_mode=deliver_mode)
-    from paper_2109_12855_gb300 import snn
     snn.snn_set_drive(net.h, nu_ext, w_e)
     return net, w_e
 
@@ -310,8 +355,9 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
 
     t_build = time.perf_counter()
     mode = {"tiled": 0, "atomic": 1}[args.deliver_mode]
+    plastic = args.workload in PLASTIC
     net, w_e = build_net(wl, fmt, nu_ext, 1 + rank, stream, log_cap=log_cap,
-                         deliver_mode=mode)
+                         deliver_mode=mode, plastic=plastic)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t_build
     h = net.h
@@ -380,11 +426,13 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
     ms_upd = b.ms_update - a.ms_update
     ev_prof = b.events_delivered - a.events_delivered
     sp_prof = b.spikes - a.spikes
+    pl_prof = b.plastic_events - a.plastic_events
     net.read_spikes(log_cap)
     # algorithmic bytes: one record per event; per spike a list entry (16 B)
-    # and its two row offsets (16 B)
+    # and its two row offsets (16 B); a plastic event also reads and writes
+    # its FP32 weight (8 B)
     n_listed = sp_prof if kind == "simulate" else len(src) * args.steps
-    alg_bytes = rec_bytes * ev_prof + 32 * n_listed
+    alg_bytes = rec_bytes * ev_prof + 32 * n_listed + 8 * pl_prof
     per_launch_bytes = alg_bytes / max(n_del, 1)
     per_launch_s = ms_del * 1e-3 / max(n_del, 1)
     hbm, peak_kind = peaks()
@@ -427,13 +475,13 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
         return
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        ctx = oracle_sample(wl, nu_ext, args.oracle_targets)
+        ctx = oracle_sample(wl, nu_ext, args.oracle_targets, plastic=plastic)
+        n_iv = args.cpu_intervals if not plastic else min(args.cpu_intervals, 150)
         oracle_step(ctx, wl, nu_ext, 5)
-        e_c, s_c = oracle_step(ctx, wl, nu_ext, args.cpu_intervals)
+        e_c, s_c = oracle_step(ctx, wl, nu_ext, n_iv)
         cpu = {"value": e_c / s_c, "unit": UNIT, "cores": 1, "kind": "oracle",
                "seconds": s_c,
-               "sample": sample_text(wl, args.oracle_targets,
-                                     args.cpu_intervals)}
+               "sample": sample_text(wl, args.oracle_targets, n_iv, plastic)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
@@ -449,6 +497,9 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
                    "mean_rate_hz": spikes_all / ws / wl.n / (
                        args.steps * bio_ms * 1e-3),
                    "events_timed": events_all, "spikes_timed": int(spikes_all),
+                   "plastic": plastic,
+                   **({"stdp": stdp_config(w_e), "plastic_events_profiled": pl_prof,
+                       "stdp_truncated": st.stdp_truncated} if plastic else {}),
                    "build_s": t_build,
                    "l2": "inputs larger than L2 (the record store is "
                          f"{wl.n_synapses * rec_bytes / 1e9:.1f} GB, streamed "
@@ -467,7 +518,7 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
                      "deliver_mode": args.deliver_mode,
                      "tiles": [st_tiles.n_tiles, st_tiles.tile_width,
                                st_tiles.window],
-                     "bytes_per_event": rec_bytes,
+                     "bytes_per_event": rec_bytes + (8 * pl_prof / max(ev_prof, 1)),
                      "ms_deliver_share": ms_del / ms_prof if ms_prof else None,
                      "ms_update_share": ms_upd / ms_prof if ms_prof else None,
                      "profiled_value": ev_prof / (ms_prof * 1e-3)},

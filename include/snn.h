@@ -187,7 +187,8 @@ typedef struct snn_stdp_params {
   double w0;                   /* pA: weight scale of the power law */
   double w_max;                /* pA: upper bound (also bounds the exact
                                   accumulation of the delivery kernel) */
-  int32_t history;             /* post spikes kept per neuron, 2..32; a
+  int32_t history;             /* post spikes kept per neuron: a power of
+                                  two, 2..32; a
                                   window that reaches past them is counted
                                   in snn_stats.stdp_truncated */
   int32_t reserved_;           /* 0 */

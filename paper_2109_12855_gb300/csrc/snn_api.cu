@@ -769,8 +769,8 @@ int setup_stdp(snn_net* net) {
   CK(cudaMemsetAsync(sp.ring_k, 0, H * net->pitch * sizeof(float), s));
   sp.n_exc = net->p.n_exc;
   sp.hist = (uint32_t)H;
-  sp.dt_plus = (float)(net->p.h / q.tau_plus);
-  sp.dt_minus = (float)(net->p.h / q.tau_minus);
+  sp.l2_plus = (float)(M_LOG2E * net->p.h / q.tau_plus);
+  sp.l2_minus = (float)(M_LOG2E * net->p.h / q.tau_minus);
   sp.c_pot = (float)(q.lambda * pow(q.w0, 1.0 - q.mu));
   sp.c_dep = (float)(q.lambda * q.alpha);
   sp.mu = (float)q.mu;
@@ -1332,8 +1332,10 @@ int snn_set_stdp(snn_net* net, const snn_stdp_params* q) {
           q->mu >= 0 && q->mu <= 1 && q->w0 > 0 && q->w_max > 0 &&
           isfinite(q->lambda) && isfinite(q->alpha) && isfinite(q->w_max),
       SNN_E_ARG, "bad STDP parameters");
-  REQ(q->history >= 2 && q->history <= kMaxStdpHistory, SNN_E_ARG,
-      "STDP history %d outside [2, %d]", q->history, kMaxStdpHistory);
+  REQ(q->history >= 2 && q->history <= kMaxStdpHistory &&
+          (q->history & (q->history - 1)) == 0,
+      SNN_E_ARG, "STDP history %d is not a power of two in [2, %d]",
+      q->history, kMaxStdpHistory);
   REQ(net->p.deliver_mode == SNN_DELIVER_TILED, SNN_E_ARG,
       "STDP needs deliver_mode SNN_DELIVER_TILED");
   net->stdp = *q;

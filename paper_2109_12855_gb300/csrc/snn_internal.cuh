@@ -99,8 +99,8 @@ struct StdpView {
   float* ring_k;        // [hist][pitch] postsynaptic trace right after each
   uint32_t* ring_n;     // [n] spikes so far (ring position = count mod hist)
   uint32_t n_exc;       // plastic: source < n_exc and target < n_exc
-  uint32_t hist;
-  float dt_plus, dt_minus;  // h / tau_plus, h / tau_minus
+  uint32_t hist;        // a power of two
+  float l2_plus, l2_minus;  // log2(e) h / tau_plus, log2(e) h / tau_minus
   float c_pot;              // lambda w0^(1 - mu)
   float c_dep;              // lambda alpha
   float mu, w_max;

@@ -157,15 +157,16 @@ __device__ __forceinline__ void stdp_on_spike(const StdpView& sp, uint32_t i,
   sp.prev_t[i] = tl;
   sp.prev_k[i] = kl;
   sp.pre_k[i] =
-      (tl == kNoSpike ? 0.f : kl * expf(-(float)(t - tl) * sp.dt_plus)) + 1.f;
+      (tl == kNoSpike ? 0.f : kl * exp2f(-(float)(t - tl) * sp.l2_plus)) + 1.f;
   sp.pre_t[i] = t;
   const uint32_t n = sp.ring_n[i];
+  const uint32_t hm = sp.hist - 1u;
   float km = 0.f;
   if (n) {
-    const size_t last = (size_t)((n - 1u) % sp.hist) * pitch + i;
-    km = sp.ring_k[last] * expf(-(float)(t - sp.ring_t[last]) * sp.dt_minus);
+    const size_t last = (size_t)((n - 1u) & hm) * pitch + i;
+    km = sp.ring_k[last] * exp2f(-(float)(t - sp.ring_t[last]) * sp.l2_minus);
   }
-  const size_t slot = (size_t)(n % sp.hist) * pitch + i;
+  const size_t slot = (size_t)(n & hm) * pitch + i;
   sp.ring_t[slot] = t;
   sp.ring_k[slot] = km + 1.f;
   sp.ring_n[i] = n + 1u;
@@ -624,41 +625,55 @@ __device__ FixScale fix_scale(const NetView& v, uint64_t n_sp,
 // potentiation owed to the post spikes seen since the previous pre spike,
 // in time order, then the depression by the post trace at t; weights stay in
 // [0, w_max].  tprev / kprev: the previous pre spike and the presynaptic
-// trace right after it.  Post spikes of target j come from the CTA's copy
-// of the last hist spikes (rt, rk: [hist][TW]; rn: spikes so far).  *trunc
-// counts updates whose window reached past the kept spikes.
-__device__ __forceinline__ float stdp_weight(
-    const StdpView& sp, float w, int32_t t, uint32_t d, int32_t tprev,
-    float kprev, uint32_t j, uint32_t TW, const int32_t* rt, const float* rk,
-    const uint32_t* rn, uint32_t* trunc) {
-  const uint32_t H = sp.hist;
-  const uint32_t n = rn[j];
+// trace right after it.  The post spikes of target j come from the CTA's
+// copy of the last hist spikes (rt, rk: [hist][TW]; n: spikes so far).
+// Compiled once (not inlined into every unrolled record slot: the code would
+// no longer fit the instruction cache).  .trunc = 1 when the potentiation
+// window or the depression trace reached past the kept spikes.
+struct StdpConst {
+  float c_pot, c_dep, mu, w_max, l2_plus, l2_minus;
+  uint32_t hmask;
+};
+struct StdpOut {
+  float w;
+  uint32_t trunc;
+};
+
+__device__ __noinline__ StdpOut stdp_weight(float w, int32_t t, uint32_t d,
+                                            int32_t tprev, float kprev,
+                                            uint32_t j, uint32_t TW,
+                                            const int32_t* rt, const float* rk,
+                                            uint32_t n, StdpConst c) {
+  const uint32_t H = c.hmask + 1u;
   const int32_t horizon = t - (int32_t)d;  // post spikes seen by step t
   const bool has_prev = tprev != kNoSpike;
   const int32_t after = has_prev ? tprev - (int32_t)d : 0;
   const int32_t k_min = n > H ? (int32_t)(n - H) : 0;
   int32_t k_dep = -1, k_lo = -1, k = (int32_t)n - 1;
   for (; k >= k_min; --k) {
-    const int32_t tp = rt[(uint32_t)k % H * TW + j];
+    const int32_t tp = rt[((uint32_t)k & c.hmask) * TW + j];
     if (tp > horizon) continue;
     if (k_dep < 0) k_dep = k;
     if (!has_prev || tp <= after) break;
     k_lo = k;
   }
-  if (k < k_min && n > H && (has_prev || k_dep < 0)) *trunc += 1u;
+  StdpOut o;
+  o.trunc = (k < k_min && n > H && (has_prev || k_dep < 0)) ? 1u : 0u;
   if (k_lo >= 0) {
     for (int32_t q = k_lo; q <= k_dep; ++q) {
-      const int32_t tp = rt[(uint32_t)q % H * TW + j];
-      const float kp = kprev * expf(-(float)(tp + (int32_t)d - tprev) * sp.dt_plus);
-      w = fminf(w + sp.c_pot * powf(w, sp.mu) * kp, sp.w_max);
+      const int32_t tp = rt[((uint32_t)q & c.hmask) * TW + j];
+      const float kp = kprev * exp2f(-(float)(tp + (int32_t)d - tprev) * c.l2_plus);
+      const float wm = w > 0.f ? exp2f(c.mu * log2f(w)) : 0.f;
+      w = fminf(w + c.c_pot * wm * kp, c.w_max);
     }
   }
   if (k_dep >= 0) {
-    const uint32_t e = (uint32_t)k_dep % H * TW + j;
-    const float km = rk[e] * expf(-(float)(horizon - rt[e]) * sp.dt_minus);
-    w = fmaxf(w - sp.c_dep * w * km, 0.f);
+    const uint32_t e = ((uint32_t)k_dep & c.hmask) * TW + j;
+    const float km = rk[e] * exp2f(-(float)(horizon - rt[e]) * c.l2_minus);
+    w = fmaxf(w - c.c_dep * w * km, 0.f);
   }
-  return w;
+  o.w = w;
+  return o;
 }
 
 template <int FMT, bool COUNT, bool PL>
@@ -753,13 +768,25 @@ __device__ __forceinline__ void deliver_tile_body(
   };
 
   // plastic E->E synapse: update its weight (record index r), store it
+  StdpConst sc{};
+  if (PL) {
+    sc.c_pot = v.sp.c_pot;
+    sc.c_dep = v.sp.c_dep;
+    sc.mu = v.sp.mu;
+    sc.w_max = v.sp.w_max;
+    sc.l2_plus = v.sp.l2_plus;
+    sc.l2_minus = v.sp.l2_minus;
+    sc.hmask = v.sp.hist - 1u;
+  }
   auto plastic = [&](uint32_t tgt, uint32_t k_run, int32_t t, uint32_t d,
                      float w, uint64_t r) -> float {
-    w = stdp_weight(v.sp, w, t, d, s_tprev[k_run], s_kprev[k_run], tgt - tgt_lo,
-                    TW, s_rt, s_rk, s_rn, &my_trunc);
-    v.sp.wp[r] = w;
+    const uint32_t j = tgt - tgt_lo;
+    const StdpOut o = stdp_weight(w, t, d, s_tprev[k_run], s_kprev[k_run], j,
+                                  TW, s_rt, s_rk, s_rn[j], sc);
+    v.sp.wp[r] = o.w;
     ++my_pl;
-    return w;
+    my_trunc += o.trunc;
+    return o.w;
   };
   auto load_pass = [&](Rec1<FMT> (&r)[U][PER], float (&wv)[U][PER], uint32_t k0,
                        uint32_t nb) {

@@ -18,11 +18,13 @@ import numpy as np
 
 
 def build_balanced(n_e, n_i, k_e, k_i, d_lo, d_hi, fmt, sd_rel, seed, stream,
-                   psp_mv=0.1, g=5.0, **pkw):
+                   psp_mv=0.1, g=5.0, stdp=None, **pkw):
     from . import snn
     p = snn.params(n_exc=n_e, n_inh=n_i, weight_format=fmt, seed=seed, **pkw)
     w_e = snn.snn_psc_weight_for_psp(p, psp_mv)
     net = snn.Net(p, stream)
+    if stdp is not None:
+        snn.snn_set_stdp(net.h, stdp)
     net.connect_fixed_indegree(snn.conn_params(
         k_exc=k_e, k_inh=k_i, w_exc=w_e, w_inh=-g * w_e, sd_exc=sd_rel * w_e,
         sd_inh=sd_rel * g * w_e, d_lo=d_lo, d_hi=d_hi, seed=seed + 1000,

@@ -151,7 +151,7 @@ def test_plastic_net_rejects_caller_lists_and_checkpoints():
             snn.snn_set_stdp(net.h, snn.stdp_params())
     p = snn.params(n_exc=10, n_inh=0)
     with snn.Net(p, stream()) as n2:
-        for bad in (dict(history=1), dict(history=33), dict(mu=1.5),
+        for bad in (dict(history=1), dict(history=33), dict(history=12), dict(mu=1.5),
                     dict(tau_plus=0.0), dict(w_max=-1.0)):
             with pytest.raises(snn.SnnError) as e:
                 snn.snn_set_stdp(n2.h, snn.stdp_params(**bad))
