@@ -45,6 +45,9 @@ WORKLOADS = {
     "balanced-112500-bf16": (W.BALANCED_112500, 1, 1000.0, "simulate"),
     "balanced-562500-bf16": (W.BALANCED_562500, 1, 500.0, "simulate"),
     "balanced-1250-fp32": (W.BALANCED_1250, 0, 1000.0, "simulate"),
+    # long run: 10 s of biological time per step, rates per second and the
+    # CV of the intervals from the FP64 accumulators (drift check)
+    "long-112500-fp32": (W.BALANCED_112500, 0, 10000.0, "long"),
     # plastic variant: E->E synapses with power-law STDP (FP32 weights
     # updated at delivery), the other synapses static BF16
     "balanced-112500-stdp-bf16": (W.BALANCED_112500, 1, 1000.0, "simulate"),
@@ -390,6 +393,16 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
                     snn.lib().snn_deliver(h, d_src.data_ptr() + 4 * a,
                                           d_t.data_ptr() + 4 * a, b - a,
                                           snn.SNN_MEM_DEVICE, None)
+    elif kind == "long":
+        # a long run in 1 s pieces: spikes per second for the drift check
+        per_s = []
+        one_s = int(round(1000.0 / 0.1))
+
+        def step():
+            for _ in range(int(round(bio_ms / 1000.0))):
+                before = net.stats().spikes
+                snn.snn_simulate(h, one_s)
+                per_s.append((net.stats().spikes - before) / wl.n)
     else:
         def step():
             snn.snn_simulate(h, steps_per)
@@ -398,6 +411,9 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
         step()
     torch.cuda.synchronize()
     net.read_spikes(log_cap)      # empty the log
+    if kind == "long":
+        per_s.clear()
+        snn.snn_clear_spike_stats(h)
 
     # ---- timed region: production path (graphs) --------------------------
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) \
@@ -414,6 +430,16 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
     net.read_spikes(log_cap)
     ms_max, events_all, spikes_all = reduce_over_ranks(ms, events, spikes)
     value = events_all / (ms_max * 1e-3)
+    long_run = None
+    if kind == "long":
+        r = np.array(per_s[:int(round(bio_ms / 1000.0))])
+        _, n_isi, s1, s2 = snn.snn_read_spike_stats(h, wl.n)
+        ok = n_isi >= 2
+        m = s1[ok] / n_isi[ok]
+        cv = float(np.mean(np.sqrt(np.maximum(s2[ok] / n_isi[ok] - m * m, 0)) / m))
+        long_run = {"rate_hz_per_s": [round(float(x), 4) for x in r],
+                    "max_rel_drift": float(np.max(np.abs(r / r.mean() - 1.0))),
+                    "cv_isi": cv, "neurons_with_2_intervals": int(ok.sum())}
 
     # ---- roofline: the same steps with every launch between CUDA events ----
     snn.snn_set_profiling(h, True)
@@ -431,7 +457,7 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
     # algorithmic bytes: one record per event; per spike a list entry (16 B)
     # and its two row offsets (16 B); a plastic event also reads and writes
     # its FP32 weight (8 B)
-    n_listed = sp_prof if kind == "simulate" else len(src) * args.steps
+    n_listed = sp_prof if kind != "deliver" else len(src) * args.steps
     alg_bytes = rec_bytes * ev_prof + 32 * n_listed + 8 * pl_prof
     per_launch_bytes = alg_bytes / max(n_del, 1)
     per_launch_s = ms_del * 1e-3 / max(n_del, 1)
@@ -528,6 +554,8 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
         "clocks": clk,
         "error_flags": err,
     }
+    if long_run:
+        line["long_run"] = long_run
     print(json.dumps(line), flush=True)
 
 

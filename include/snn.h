@@ -326,6 +326,18 @@ int snn_write_state(snn_net* net, const float* V, const float* I,
  * SNN_E_STATE if the net is already connected. */
 int snn_set_stdp(snn_net* net, const snn_stdp_params* p);
 
+/* Long-run spike statistics, kept per neuron by snn_update / snn_simulate
+ * (not by the batched steps of a server): spikes counted, inter-spike
+ * intervals counted, and FP64 sums of the intervals and of their squares,
+ * in steps (integers, so the sums are exact below 2^53).  The mean rate is
+ * n_spikes / time and the CV of the intervals sqrt(sq/n - (sum/n)^2) /
+ * (sum/n).  Host arrays of N entries (any may be NULL); synchronises. */
+int snn_read_spike_stats(snn_net* net, uint32_t* n_spikes, uint32_t* n_isi,
+                         double* isi_sum, double* isi_sq);
+/* Zero the counts and sums (the latest spike times are kept, so the first
+ * interval after a clear is counted whole). */
+int snn_clear_spike_stats(snn_net* net);
+
 /* Current weight of every synapse in store order (the order of
  * snn_read_store): n_synapses floats into w (host or device memory per
  * mem).  Static synapses return their stored weight. */

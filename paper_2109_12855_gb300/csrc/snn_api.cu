@@ -587,6 +587,11 @@ int snn_create(const snn_params* p, void* stream, snn_net** out) {
   ALLOC(net->rb, rb_bytes);
   ALLOC(net->ctl, sizeof(Ctl));
   if (p->count_events) ALLOC(net->counts, rb_bytes);
+  ALLOC(net->isi_last, n * sizeof(int32_t));
+  ALLOC(net->isi_spikes, n * sizeof(uint32_t));
+  ALLOC(net->isi_n, n * sizeof(uint32_t));
+  ALLOC(net->isi_sum, n * sizeof(double));
+  ALLOC(net->isi_sq, n * sizeof(double));
   if (p->spike_log_capacity) {
     ALLOC(net->log_src, p->spike_log_capacity * sizeof(uint32_t));
     ALLOC(net->log_t, p->spike_log_capacity * sizeof(int32_t));
@@ -597,6 +602,12 @@ int snn_create(const snn_params* p, void* stream, snn_net** out) {
       cudaMemsetAsync(net->ctl, 0, sizeof(Ctl), s) != cudaSuccess ||
       (net->counts && cudaMemsetAsync(net->counts, 0, rb_bytes, s) != cudaSuccess))
     return bail(fail(SNN_E_CUDA, "memset failed"));
+  if (launch_fill_i32(net->isi_last, kNoSpike, n, s) != cudaSuccess ||
+      cudaMemsetAsync(net->isi_spikes, 0, n * sizeof(uint32_t), s) != cudaSuccess ||
+      cudaMemsetAsync(net->isi_n, 0, n * sizeof(uint32_t), s) != cudaSuccess ||
+      cudaMemsetAsync(net->isi_sum, 0, n * sizeof(double), s) != cudaSuccess ||
+      cudaMemsetAsync(net->isi_sq, 0, n * sizeof(double), s) != cudaSuccess)
+    return bail(fail(SNN_E_CUDA, "statistics initialisation failed"));
   NetView v = net->view();
   if (launch_init_v(v, &net->uc, p->init_v_random, s) != cudaSuccess)
     return bail(fail(SNN_E_CUDA, "init kernel launch failed"));
@@ -1343,6 +1354,36 @@ int snn_set_stdp(snn_net* net, const snn_stdp_params* q) {
   return SNN_OK;
 }
 
+int snn_read_spike_stats(snn_net* net, uint32_t* n_spikes, uint32_t* n_isi,
+                         double* isi_sum, double* isi_sq) {
+  REQ(net, SNN_E_ARG, "null net");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  const size_t n = net->n;
+  if (n_spikes)
+    CK(cudaMemcpyAsync(n_spikes, net->isi_spikes, n * 4, cudaMemcpyDeviceToHost, s));
+  if (n_isi) CK(cudaMemcpyAsync(n_isi, net->isi_n, n * 4, cudaMemcpyDeviceToHost, s));
+  if (isi_sum)
+    CK(cudaMemcpyAsync(isi_sum, net->isi_sum, n * 8, cudaMemcpyDeviceToHost, s));
+  if (isi_sq) CK(cudaMemcpyAsync(isi_sq, net->isi_sq, n * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return SNN_OK;
+}
+
+int snn_clear_spike_stats(snn_net* net) {
+  REQ(net, SNN_E_ARG, "null net");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  const size_t n = net->n;
+  CK(cudaMemsetAsync(net->isi_spikes, 0, n * 4, s));
+  CK(cudaMemsetAsync(net->isi_n, 0, n * 4, s));
+  CK(cudaMemsetAsync(net->isi_sum, 0, n * 8, s));
+  CK(cudaMemsetAsync(net->isi_sq, 0, n * 8, s));
+  return SNN_OK;
+}
+
 int snn_read_weights(snn_net* net, float* w, int32_t mem) {
   REQ(net && w, SNN_E_ARG, "null argument");
   REQ(net->finalized, SNN_E_STATE, "net not finalized");
@@ -1396,6 +1437,9 @@ int snn_destroy(snn_net* net) {
                   net->recs,     net->list,     net->ext_list, net->ext_src,
                   net->ext_t,    net->log_src,  net->log_t,   net->tile_off};
   for (void* b : bufs) dfree(b, net->stream);
+  void* ibufs[] = {net->isi_last, net->isi_spikes, net->isi_n, net->isi_sum,
+                   net->isi_sq};
+  for (void* b : ibufs) dfree(b, net->stream);
   void* sbufs[] = {net->sp.wp,     net->sp.pre_t,  net->sp.prev_t,
                    net->sp.pre_k,  net->sp.prev_k, net->sp.ring_t,
                    net->sp.ring_k, net->sp.ring_n};

@@ -226,6 +226,12 @@ struct NetView {
   Ctl* ctl;
   int plastic;              // STDP on (state in sp)
   StdpView sp;
+  // long-run spike statistics (FP64 sums of integer inter-spike intervals)
+  int32_t* isi_last;        // [n] latest spike step (kNoSpike if none)
+  uint32_t* isi_spikes;     // [n] spikes counted
+  uint32_t* isi_n;          // [n] intervals counted
+  double* isi_sum;          // [n] sum of intervals (steps)
+  double* isi_sq;           // [n] sum of squared intervals
 };
 
 // One net of a batch advanced by the batched kernels (device table entry).

@@ -174,6 +174,8 @@ __device__ __forceinline__ void stdp_on_spike(const StdpView& sp, uint32_t i,
 
 // Body of the update for neuron block `block` of net v (one thread per
 // neuron); shared by the single-net and the batched kernels.
+// PL: the single-net update, which also keeps the plasticity state and the
+// long-run spike statistics (the batched serving update does neither).
 template <bool PL>
 __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
                                             int n_steps, int from_ctl,
@@ -319,6 +321,17 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
         }
         if (PL && v.plastic && i < v.sp.n_exc)
           stdp_on_spike(v.sp, i, (int32_t)t, v.pitch);
+        if (PL && v.isi_spikes) {
+          const int32_t tl = v.isi_last[i];
+          if (tl != kNoSpike) {
+            const double d = (double)((int32_t)t - tl);  // exact in FP64
+            v.isi_sum[i] += d;
+            v.isi_sq[i] += d * d;
+            v.isi_n[i] += 1u;
+          }
+          v.isi_last[i] = (int32_t)t;
+          v.isi_spikes[i] += 1u;
+        }
         ++k;
       }
       __syncthreads();  // s_base is rewritten by the next chunk

@@ -69,6 +69,12 @@ struct snn_net {
   bool stdp_on = false;
   snn_stdp_params stdp{};
   StdpView sp{};
+  // long-run spike statistics
+  int32_t* isi_last = nullptr;
+  uint32_t* isi_spikes = nullptr;
+  uint32_t* isi_n = nullptr;
+  double* isi_sum = nullptr;
+  double* isi_sq = nullptr;
 
   NetView view() const {
     NetView v;
@@ -103,6 +109,11 @@ struct snn_net {
     v.ctl = ctl;
     v.plastic = stdp_on && sp.wp != nullptr;
     v.sp = sp;
+    v.isi_last = isi_last;
+    v.isi_spikes = isi_spikes;
+    v.isi_n = isi_n;
+    v.isi_sum = isi_sum;
+    v.isi_sq = isi_sq;
     return v;
   }
 };

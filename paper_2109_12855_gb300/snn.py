@@ -38,7 +38,7 @@ EXPORTS = [
     "snn_destroy", "snn_server_create", "snn_server_submit", "snn_server_step",
     "snn_server_poll", "snn_server_spikes", "snn_server_release",
     "snn_server_get_stats", "snn_server_destroy", "snn_set_stdp",
-    "snn_read_weights",
+    "snn_read_weights", "snn_read_spike_stats", "snn_clear_spike_stats",
 ]
 SNN_REQ_QUEUED, SNN_REQ_BUILDING, SNN_REQ_RUNNING, SNN_REQ_DONE = 0, 1, 2, 3
 SNN_REQ_FAILED = -1
@@ -174,6 +174,8 @@ def lib():
             "snn_destroy": ([_P], C.c_int),
             "snn_set_stdp": ([_P, C.POINTER(snn_stdp_params)], C.c_int),
             "snn_read_weights": ([_P, _P, C.c_int32], C.c_int),
+            "snn_read_spike_stats": ([_P, _P, _P, _P, _P], C.c_int),
+            "snn_clear_spike_stats": ([_P], C.c_int),
             "snn_server_create": ([C.c_uint64, C.c_int32, _P, C.POINTER(_P)],
                                   C.c_int),
             "snn_server_submit": ([_P, C.POINTER(snn_request),
@@ -361,6 +363,21 @@ def snn_set_stdp(net, q: snn_stdp_params):
 def snn_read_weights(net, w):
     mem = _mem_of(w)
     _check(lib().snn_read_weights(net, _buf(w)[0], mem))
+
+
+def snn_read_spike_stats(net, n: int):
+    """(spikes, intervals, interval sum, interval square sum) per neuron."""
+    a = np.zeros(n, np.uint32)
+    b = np.zeros(n, np.uint32)
+    c = np.zeros(n, np.float64)
+    d = np.zeros(n, np.float64)
+    _check(lib().snn_read_spike_stats(net, a.ctypes.data, b.ctypes.data,
+                                      c.ctypes.data, d.ctypes.data))
+    return a, b, c, d
+
+
+def snn_clear_spike_stats(net):
+    _check(lib().snn_clear_spike_stats(net))
 
 
 def snn_state_size(net) -> int:
