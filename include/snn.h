@@ -125,6 +125,17 @@ typedef struct snn_params {
                              automatic choice (about N / #SMs), otherwise used
                              as given when its shared-memory window fits */
   int32_t reserved_;
+  uint32_t part_lo, part_hi; /* target partition: this net holds neurons
+                             [part_lo, part_hi) of the population of n_exc +
+                             n_inh neurons and the synapses of all sources
+                             onto them (0, 0: the whole population).  Neuron
+                             indices in spike lists, the spike log and the
+                             random streams are global; state and ring-buffer
+                             arrays are local (part_hi - part_lo entries).
+                             Partitions exchange their interval lists (see
+                             snn_read_pending) and agree on the accumulation
+                             bounds (snn_get_bounds / snn_set_bounds) so that
+                             their union equals the whole net bit for bit. */
 } snn_params;
 
 /* Fixed in-degree connection rule (the benchmark model's random
@@ -168,7 +179,17 @@ typedef struct snn_stats {
   uint64_t plastic_events;      /* plastic weight updates (STDP nets) */
   uint64_t stdp_truncated;      /* of which the post-spike window reached
                                    past the kept history (see snn_set_stdp) */
+  uint32_t first_neuron;        /* global index of local neuron 0 */
+  uint32_t n_sources;           /* rows of the store (the whole population) */
 } snn_stats;
+
+/* Bounds of one delivery launch's exact accumulation (see snn_set_bounds). */
+typedef struct snn_bounds {
+  uint32_t mult_max;  /* most synapses sharing (source, target, delay) */
+  uint32_t k_in_max;  /* largest in-degree */
+  float max_abs_w;    /* largest |weight| */
+  uint32_t reserved_; /* 0 */
+} snn_bounds;
 
 /* Pair-based power-law STDP of the excitatory-to-excitatory synapses
  * (arXiv 2109.12855, Section 6: plasticity as an update scheme driven by
@@ -325,6 +346,37 @@ int snn_write_state(snn_net* net, const float* V, const float* I,
  * read them with snn_read_weights.  SNN_E_ARG for bad parameters,
  * SNN_E_STATE if the net is already connected. */
 int snn_set_stdp(snn_net* net, const snn_stdp_params* p);
+
+/* The pending interval list of the last snn_update (before its delivery):
+ * global source indices and emission steps, n entries (*n; up to cap are
+ * copied).  Partitions gather these lists from each other (all-gather) and
+ * deliver the union to themselves with snn_deliver after
+ * snn_discard_pending.  mem: SNN_MEM_HOST or SNN_MEM_DEVICE for src / t.
+ * Synchronises.  SNN_E_STATE without a pending update, SNN_E_OVERFLOW when
+ * n > cap. */
+int snn_read_pending(snn_net* net, uint32_t* src, int32_t* t, uint64_t cap,
+                     uint64_t* n, int32_t mem);
+
+/* Deliver the spike list gathered from all partitions of a partitioned
+ * network as this interval's list: like snn_deliver_pending, with the
+ * pending list of the last snn_update replaced by src / t (global sources;
+ * host or device memory per mem).  The list must be an interval list (every
+ * neuron at most once per refractory period plus one step), so the same
+ * accumulation bounds as snn_deliver_pending apply and a partition sums
+ * exactly as the whole net does.  Advances the clock; *n_events_out (may be
+ * NULL) receives the events delivered into this partition.  SNN_E_STATE
+ * without a pending update, SNN_E_OVERFLOW beyond N x interval spikes. */
+int snn_deliver_gathered(snn_net* net, const uint32_t* src,
+                         const int32_t* t_emit, uint32_t n_spikes, int mem,
+                         uint64_t* n_events_out);
+
+/* Accumulation bounds of the store (finalized nets).  The tiled delivery
+ * sums each ring-buffer cell exactly in fixed point with scales derived
+ * from these bounds; partitions of one network take the maximum of their
+ * bounds (snn_set_bounds raises each field to at least the given value) so
+ * that they round every event the way the whole net does. */
+int snn_get_bounds(snn_net* net, snn_bounds* out);
+int snn_set_bounds(snn_net* net, const snn_bounds* b);
 
 /* Long-run spike statistics, kept per neuron by snn_update / snn_simulate
  * (not by the batched steps of a server): spikes counted, inter-spike

@@ -317,7 +317,7 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
                 const BuildFixed* bf, const double* d_edge_w, int d_lo,
                 int d_hi) {
   cudaStream_t s = net->stream;
-  const uint32_t n = net->n;
+  const uint32_t n = net->n_src;  // rows: every source of the population
   std::vector<uint32_t> deg(n);
   CK(cudaMemcpyAsync(deg.data(), d_deg, n * sizeof(uint32_t),
                      cudaMemcpyDeviceToHost, s));
@@ -347,7 +347,7 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
                      cudaMemcpyHostToDevice, s));
   // tiles sized for the widest window the interval can reach
   const int iv = net->p.interval ? net->p.interval : d_lo;
-  choose_tiles(n, iv + (d_hi - d_lo), net->p.tile_width,
+  choose_tiles(net->n, iv + (d_hi - d_lo), net->p.tile_width,
                stdp_bytes_per_target(net), &net->tile_w, &net->lo_bits,
                &net->n_tiles);
   CK(dalloc(&net->tile_off, (uint64_t)n * (net->n_tiles + 1) * sizeof(uint32_t), net->stream));
@@ -544,10 +544,17 @@ int snn_create(const snn_params* p, void* stream, snn_net** out) {
   REQ(p->deliver_mode == SNN_DELIVER_TILED || p->deliver_mode == SNN_DELIVER_ATOMIC,
       SNN_E_ARG, "bad deliver_mode %d", p->deliver_mode);
   REQ(p->tile_width >= 0, SNN_E_ARG, "bad tile_width %d", p->tile_width);
+  const bool part = p->part_hi != 0 || p->part_lo != 0;
+  REQ(!part || (p->part_lo < p->part_hi && p->part_hi <= n), SNN_E_ARG,
+      "partition [%u, %u) outside [0, %llu)", p->part_lo, p->part_hi,
+      (unsigned long long)n);
+  const uint64_t n_loc = part ? (uint64_t)(p->part_hi - p->part_lo) : n;
   snn_net* net = new snn_net();
   net->p = *p;
-  net->n = (uint32_t)n;
-  net->pitch = (uint32_t)((n + 31) / 32 * 32);
+  net->n = (uint32_t)n_loc;
+  net->n_src = (uint32_t)n;
+  net->g0 = part ? p->part_lo : 0u;
+  net->pitch = (uint32_t)((n_loc + 31) / 32 * 32);
   net->fmt = p->weight_format;
   net->n_slots = p->n_slots;
   if (make_upd_const(*p, &net->uc) != 0) {
@@ -643,9 +650,11 @@ int snn_connect_fixed_indegree(snn_net* net, const snn_conn_params* c) {
   b.seed = c->seed;
   b.clip_e = c->clip_exc;
   b.clip_i = c->clip_inh;
+  b.n_tgt = net->n;
+  b.tgt0 = net->g0;
   uint32_t* deg = nullptr;
-  CK(dalloc(&deg, net->n * sizeof(uint32_t), net->stream));
-  CK(cudaMemsetAsync(deg, 0, net->n * sizeof(uint32_t), net->stream));
+  CK(dalloc(&deg, net->n_src * sizeof(uint32_t), net->stream));
+  CK(cudaMemsetAsync(deg, 0, net->n_src * sizeof(uint32_t), net->stream));
   cudaError_t e = build_count_fixed(b, deg, net->stream);
   if (e != cudaSuccess) {
     dfree(deg, net->stream);
@@ -666,6 +675,8 @@ int snn_connect_fixed_indegree(snn_net* net, const snn_conn_params* c) {
 int snn_connect_edges(snn_net* net, const uint32_t* src, const uint32_t* tgt,
                       const uint8_t* delay, const double* w, uint64_t n,
                       int mem) {
+  REQ(net && net->g0 == 0 && net->n == net->n_src, SNN_E_ARG,
+      "explicit edge lists are not supported for target partitions");
   REQ(net, SNN_E_ARG, "null net");
   REQ(!net->connected && !net->finalized, SNN_E_STATE, "net already connected");
   REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
@@ -800,8 +811,8 @@ int snn_finalize(snn_net* net) {
   cudaStream_t s = net->stream;
   if (!net->connected) {
     // a net without synapses: empty store
-    CK(dalloc(&net->row_ptr, (net->n + 1) * sizeof(uint64_t), net->stream));
-    CK(cudaMemsetAsync(net->row_ptr, 0, (net->n + 1) * sizeof(uint64_t), s));
+    CK(dalloc(&net->row_ptr, (net->n_src + 1) * sizeof(uint64_t), net->stream));
+    CK(cudaMemsetAsync(net->row_ptr, 0, (net->n_src + 1) * sizeof(uint64_t), s));
     CK(dalloc(&net->recs, 4096, net->stream));
     CK(cudaMemsetAsync(net->recs, 0, 4096, s));
     net->n_syn = 0;
@@ -828,7 +839,8 @@ int snn_finalize(snn_net* net) {
   // a neuron fires at most once per refractory period plus one step
   net->spikes_per_iv =
       (uint32_t)((iv + net->uc.refr_steps) / (net->uc.refr_steps + 1));
-  net->list_cap = (uint64_t)net->n * iv;
+  // a partition also takes the gathered list of the whole population
+  net->list_cap = (uint64_t)net->n_src * iv;
   CK(dalloc(&net->list, net->list_cap * sizeof(SpikeEntry), net->stream));
   if (net->stdp_on) {
     int rc2;
@@ -878,6 +890,8 @@ int snn_discard_pending(snn_net* net) {
   if ((rc = set_device(net)) != SNN_OK) return rc;
   CK(cudaMemsetAsync(&net->ctl->pair, 0, sizeof(unsigned long long),
                      net->stream));
+  CK(cudaMemsetAsync(&net->ctl->pending_events, 0, sizeof(unsigned long long),
+                     net->stream));
   CK(cudaMemcpyAsync(&net->ctl->t_now, &net->t_host, sizeof(long long),
                      cudaMemcpyHostToDevice, net->stream));
   CK(cudaStreamSynchronize(net->stream));
@@ -905,7 +919,7 @@ int snn_deliver(snn_net* net, const uint32_t* src, const int32_t* t_emit,
   const int32_t* d_t = t_emit;
   if (mem == SNN_MEM_HOST) {
     for (uint32_t k = 0; k < n_spikes; ++k)
-      REQ(src[k] < net->n, SNN_E_ARG, "spike %u: source %u >= N", k, src[k]);
+      REQ(src[k] < net->n_src, SNN_E_ARG, "spike %u: source %u >= N", k, src[k]);
     CK(cudaMemcpyAsync(net->ext_src, src, n_spikes * 4ull,
                        cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(net->ext_t, t_emit, n_spikes * 4ull,
@@ -938,6 +952,60 @@ int snn_deliver(snn_net* net, const uint32_t* src, const int32_t* t_emit,
     CK(cudaEventElapsedTime(&ms, e0, e1));
     net->ms_deliver += ms;
   }
+  if (n_events_out) {
+    CK(cudaMemcpyAsync(&ev1, &net->ctl->events, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *n_events_out = ev1 - ev0;
+  }
+  return SNN_OK;
+}
+
+int snn_deliver_gathered(snn_net* net, const uint32_t* src,
+                         const int32_t* t_emit, uint32_t n_spikes, int mem,
+                         uint64_t* n_events_out) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  REQ(net->pending, SNN_E_STATE, "no pending interval (call snn_update first)");
+  REQ(!net->stdp_on, SNN_E_STATE, "plastic nets deliver their own spikes");
+  REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
+  REQ(n_spikes == 0 || (src && t_emit), SNN_E_ARG, "null spike arrays");
+  REQ(n_spikes <= net->list_cap, SNN_E_OVERFLOW,
+      "%u gathered spikes exceed the interval list (%llu)", n_spikes,
+      (unsigned long long)net->list_cap);
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  const uint32_t* d_src = src;
+  const int32_t* d_t = t_emit;
+  if (n_spikes && mem == SNN_MEM_HOST) {
+    if ((rc = ensure_ext(net, n_spikes)) != SNN_OK) return rc;
+    for (uint32_t k = 0; k < n_spikes; ++k)
+      REQ(src[k] < net->n_src, SNN_E_ARG, "spike %u: source %u >= N", k, src[k]);
+    CK(cudaMemcpyAsync(net->ext_src, src, n_spikes * 4ull,
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(net->ext_t, t_emit, n_spikes * 4ull,
+                       cudaMemcpyHostToDevice, s));
+    d_src = net->ext_src;
+    d_t = net->ext_t;
+  }
+  unsigned long long ev0 = 0, ev1 = 0;
+  if (n_events_out) {
+    CK(cudaMemcpyAsync(&ev0, &net->ctl->events, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  // the gathered list replaces the update's own list (and its events)
+  CK(cudaMemsetAsync(&net->ctl->pair, 0, sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(&net->ctl->pending_events, 0, sizeof(unsigned long long), s));
+  NetView v = net->view();
+  if (n_spikes) {
+    CK(launch_prepare_external(v, d_src, d_t, n_spikes, net->list,
+                               &net->ctl->pair, s));
+    net->launches += 1;
+  }
+  CK(launch_deliver_any(net, &net->ctl->pair, &net->ctl->done, net->list, 0, 1));
+  net->launches += 1;
+  net->del_launches += 1;
+  net->pending = false;
   if (n_events_out) {
     CK(cudaMemcpyAsync(&ev1, &net->ctl->events, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1153,7 +1221,7 @@ int snn_read_store(snn_net* net, uint64_t* row_ptr, uint32_t* tgt,
   if ((rc = set_device(net)) != SNN_OK) return rc;
   cudaStream_t s = net->stream;
   if (row_ptr)
-    CK(cudaMemcpyAsync(row_ptr, net->row_ptr, (net->n + 1) * 8ull,
+    CK(cudaMemcpyAsync(row_ptr, net->row_ptr, (net->n_src + 1) * 8ull,
                        kind_to(mem), s));
   const uint64_t m = net->n_syn;
   if (m && (tgt || delay || w)) {
@@ -1332,6 +1400,66 @@ int snn_get_stats(snn_net* net, snn_stats* out) {
   out->deliver_mode = use_tiled(net) ? SNN_DELIVER_TILED : SNN_DELIVER_ATOMIC;
   out->plastic_events = c.plastic_events;
   out->stdp_truncated = c.stdp_truncated;
+  out->first_neuron = net->g0;
+  out->n_sources = net->n_src;
+  return SNN_OK;
+}
+
+int snn_read_pending(snn_net* net, uint32_t* src, int32_t* t, uint64_t cap,
+                     uint64_t* n, int32_t mem) {
+  REQ(net && n, SNN_E_ARG, "null argument");
+  REQ(net->pending, SNN_E_STATE, "no pending interval list");
+  REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  unsigned long long pair = 0;
+  CK(cudaMemcpyAsync(&pair, &net->ctl->pair, sizeof pair, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const uint64_t cnt = std::min<uint64_t>(pair >> 32, net->list_cap);
+  *n = cnt;
+  const uint64_t k = std::min(cap, cnt);
+  if (k) {
+    REQ(src && t, SNN_E_ARG, "null output arrays");
+    if (mem == SNN_MEM_DEVICE) {
+      CK(launch_list_to_arrays(net->list, k, src, t, s));
+    } else {
+      std::vector<SpikeEntry> h(k);
+      CK(cudaMemcpyAsync(h.data(), net->list, k * sizeof(SpikeEntry),
+                         cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (uint64_t q = 0; q < k; ++q) {
+        src[q] = h[q].src;
+        t[q] = h[q].t;
+      }
+    }
+    CK(cudaStreamSynchronize(s));
+  }
+  return k < cnt ? fail(SNN_E_OVERFLOW, "%llu pending spikes", (unsigned long long)cnt)
+                 : SNN_OK;
+}
+
+int snn_get_bounds(snn_net* net, snn_bounds* out) {
+  REQ(net && out, SNN_E_ARG, "null argument");
+  REQ(net->connected, SNN_E_STATE, "net not connected");
+  memset(out, 0, sizeof *out);
+  out->mult_max = net->mult_max;
+  out->k_in_max = net->k_in_max;
+  out->max_abs_w = net->max_abs_w;
+  return SNN_OK;
+}
+
+int snn_set_bounds(snn_net* net, const snn_bounds* b) {
+  REQ(net && b, SNN_E_ARG, "null argument");
+  REQ(net->connected, SNN_E_STATE, "net not connected");
+  REQ(isfinite(b->max_abs_w) && b->max_abs_w >= 0.f, SNN_E_ARG, "bad max |w|");
+  net->mult_max = std::max(net->mult_max, b->mult_max);
+  net->k_in_max = std::max(net->k_in_max, b->k_in_max);
+  net->max_abs_w = std::max(net->max_abs_w, b->max_abs_w);
+  if (net->graph) {  // the captured intervals hold the old view
+    cudaGraphExecDestroy(net->graph);
+    net->graph = nullptr;
+  }
   return SNN_OK;
 }
 
@@ -1349,6 +1477,7 @@ int snn_set_stdp(snn_net* net, const snn_stdp_params* q) {
       q->history, kMaxStdpHistory);
   REQ(net->p.deliver_mode == SNN_DELIVER_TILED, SNN_E_ARG,
       "STDP needs deliver_mode SNN_DELIVER_TILED");
+  REQ(net->n == net->n_src, SNN_E_ARG, "STDP is not supported for partitions");
   net->stdp = *q;
   net->stdp_on = true;
   return SNN_OK;

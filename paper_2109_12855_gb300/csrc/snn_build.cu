@@ -53,10 +53,10 @@ __device__ __forceinline__ uint32_t fixed_source(const BuildFixed& b,
 }
 
 __global__ void k_count_fixed(BuildFixed b, uint32_t* deg) {
-  const uint32_t tgt = blockIdx.x;
+  const uint32_t tgt = blockIdx.x;  // local target; draws use the global one
   const uint32_t kk = b.k_e + b.k_i;
   for (uint32_t k = threadIdx.x; k < kk; k += blockDim.x) {
-    U4 r = draw(b.seed, tgt, k, 0u);
+    U4 r = draw(b.seed, b.tgt0 + tgt, k, 0u);
     atomicAdd(&deg[fixed_source(b, k, r.x)], 1u);
   }
 }
@@ -67,7 +67,7 @@ __global__ void k_scatter_fixed(BuildFixed b, const uint64_t* row_ptr,
   const uint32_t kk = b.k_e + b.k_i;
   const uint32_t span = (uint32_t)(b.d_hi - b.d_lo + 1);
   for (uint32_t k = threadIdx.x; k < kk; k += blockDim.x) {
-    U4 r = draw(b.seed, tgt, k, 0u);
+    U4 r = draw(b.seed, b.tgt0 + tgt, k, 0u);
     uint32_t src = fixed_source(b, k, r.x);
     uint32_t d = (uint32_t)b.d_lo + scale_u32(r.y, span);
     uint32_t pos = atomicAdd(&cursor[src], 1u);
@@ -102,7 +102,7 @@ __device__ double weight_of(const BuildFixed& b, const double* edge_w,
   double mean = exc ? b.w_e : b.w_i, sd = exc ? b.sd_e : b.sd_i;
   double x = mean;
   if (sd != 0.0) {
-    U4 r = draw(b.seed, tgt, tie, 0u);
+    U4 r = draw(b.seed, b.tgt0 + tgt, tie, 0u);
     double u1 = ((double)r.z + 1.0) * 0x1p-32;
     double u2 = (double)r.w * 0x1p-32;
     double z = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.14159265358979323846 * u2);
@@ -334,18 +334,16 @@ cudaError_t sort_pack_t(uint32_t n, const uint64_t* row_ptr, uint64_t* keys,
 
 cudaError_t build_count_fixed(const BuildFixed& b, uint32_t* deg,
                               cudaStream_t s) {
-  uint32_t n = b.n_e + b.n_i;
-  if (n == 0 || b.k_e + b.k_i == 0) return cudaSuccess;
-  k_count_fixed<<<n, 256, 0, s>>>(b, deg);
+  if (b.n_tgt == 0 || b.k_e + b.k_i == 0) return cudaSuccess;
+  k_count_fixed<<<b.n_tgt, 256, 0, s>>>(b, deg);
   return cudaGetLastError();
 }
 
 cudaError_t build_scatter_fixed(const BuildFixed& b, const uint64_t* row_ptr,
                                 uint32_t* cursor, uint64_t* keys,
                                 uint32_t tile_w, int lo_bits, cudaStream_t s) {
-  uint32_t n = b.n_e + b.n_i;
-  if (n == 0 || b.k_e + b.k_i == 0) return cudaSuccess;
-  k_scatter_fixed<<<n, 256, 0, s>>>(b, row_ptr, cursor, keys,
+  if (b.n_tgt == 0 || b.k_e + b.k_i == 0) return cudaSuccess;
+  k_scatter_fixed<<<b.n_tgt, 256, 0, s>>>(b, row_ptr, cursor, keys,
                                     TileGeom{tile_w, lo_bits});
   return cudaGetLastError();
 }

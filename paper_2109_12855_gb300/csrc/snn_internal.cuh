@@ -78,6 +78,8 @@ struct Ctl {
   unsigned int ext_done;        // CTAs finished delivering an external list
   unsigned long long ext_pair;  // (spikes << 32) | chunks of an external list
   int ext_tmin, ext_tmax;       // emission-step range of an external list
+  unsigned long long pending_events;  // events of the pending list (moved to
+                                      // events when that list is delivered)
   unsigned long long plastic_events;  // plastic synapse updates (accumulated)
   unsigned long long stdp_truncated;  // updates whose post-spike window
                                       // reached past the kept history
@@ -195,7 +197,9 @@ struct UpdConst {
 
 // Device view of one net.
 struct NetView {
-  uint32_t n;
+  uint32_t n;               // local neurons (targets)
+  uint32_t n_src;           // store rows: sources (the whole population)
+  uint32_t g0;              // global index of local neuron 0
   uint32_t pitch;           // ring-buffer row pitch (floats)
   uint32_t slot_mask;       // n_slots - 1
   uint32_t chunk;           // records per chunk
@@ -281,7 +285,8 @@ cudaError_t launch_deliver_noalloc(const NetView& v, const uint32_t* src,
 
 // store construction
 struct BuildFixed {
-  uint32_t n_e, n_i, k_e, k_i;
+  uint32_t n_e, n_i, k_e, k_i;  // source populations, in-degrees
+  uint32_t n_tgt, tgt0;         // local targets; global index of the first
   double w_e, w_i, sd_e, sd_i;
   int d_lo, d_hi;
   uint64_t seed;
@@ -316,6 +321,8 @@ cudaError_t build_sort_pack(int fmt, uint32_t n, const uint64_t* row_ptr,
                             uint32_t* stats, cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t* p, int32_t value, uint64_t n,
                             cudaStream_t s);
+cudaError_t launch_list_to_arrays(const SpikeEntry* list, uint64_t n,
+                                  uint32_t* src, int32_t* t, cudaStream_t s);
 cudaError_t unpack_store(int fmt, const void* recs, uint64_t n_syn,
                          uint32_t* tgt, uint8_t* delay, float* w,
                          cudaStream_t s);

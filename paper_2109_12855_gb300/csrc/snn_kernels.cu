@@ -51,7 +51,7 @@ __global__ void k_init_state(NetView v, float v_reset, float v_span,
   if (i >= v.n) return;
   float V0 = 0.0f;
   if (random) {
-    U4 r = draw(seed, i, 0, 1u);
+    U4 r = draw(seed, v.g0 + i, 0, 1u);  // keyed by the global index
     double u = (double)r.x * 0x1p-32;
     V0 = (float)((double)v_reset + (double)v_span * u);
   }
@@ -59,6 +59,15 @@ __global__ void k_init_state(NetView v, float v_reset, float v_span,
   v.I[i] = 0.0f;
   v.J[i] = 0.0f;
   v.refr[i] = 0;
+}
+
+__global__ void k_list_to_arrays(const SpikeEntry* list, uint64_t n,
+                                 uint32_t* src, int32_t* t) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    src[k] = list[k].src;
+    t[k] = list[k].t;
+  }
 }
 
 __global__ void k_fill_i32(int32_t* p, int32_t value, uint64_t n) {
@@ -203,7 +212,8 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
     I = v.I[i];
     J = v.J[i];
     refr = v.refr[i];
-    uint64_t beg = v.row_ptr[i], end = v.row_ptr[i + 1];
+    // the neuron's own row (rows are indexed by global source)
+    uint64_t beg = v.row_ptr[v.g0 + i], end = v.row_ptr[v.g0 + i + 1];
     nch = row_chunks(beg, end, v.chunk);
     deg = end - beg;
   }
@@ -231,10 +241,11 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
         // the draws are independent of one another (issued together), and
         // the block drawn last is kept for the next group
         const long long b0 = tf >> 2, bl = (tf + ng - 1) >> 2;
-        const U4 r0 = b0 == rnd_block ? rnd : draw(c.seed, i, (uint64_t)b0, 2u);
+        const uint32_t ig = v.g0 + i;  // drive keyed by the global index
+        const U4 r0 = b0 == rnd_block ? rnd : draw(c.seed, ig, (uint64_t)b0, 2u);
         U4 r1 = r0, r2 = r0;
-        if (bl >= b0 + 1) r1 = draw(c.seed, i, (uint64_t)(b0 + 1), 2u);
-        if (bl >= b0 + 2) r2 = draw(c.seed, i, (uint64_t)(b0 + 2), 2u);
+        if (bl >= b0 + 1) r1 = draw(c.seed, ig, (uint64_t)(b0 + 1), 2u);
+        if (bl >= b0 + 2) r2 = draw(c.seed, ig, (uint64_t)(b0 + 2), 2u);
         rnd = bl == b0 ? r0 : bl == b0 + 1 ? r1 : r2;
         rnd_block = bl;
         const uint32_t wd[12] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y,
@@ -285,7 +296,7 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
             atomicAdd(&v.ctl->pair, ((unsigned long long)tot_cnt << 32) | tot_ch);
         if ((uint32_t)old + (unsigned long long)tot_ch > 0xFFFFFFFFull)
           atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_CHUNKS);
-        atomicAdd(&v.ctl->events, tot_deg);
+        atomicAdd(&v.ctl->pending_events, tot_deg);
         atomicAdd(&v.ctl->spikes, (unsigned long long)tot_cnt);
         s_base[0] = old;
         s_base[1] = v.log_cap
@@ -302,7 +313,7 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
         const unsigned long long idx = (old >> 32) + ex_cnt + k;
         if (idx < v.list_cap) {
           SpikeEntry e;
-          e.src = i;
+          e.src = v.g0 + i;
           e.t = (int32_t)t;
           e.choff = (uint32_t)old + ex_ch + k * nch;
           e.pad = 0;
@@ -313,7 +324,7 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
         if (v.log_cap) {
           const unsigned long long li = logb + ex_cnt + k;
           if (li < v.log_cap) {
-            v.log_src[li] = i;
+            v.log_src[li] = v.g0 + i;
             v.log_t[li] = (int32_t)t;
           } else {
             atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_SPIKE_LOG);
@@ -463,7 +474,7 @@ k_deliver(NetView v, unsigned long long* pair_p, unsigned int* done_p,
     while (c < c_end && j < n_sp) {
       const SpikeEntry e = list[j];
       ++j;
-      if (e.src >= v.n) continue;
+      if (e.src >= v.n_src) continue;
       const uint64_t beg = v.row_ptr[e.src], end = v.row_ptr[e.src + 1];
       const uint64_t last = (uint64_t)e.choff + row_chunks(beg, end, CH);
       const uint64_t stop = last < c_end ? last : c_end;
@@ -511,7 +522,11 @@ k_deliver(NetView v, unsigned long long* pair_p, unsigned int* done_p,
     if (prev == gridDim.x - 1) {
       *pair_p = 0ull;
       *done_p = 0u;
-      if (advance_time) v.ctl->t_now += v.ctl->iv_steps;
+      if (advance_time) {  // the interval's own list: commit its events
+        v.ctl->t_now += v.ctl->iv_steps;
+        v.ctl->events += v.ctl->pending_events;
+        v.ctl->pending_events = 0ull;
+      }
     }
   }
 }
@@ -859,7 +874,7 @@ __device__ __forceinline__ void deliver_tile_body(
     for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) {
       const SpikeEntry e = list[j0 + k];
       SegDesc sd{0, 0u, e.t};
-      if (e.src < v.n) {
+      if (e.src < v.n_src) {
         const uint32_t* to = v.tile_off + (uint64_t)e.src * row_stride + tile;
         const uint32_t a = to[0], b = to[1];
         sd.beg = v.row_ptr[e.src] + a;
@@ -941,7 +956,11 @@ __device__ __forceinline__ void deliver_tile_body(
     if (prev == v.n_tiles - 1) {
       *pair_p = 0ull;
       *done_p = 0u;
-      if (advance_time) v.ctl->t_now += v.ctl->iv_steps;
+      if (advance_time) {  // the interval's own list: commit its events
+        v.ctl->t_now += v.ctl->iv_steps;
+        v.ctl->events += v.ctl->pending_events;
+        v.ctl->pending_events = 0ull;
+      }
     }
   }
 }
@@ -998,7 +1017,7 @@ k_prepare_external(NetView v, const uint32_t* __restrict__ src,
       t = tt[i];
       tmin = min(tmin, t);
       tmax = max(tmax, t);
-      if (s < v.n) {
+      if (s < v.n_src) {
         uint64_t b = v.row_ptr[s], e = v.row_ptr[s + 1];
         nch = row_chunks(b, e, v.chunk);
         deg_sum += e - b;
@@ -1167,6 +1186,14 @@ cudaError_t launch_fill_i32(int32_t* p, int32_t value, uint64_t n,
   if (n == 0) return cudaSuccess;
   const uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 4096);
   k_fill_i32<<<(unsigned)blocks, 256, 0, s>>>(p, value, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_list_to_arrays(const SpikeEntry* list, uint64_t n,
+                                  uint32_t* src, int32_t* t, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 4096);
+  k_list_to_arrays<<<(unsigned)blocks, 256, 0, s>>>(list, n, src, t);
   return cudaGetLastError();
 }
 

@@ -32,6 +32,7 @@ struct snn_net {
   bool own_stream = false;
   int device = 0;
   uint32_t n = 0, pitch = 0;
+  uint32_t n_src = 0, g0 = 0;  // store rows (all sources); first neuron
   int fmt = 0, n_slots = 0;
   UpdConst uc{};
   float *V = nullptr, *I = nullptr, *J = nullptr;
@@ -79,6 +80,8 @@ struct snn_net {
   NetView view() const {
     NetView v;
     v.n = n;
+    v.n_src = n_src;
+    v.g0 = g0;
     v.pitch = pitch;
     v.slot_mask = (uint32_t)n_slots - 1u;
     v.chunk = (uint32_t)chunk_records(fmt);

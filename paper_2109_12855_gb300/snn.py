@@ -39,6 +39,8 @@ EXPORTS = [
     "snn_server_poll", "snn_server_spikes", "snn_server_release",
     "snn_server_get_stats", "snn_server_destroy", "snn_set_stdp",
     "snn_read_weights", "snn_read_spike_stats", "snn_clear_spike_stats",
+    "snn_read_pending", "snn_get_bounds", "snn_set_bounds",
+    "snn_deliver_gathered",
 ]
 SNN_REQ_QUEUED, SNN_REQ_BUILDING, SNN_REQ_RUNNING, SNN_REQ_DONE = 0, 1, 2, 3
 SNN_REQ_FAILED = -1
@@ -60,7 +62,8 @@ class snn_params(C.Structure):
                 ("n_slots", C.c_int32), ("interval", C.c_int32),
                 ("init_v_random", C.c_int32), ("count_events", C.c_int32),
                 ("deliver_mode", C.c_int32), ("spike_log_capacity", C.c_uint64),
-                ("tile_width", C.c_int32), ("reserved_", C.c_int32)]
+                ("tile_width", C.c_int32), ("reserved_", C.c_int32),
+                ("part_lo", C.c_uint32), ("part_hi", C.c_uint32)]
 
 
 class snn_conn_params(C.Structure):
@@ -83,7 +86,13 @@ class snn_stats(C.Structure):
                 ("store_bytes", C.c_uint64), ("n_tiles", C.c_uint32),
                 ("tile_width", C.c_uint32), ("window", C.c_int32),
                 ("deliver_mode", C.c_int32), ("plastic_events", C.c_uint64),
-                ("stdp_truncated", C.c_uint64)]
+                ("stdp_truncated", C.c_uint64), ("first_neuron", C.c_uint32),
+                ("n_sources", C.c_uint32)]
+
+
+class snn_bounds(C.Structure):
+    _fields_ = [("mult_max", C.c_uint32), ("k_in_max", C.c_uint32),
+                ("max_abs_w", C.c_float), ("reserved_", C.c_uint32)]
 
 
 class snn_stdp_params(C.Structure):
@@ -176,6 +185,12 @@ def lib():
             "snn_read_weights": ([_P, _P, C.c_int32], C.c_int),
             "snn_read_spike_stats": ([_P, _P, _P, _P, _P], C.c_int),
             "snn_clear_spike_stats": ([_P], C.c_int),
+            "snn_read_pending": ([_P, _P, _P, C.c_uint64,
+                                  C.POINTER(C.c_uint64), C.c_int32], C.c_int),
+            "snn_get_bounds": ([_P, C.POINTER(snn_bounds)], C.c_int),
+            "snn_deliver_gathered": ([_P, _P, _P, C.c_uint32, C.c_int32,
+                                      C.POINTER(C.c_uint64)], C.c_int),
+            "snn_set_bounds": ([_P, C.POINTER(snn_bounds)], C.c_int),
             "snn_server_create": ([C.c_uint64, C.c_int32, _P, C.POINTER(_P)],
                                   C.c_int),
             "snn_server_submit": ([_P, C.POINTER(snn_request),
@@ -380,6 +395,39 @@ def snn_clear_spike_stats(net):
     _check(lib().snn_clear_spike_stats(net))
 
 
+def snn_read_pending(net, src, t) -> int:
+    """Pending interval list into src / t (numpy or device tensors); returns
+    the number of spikes."""
+    mem = _mem_of(src, t)
+    n = C.c_uint64()
+    cap = len(src) if hasattr(src, "__len__") else src.numel()
+    _check(lib().snn_read_pending(net, _buf(src)[0], _buf(t)[0], cap,
+                                  C.byref(n), mem))
+    return n.value
+
+
+def snn_deliver_gathered(net, src, t) -> int:
+    """Deliver the gathered interval list (numpy uint32/int32 or device
+    int32 tensors); returns the events this partition received."""
+    mem = _mem_of(src, t)
+    ev = C.c_uint64()
+    n = len(src)
+    _check(lib().snn_deliver_gathered(net, _buf(src)[0] if n else None,
+                                      _buf(t)[0] if n else None, n, mem,
+                                      C.byref(ev)))
+    return ev.value
+
+
+def snn_get_bounds(net) -> snn_bounds:
+    b = snn_bounds()
+    _check(lib().snn_get_bounds(net, C.byref(b)))
+    return b
+
+
+def snn_set_bounds(net, b: snn_bounds):
+    _check(lib().snn_set_bounds(net, C.byref(b)))
+
+
 def snn_state_size(net) -> int:
     n = C.c_uint64()
     _check(lib().snn_state_size(net, C.byref(n)))
@@ -455,7 +503,9 @@ class Net:
 
     def __init__(self, p: snn_params, stream: int | None = None):
         self.p = p
-        self.n = p.n_exc + p.n_inh
+        part = p.part_hi != 0 or p.part_lo != 0
+        self.n_src = p.n_exc + p.n_inh          # store rows: every source
+        self.n = p.part_hi - p.part_lo if part else self.n_src  # local
         self.h = snn_create(p, stream)
 
     def close(self):
@@ -518,7 +568,7 @@ class Net:
     def read_store(self):
         st = self.stats()
         m = st.n_synapses
-        rp = np.zeros(self.n + 1, np.uint64)
+        rp = np.zeros(self.n_src + 1, np.uint64)
         tg = np.zeros(max(m, 1), np.uint32)
         dl = np.zeros(max(m, 1), np.uint8)
         w = np.zeros(max(m, 1), np.float32)

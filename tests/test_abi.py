@@ -51,10 +51,10 @@ def test_struct_layouts_match_header(libpath):
     """sizeof of the C structs as compiled (g++) equals the ctypes mirrors."""
     import ctypes
     from paper_2109_12855_gb300 import snn
-    src = ('#include "snn.h"\n#include <stdio.h>\nint main(){printf("%zu %zu %zu %zu %zu %zu %zu",'
+    src = ('#include "snn.h"\n#include <stdio.h>\nint main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu",'
            'sizeof(snn_params),sizeof(snn_conn_params),sizeof(snn_stats),'
            'sizeof(snn_request),sizeof(snn_result),sizeof(snn_server_stats),'
-           'sizeof(snn_stdp_params));}')
+           'sizeof(snn_stdp_params),sizeof(snn_bounds));}')
     exe = os.path.join(ROOT, "paper_2109_12855_gb300", "_build", "sizes")
     os.makedirs(os.path.dirname(exe), exist_ok=True)
     r = subprocess.run(["gcc", "-x", "c", "-I", os.path.join(ROOT, "include"),
@@ -69,7 +69,8 @@ def test_struct_layouts_match_header(libpath):
                      ctypes.sizeof(snn.snn_request),
                      ctypes.sizeof(snn.snn_result),
                      ctypes.sizeof(snn.snn_server_stats),
-                     ctypes.sizeof(snn.snn_stdp_params)]
+                     ctypes.sizeof(snn.snn_stdp_params),
+                     ctypes.sizeof(snn.snn_bounds)]
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
