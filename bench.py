@@ -792,6 +792,113 @@ def ctypes_size(t):
     return ctypes.sizeof(t)
 
 
+# ---------------------------------------------------------------------------
+# target-partitioned network over the ranks (one partition per GPU)
+# ---------------------------------------------------------------------------
+def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
+    """Rank r simulates neurons split(N, world)[r] of ONE network with the
+    synapses of all sources onto them; every interval the ranks all-gather
+    their spike lists (NCCL, device tensors) and deliver the union.  The
+    union of the partitions equals the whole net bit for bit.  Strong
+    scaling: the total work is fixed as the number of GPUs grows."""
+    import torch
+    from paper_2109_12855_gb300 import partition as PT
+    from paper_2109_12855_gb300 import snn
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    s = torch.cuda.Stream()
+    torch.cuda.set_stream(s)
+    lo, hi = PT.split(wl.n, ws)[rank]
+    p = snn.params(n_exc=wl.n_e, n_inh=wl.n_i, weight_format=fmt, seed=1,
+                   nu_ext=nu_ext)
+    w_e = snn.snn_psc_weight_for_psp(p, wl.psp_mv)
+    p.w_ext = w_e
+    c = snn.conn_params(k_exc=wl.k_e, k_inh=wl.k_i, w_exc=w_e,
+                        w_inh=-wl.g * w_e, sd_exc=wl.sd_rel * w_e,
+                        sd_inh=wl.sd_rel * wl.g * w_e, d_lo=wl.d_lo,
+                        d_hi=wl.d_hi, seed=1001, clip_exc=1, clip_inh=0)
+    t_build = time.perf_counter()
+    net = PT.create(p, c, lo, hi, s.cuda_stream)
+
+    def reduce_max(v):
+        import torch.distributed as dist
+        x = torch.tensor([float(a) for a in v], dtype=torch.float64,
+                         device="cuda")
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        return [x[0].item(), x[1].item(), x[2].item()]
+
+    PT.agree_bounds([net], reduce_max if ws > 1 else None)
+    net.finalize()
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t_build
+    D = net.stats().interval
+    d_src = torch.empty(max(net.n * D, 1), dtype=torch.int32, device="cuda")
+    d_t = torch.empty_like(d_src)
+    steps_per = int(round(bio_ms / 0.1))
+
+    def step(t0):
+        t = t0
+        while t < t0 + steps_per:
+            m = min(D, t0 + steps_per - t)
+            snn.snn_update(net.h, t, m)
+            k = snn.snn_read_pending(net.h, d_src, d_t)
+            a_s, a_t = d_src[:k], d_t[:k]
+            if ws > 1:
+                a_s, a_t = PT.allgather_spikes(a_s, a_t)
+            snn.snn_deliver_gathered(net.h, a_s, a_t, want_events=False)
+            t += m
+        return t
+
+    t = 0
+    for _ in range(args.warmup):
+        t = step(t)
+    torch.cuda.synchronize()
+    a = net.stats()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        t = step(t)
+    e1.record(s)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    b = net.stats()
+    events = b.events_delivered - a.events_delivered
+    spikes = b.spikes - a.spikes
+    launches = b.kernel_launches - a.kernel_launches
+    ms_max, ev_all, sp_all = reduce_over_ranks(ms, events, spikes)
+    net.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": ev_all / (ms_max * 1e-3), "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None,
+        "dtype": "f32" if fmt == 0 else "bf16-store/f32-accumulate",
+        "data": "synthetic", "real_time_factor": (ms_max / args.steps) / bio_ms,
+        "config": {"workload": args.workload, "neurons": wl.n,
+                   "synapses": wl.n_synapses, "bio_ms_per_step": bio_ms,
+                   "mean_rate_hz": sp_all / wl.n / (args.steps * bio_ms * 1e-3),
+                   "build_s": t_build,
+                   "parallelism": f"target partition x{ws}: each GPU holds "
+                                  "1/N of the neurons and the synapses onto "
+                                  "them; spike lists all-gathered every "
+                                  "interval"},
+        "roofline": None, "cpu_baseline": None, "e2e": None,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -800,6 +907,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) +
                     sorted(SERVE_WORKLOADS), default=DEFAULT)
+    ap.add_argument("--partition", action="store_true",
+                    help="split one network over the ranks (target "
+                         "partition, spike all-gather every interval) "
+                         "instead of running independent replicas")
     ap.add_argument("--requests", type=int, default=40,
                     help="serving workloads: requests in the stream")
     ap.add_argument("--nu-ext", type=float, default=None)
@@ -827,6 +938,11 @@ def main():
             run_serve(args, SERVE_WORKLOADS[args.workload], nu_ext)
         return
     wl, fmt, bio_ms, kind = WORKLOADS[args.workload]
+    if args.partition and args.impl != "reference":
+        from paper_2109_12855_gb300 import build
+        build()
+        run_partitioned(args, wl, fmt, bio_ms, nu_ext)
+        return
     if args.impl == "reference":
         run_reference(args, wl, nu_ext)
     else:

@@ -406,15 +406,16 @@ def snn_read_pending(net, src, t) -> int:
     return n.value
 
 
-def snn_deliver_gathered(net, src, t) -> int:
+def snn_deliver_gathered(net, src, t, want_events: bool = True) -> int:
     """Deliver the gathered interval list (numpy uint32/int32 or device
-    int32 tensors); returns the events this partition received."""
+    int32 tensors); returns the events this partition received (0 when
+    want_events is false, which saves two synchronisations)."""
     mem = _mem_of(src, t)
     ev = C.c_uint64()
     n = len(src)
     _check(lib().snn_deliver_gathered(net, _buf(src)[0] if n else None,
                                       _buf(t)[0] if n else None, n, mem,
-                                      C.byref(ev)))
+                                      C.byref(ev) if want_events else None))
     return ev.value
 
 
