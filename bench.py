@@ -597,6 +597,7 @@ def serve_batched(snn, reqs, arrivals, budget, stream, clocks=None):
             clocks.start()
         t0 = time.perf_counter()
         nxt, n = 0, len(reqs)
+        last_steps = -1
         while True:
             now = time.perf_counter() - t0
             while nxt < n and arrivals[nxt] <= now:
@@ -609,6 +610,9 @@ def serve_batched(snn, reqs, arrivals, budget, stream, clocks=None):
                 break
             if active == 0:
                 time.sleep(1e-4)          # nothing on the GPU yet
+            elif st.steps == last_steps:
+                time.sleep(2e-5)          # every lane busy: let the GPU run
+            last_steps = st.steps
         wall = time.perf_counter() - t0
         clk = clocks.stop() if clocks else None
         res = [snn.snn_server_poll(sv, i) for i in ids]
@@ -617,8 +621,12 @@ def serve_batched(snn, reqs, arrivals, budget, stream, clocks=None):
                 [(r.id, r.error) for r in res if r.state != snn.SNN_REQ_DONE]))
         lat = [r.t_done - r.t_submit + g for r, g in zip(res, lag)]
         spikes_read = sum(r.spikes for r in res)
+        parts = {"queue_p50_ms": 1e3 * float(np.median([r.t_admit - r.t_submit for r in res])),
+                 "build_p50_ms": 1e3 * float(np.median([r.t_start - r.t_admit for r in res])),
+                 "run_p50_ms": 1e3 * float(np.median([r.t_done - r.t_start for r in res]))}
         return {"wall_s": wall, "events": sum(r.events for r in res),
                 "spikes": spikes_read, "latency": _lat_stats(lat),
+                "latency_parts": parts,
                 "server_steps": st.steps, "intervals": st.intervals,
                 "kernel_launches": st.kernel_launches, "gpu_ms": st.gpu_ms,
                 "intervals_per_step": st.intervals_per_step,

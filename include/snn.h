@@ -124,7 +124,10 @@ typedef struct snn_params {
   int32_t tile_width;     /* targets per tile of the tiled delivery; 0 = the
                              automatic choice (about N / #SMs), otherwise used
                              as given when its shared-memory window fits */
-  int32_t reserved_;
+  int32_t stream_priority; /* priority of the stream the library creates for
+                             the net when none is given (0: default; see
+                             cudaDeviceGetStreamPriorityRange: larger is
+                             lower priority) */
   uint32_t part_lo, part_hi; /* target partition: this net holds neurons
                              [part_lo, part_hi) of the population of n_exc +
                              n_inh neurons and the synapses of all sources

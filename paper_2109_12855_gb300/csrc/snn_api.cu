@@ -575,7 +575,8 @@ int snn_create(const snn_params* p, void* stream, snn_net** out) {
   } else {
     // a blocking stream stays ordered with the legacy default stream and,
     // unlike it, can be captured into graphs
-    if (cudaStreamCreate(&net->stream) != cudaSuccess)
+    if (cudaStreamCreateWithPriority(&net->stream, cudaStreamDefault,
+                                     p->stream_priority) != cudaSuccess)
       return bail(fail(SNN_E_CUDA, "stream creation failed"));
     net->own_stream = true;
   }

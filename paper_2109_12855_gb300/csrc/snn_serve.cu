@@ -4,13 +4,16 @@
 // Requests queue in arrival order.  A builder thread admits the head request
 // when its estimated device footprint fits the budget and builds its net
 // (store construction on the net's own stream) while the admitted nets keep
-// running on the server's stream.  A step advances every running net by its
-// next interval with one batched update launch and one batched tiled-delivery
-// launch for all nets (k_update_batch / k_deliver_tiled_batch): a device table
-// holds each net's view, update constants and step count, and a block map
-// sends every CTA to its (net, block) or (net, tile).  While the batch is
-// unchanged a step may run several intervals, captured as one CUDA graph; a
-// small autotuner picks that number from measured GPU time per interval.
+// running.  Running nets are grouped into lanes by size (synapse count); a
+// lane is a batch with its own stream: a step advances every net of a lane
+// by its next interval with one batched update launch and one batched
+// tiled-delivery launch for all of them (k_update_batch /
+// k_deliver_tiled_batch: a device table holds each net's view, update
+// constants and step count, and a block map sends every CTA to its (net,
+// block) or (net, tile)).  Lanes run concurrently, so a small net does not
+// advance at the pace of the largest one.  While a lane's batch is unchanged
+// a step may run several intervals captured as one CUDA graph; a small
+// autotuner per lane picks that number from measured GPU time per interval.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -56,13 +59,20 @@ int sfail(int code, const char* fmt, ...) {
     if (!(cond)) return sfail(code, __VA_ARGS__); \
   } while (0)
 
-constexpr int kTuneCandidates[] = {1, 2, 4, 8};
+constexpr int kTuneCandidates[] = {1, 2, 4, 8, 16};  // 2^0 .. 2^kMaxGraphLog
 constexpr int kTuneStepsPerCandidate = 4;
 constexpr uint64_t kLogCapMax = 1ull << 22;  // recorded spikes per request
 // Served nets share each delivery launch, so a net gets tiles in proportion
 // to its synapses (one per kSynPerTile, at most one per SM) rather than one
 // per SM: small nets then add few CTAs of fixed per-CTA cost to the batch.
 constexpr uint64_t kSynPerTile = 1ull << 22;
+// At most this many tiles per served net, so that other lanes keep SMs.
+constexpr uint64_t kServeMaxTiles = 120;
+// Graphs cached per lane for steps of 2^1 .. 2^kMaxGraphLog intervals.
+constexpr int kMaxGraphLog = 4;
+// Lanes by synapse count: below 2^24, below 2^27, and the rest.
+constexpr int kLanes = 3;
+constexpr uint64_t kLaneBound[kLanes - 1] = {1ull << 24, 1ull << 27};
 
 double now_s() {
   using namespace std::chrono;
@@ -82,25 +92,10 @@ struct Req {
 
 }  // namespace
 
-struct snn_server {
-  uint64_t budget = 0, used = 0;
-  int fmt = 0;
-  int device = 0;
+// One lane: a batch of running nets advanced together on its own stream.
+struct Lane {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  double t0 = 0;
-
-  std::mutex mu;                       // guards everything below it
-  std::condition_variable cv;          // builder wake-ups
-  std::deque<uint64_t> queue;          // ids waiting for admission
-  std::map<uint64_t, Req> reqs;
-  std::vector<Req*> ready;             // built, not yet in the batch
-  uint64_t next_id = 1;
-  bool stop = false;
-  uint64_t submitted = 0, done = 0, failed = 0, events = 0, spikes = 0;
-
-  // used by the stepping thread only (map nodes are stable: a request is
-  // erased only after it finished)
   std::vector<Req*> active;
   std::vector<int> active_steps;       // n_steps per net in the tables
   BatchNet* d_nets = nullptr;
@@ -110,8 +105,8 @@ struct snn_server {
   uint32_t n_ublocks = 0, n_dctas = 0;
   size_t dsmem = 0;
   bool dirty = true;
-  cudaGraphExec_t graph = nullptr;
-  int graph_m = 0;
+  // captured steps of 2, 4, 8 and 16 intervals for the current tables
+  cudaGraphExec_t graph[kMaxGraphLog + 1] = {};
   // GPU time per step: two event pairs used in turn, so that the host
   // prepares step k+1 while step k runs and reads step k's time afterwards
   cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -127,8 +122,32 @@ struct snn_server {
   double tune_ms = 0;
   double tune_best = 1e300;
   int tune_best_m = 1;
+  double t_last = 0;      // wall time of the lane's previous step (0: idle)
+  int m_last = 0;         // intervals of that step
+};
 
-  std::thread builder;
+struct snn_server {
+  uint64_t budget = 0, used = 0;
+  int fmt = 0;
+  int device = 0;
+  double t0 = 0;
+
+  std::mutex mu;                       // guards everything below it
+  std::condition_variable cv;          // builder wake-ups
+  std::deque<uint64_t> queue[2];       // ids waiting for admission, by
+                                       // size class (small, large)
+  std::map<uint64_t, Req> reqs;
+  std::vector<Req*> ready;             // built, not yet in a lane
+  uint64_t next_id = 1;
+  bool stop = false;
+  uint64_t submitted = 0, done = 0, failed = 0, events = 0, spikes = 0;
+
+  // used by the stepping thread only (map nodes are stable: a request is
+  // erased only after it finished)
+  Lane lanes[kLanes];
+  uint64_t steps = 0;
+
+  std::thread builder[2];
 };
 
 namespace {
@@ -143,7 +162,8 @@ int32_t serve_tile_width(const snn_request& r) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   uint64_t tiles = (n_syn + kSynPerTile - 1) / kSynPerTile;
-  tiles = std::min<uint64_t>(std::max<uint64_t>(tiles, 1), (uint64_t)std::max(sms, 1));
+  tiles = std::min<uint64_t>(std::max<uint64_t>(tiles, 1),
+                             std::min<uint64_t>(kServeMaxTiles, std::max(sms, 1)));
   return (int32_t)std::min<uint64_t>((n + tiles - 1) / tiles, 1u << 30);
 }
 
@@ -168,24 +188,33 @@ uint64_t estimate_bytes(const snn_request& r, int fmt) {
   return store + index + state + (8ull << 20);
 }
 
-void builder_main(snn_server* sv) {
+// Builder thread for one size class (0: small requests, 1: large): admits
+// the oldest queued request of its class when its footprint fits the budget
+// and builds it on the net's own stream, at the lowest stream priority so
+// that the running nets' kernels are served first.  Small requests thus never
+// wait behind the build of a large one.
+void builder_main(snn_server* sv, int cls) {
   cudaSetDevice(sv->device);
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  std::deque<uint64_t>& queue = sv->queue[cls];
   std::unique_lock<std::mutex> lk(sv->mu);
   for (;;) {
     sv->cv.wait(lk, [&] {
       if (sv->stop) return true;
-      if (sv->queue.empty()) return false;
-      const Req& h = sv->reqs[sv->queue.front()];
+      if (queue.empty()) return false;
+      const Req& h = sv->reqs[queue.front()];
       return sv->used + h.est <= sv->budget;
     });
     if (sv->stop) return;
-    const uint64_t id = sv->queue.front();
-    sv->queue.pop_front();
+    const uint64_t id = queue.front();
+    queue.pop_front();
     Req& q = sv->reqs[id];
     q.res.state = SNN_REQ_BUILDING;
     q.res.t_admit = now_s() - sv->t0;
     sv->used += q.est;
-    const snn_request r = q.r;
+    snn_request r = q.r;
+    r.params.stream_priority = prio_least;
     lk.unlock();
     // build outside the lock, on the net's own stream
     snn_net* net = nullptr;
@@ -226,19 +255,25 @@ int ensure_dev(T** p, size_t* cap, size_t n, cudaStream_t s) {
   return SNN_OK;
 }
 
-// Rebuild the batch table and block maps for the active nets.
-int rebuild_tables(snn_server* sv) {
+int lane_of(const snn_net* net) {
+  int k = 0;
+  while (k < kLanes - 1 && net->n_syn >= kLaneBound[k]) ++k;
+  return k;
+}
+
+// Rebuild a lane's batch table and block maps for its active nets.
+int rebuild_tables(Lane* ln) {
   // earlier steps may still read the tables: finish them first
-  SCK(cudaStreamSynchronize(sv->stream));
-  std::vector<BatchNet> nets(sv->active.size());
+  SCK(cudaStreamSynchronize(ln->stream));
+  std::vector<BatchNet> nets(ln->active.size());
   std::vector<uint2> umap, dmap;
   size_t smem = 0;
   const uint32_t ut = update_threads();
-  for (size_t k = 0; k < sv->active.size(); ++k) {
-    snn_net* net = sv->active[k]->net;
+  for (size_t k = 0; k < ln->active.size(); ++k) {
+    snn_net* net = ln->active[k]->net;
     nets[k].v = net->view();
     nets[k].c = net->uc;
-    nets[k].n_steps = sv->active_steps[k];
+    nets[k].n_steps = ln->active_steps[k];
     nets[k].pad_ = 0;
     const uint32_t nb = (net->n + ut - 1) / ut;
     for (uint32_t b = 0; b < nb; ++b) umap.push_back(make_uint2((uint32_t)k, b));
@@ -247,96 +282,108 @@ int rebuild_tables(snn_server* sv) {
     smem = std::max(smem, tiled_smem_bytes(nets[k].v));
   }
   int rc;
-  if ((rc = ensure_dev(&sv->d_nets, &sv->cap_nets, nets.size(), sv->stream)) != SNN_OK) return rc;
-  if ((rc = ensure_dev(&sv->d_umap, &sv->cap_umap, umap.size(), sv->stream)) != SNN_OK) return rc;
-  if ((rc = ensure_dev(&sv->d_dmap, &sv->cap_dmap, dmap.size(), sv->stream)) != SNN_OK) return rc;
-  SCK(cudaMemcpyAsync(sv->d_nets, nets.data(), nets.size() * sizeof(BatchNet),
-                      cudaMemcpyHostToDevice, sv->stream));
-  SCK(cudaMemcpyAsync(sv->d_umap, umap.data(), umap.size() * sizeof(uint2),
-                      cudaMemcpyHostToDevice, sv->stream));
-  SCK(cudaMemcpyAsync(sv->d_dmap, dmap.data(), dmap.size() * sizeof(uint2),
-                      cudaMemcpyHostToDevice, sv->stream));
-  SCK(cudaStreamSynchronize(sv->stream));  // host vectors go out of scope
-  sv->n_ublocks = (uint32_t)umap.size();
-  sv->n_dctas = (uint32_t)dmap.size();
-  sv->dsmem = smem;
-  if (sv->graph) {
-    cudaGraphExecDestroy(sv->graph);
-    sv->graph = nullptr;
-  }
-  sv->dirty = false;
+  if ((rc = ensure_dev(&ln->d_nets, &ln->cap_nets, nets.size(), ln->stream)) != SNN_OK)
+    return rc;
+  if ((rc = ensure_dev(&ln->d_umap, &ln->cap_umap, umap.size(), ln->stream)) != SNN_OK)
+    return rc;
+  if ((rc = ensure_dev(&ln->d_dmap, &ln->cap_dmap, dmap.size(), ln->stream)) != SNN_OK)
+    return rc;
+  SCK(cudaMemcpyAsync(ln->d_nets, nets.data(), nets.size() * sizeof(BatchNet),
+                      cudaMemcpyHostToDevice, ln->stream));
+  SCK(cudaMemcpyAsync(ln->d_umap, umap.data(), umap.size() * sizeof(uint2),
+                      cudaMemcpyHostToDevice, ln->stream));
+  SCK(cudaMemcpyAsync(ln->d_dmap, dmap.data(), dmap.size() * sizeof(uint2),
+                      cudaMemcpyHostToDevice, ln->stream));
+  SCK(cudaStreamSynchronize(ln->stream));  // host vectors go out of scope
+  ln->n_ublocks = (uint32_t)umap.size();
+  ln->n_dctas = (uint32_t)dmap.size();
+  ln->dsmem = smem;
+  for (cudaGraphExec_t& g : ln->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  ln->dirty = false;
   return SNN_OK;
 }
 
-int launch_intervals(snn_server* sv, int m) {
+int launch_intervals(Lane* ln, int fmt, int m) {
   for (int i = 0; i < m; ++i) {
-    SCK(launch_update_batch(sv->d_nets, sv->d_umap, sv->n_ublocks, sv->stream));
-    SCK(launch_deliver_tiled_batch(sv->fmt, sv->d_nets, sv->d_dmap, sv->n_dctas,
-                                   sv->dsmem, sv->stream));
+    SCK(launch_update_batch(ln->d_nets, ln->d_umap, ln->n_ublocks, ln->stream));
+    SCK(launch_deliver_tiled_batch(fmt, ln->d_nets, ln->d_dmap, ln->n_dctas,
+                                   ln->dsmem, ln->stream));
   }
   return SNN_OK;
 }
 
-int capture(snn_server* sv, int m) {
-  if (sv->graph) {
-    cudaGraphExecDestroy(sv->graph);
-    sv->graph = nullptr;
+int log2_of(int m) {
+  int l = 0;
+  while ((1 << (l + 1)) <= m) ++l;
+  return l;
+}
+
+// The lane's graph of m intervals (m a power of two, 2 .. 2^kMaxGraphLog),
+// captured on first use for the current tables.
+int graph_for(Lane* ln, int fmt, int m, cudaGraphExec_t* out) {
+  const int l = log2_of(m);
+  if (!ln->graph[l]) {
+    cudaGraph_t g;
+    SCK(cudaStreamBeginCapture(ln->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_intervals(ln, fmt, m);
+    cudaError_t e = cudaStreamEndCapture(ln->stream, &g);
+    if (rc != SNN_OK) return rc;
+    SCK(e);
+    e = cudaGraphInstantiate(&ln->graph[l], g, 0);
+    cudaGraphDestroy(g);
+    SCK(e);
   }
-  cudaGraph_t g;
-  SCK(cudaStreamBeginCapture(sv->stream, cudaStreamCaptureModeThreadLocal));
-  int rc = launch_intervals(sv, m);
-  cudaError_t e = cudaStreamEndCapture(sv->stream, &g);
-  if (rc != SNN_OK) return rc;
-  SCK(e);
-  e = cudaGraphInstantiate(&sv->graph, g, 0);
-  cudaGraphDestroy(g);
-  SCK(e);
-  sv->graph_m = m;
+  *out = ln->graph[l];
   return SNN_OK;
 }
 
-// Feed the autotuner with the GPU time of the last step (per interval).
-void tune_observe(snn_server* sv, double ms, int m) {
-  if (sv->tuned || m != kTuneCandidates[sv->tune_idx]) return;
-  sv->tune_ms += ms / m;
-  if (++sv->tune_count < kTuneStepsPerCandidate) return;
-  const double avg = sv->tune_ms / sv->tune_count;
-  if (avg < sv->tune_best) {
-    sv->tune_best = avg;
-    sv->tune_best_m = m;
+// Feed a lane's autotuner with the wall time of one of its steps (from its
+// start to the start of the next: what the stepping loop, host overheads
+// included, spends per interval).
+void tune_observe(Lane* ln, double ms, int m) {
+  if (ln->tuned || m != kTuneCandidates[ln->tune_idx]) return;
+  ln->tune_ms += ms / m;
+  if (++ln->tune_count < kTuneStepsPerCandidate) return;
+  const double avg = ln->tune_ms / ln->tune_count;
+  if (avg < ln->tune_best) {
+    ln->tune_best = avg;
+    ln->tune_best_m = m;
   }
-  sv->tune_ms = 0;
-  sv->tune_count = 0;
-  if (++sv->tune_idx == (int)(sizeof(kTuneCandidates) / sizeof(int))) {
-    sv->tuned = 1;
-    sv->ips = sv->tune_best_m;
+  ln->tune_ms = 0;
+  ln->tune_count = 0;
+  if (++ln->tune_idx == (int)(sizeof(kTuneCandidates) / sizeof(int))) {
+    ln->tuned = 1;
+    ln->ips = ln->tune_best_m;
   } else {
-    sv->ips = kTuneCandidates[sv->tune_idx];
+    ln->ips = kTuneCandidates[ln->tune_idx];
   }
 }
 
 // Add the GPU time of the step recorded in event pair `slot` if it has
 // finished (or wait for it when `wait`).
-int fold_step_time(snn_server* sv, int slot, bool wait) {
-  if (!sv->ev_pending[slot]) return SNN_OK;
+int fold_step_time(Lane* ln, int slot, bool wait) {
+  if (!ln->ev_pending[slot]) return SNN_OK;
   if (wait) {
-    SCK(cudaEventSynchronize(sv->ev[slot][1]));
+    SCK(cudaEventSynchronize(ln->ev[slot][1]));
   } else {
-    const cudaError_t q = cudaEventQuery(sv->ev[slot][1]);
+    const cudaError_t q = cudaEventQuery(ln->ev[slot][1]);
     if (q == cudaErrorNotReady) return SNN_OK;
     SCK(q);
   }
   float ms = 0;
-  SCK(cudaEventElapsedTime(&ms, sv->ev[slot][0], sv->ev[slot][1]));
-  sv->gpu_ms += ms;
-  tune_observe(sv, ms, sv->ev_m[slot]);
-  sv->ev_pending[slot] = false;
+  SCK(cudaEventElapsedTime(&ms, ln->ev[slot][0], ln->ev[slot][1]));
+  ln->gpu_ms += ms;
+  ln->ev_pending[slot] = false;
   return SNN_OK;
 }
 
-int retire(snn_server* sv, std::vector<Req*>& finished) {
+int retire(snn_server* sv, Lane* ln, std::vector<Req*>& finished) {
   if (finished.empty()) return SNN_OK;
-  SCK(cudaStreamSynchronize(sv->stream));
+  SCK(cudaStreamSynchronize(ln->stream));
   for (Req* q : finished) {
     snn_net* net = q->net;
     const bool rec = q->r.record_spikes != 0;
@@ -378,6 +425,79 @@ int retire(snn_server* sv, std::vector<Req*>& finished) {
   return SNN_OK;
 }
 
+// One step of one lane: launch its nets' next intervals (several in one
+// graph when the autotuner chose so), then retire the nets that finished.
+int lane_step(snn_server* sv, Lane* ln, bool* launched) {
+  *launched = false;
+  int rc;
+  // fold in the GPU time of finished steps, oldest first; the pair this
+  // step reuses must be finished
+  for (int k = 0; k < 2; ++k) {
+    const int slot = ln->ev_cur ^ k;
+    if ((rc = fold_step_time(ln, slot, k == 0)) != SNN_OK) return rc;
+  }
+  const double now = now_s();
+  if (ln->t_last > 0 && ln->m_last > 0)
+    tune_observe(ln, 1e3 * (now - ln->t_last), ln->m_last);
+  ln->t_last = 0;
+  if (ln->active.empty()) return SNN_OK;
+  // this step's intervals: the largest power of two up to the tuned number
+  // that every net can fill with whole intervals (1 for a net's last,
+  // possibly short, interval)
+  int m = ln->ips;
+  for (size_t k = 0; k < ln->active.size(); ++k) {
+    const Req& q = *ln->active[k];
+    const int iv = q.net->interval;
+    const int next = (int)std::min<int64_t>(iv, q.steps_left);
+    while (m > 1 && q.steps_left < (int64_t)m * iv) m >>= 1;
+    if (ln->active_steps[k] != next) {
+      ln->active_steps[k] = next;
+      ln->dirty = true;
+    }
+  }
+  if (ln->dirty && (rc = rebuild_tables(ln)) != SNN_OK) return rc;
+  cudaGraphExec_t gx = nullptr;
+  if (m > 1 && (rc = graph_for(ln, sv->fmt, m, &gx)) != SNN_OK) return rc;
+  const int slot = ln->ev_cur;
+  SCK(cudaEventRecord(ln->ev[slot][0], ln->stream));
+  if (m > 1) {
+    SCK(cudaGraphLaunch(gx, ln->stream));
+  } else {
+    if ((rc = launch_intervals(ln, sv->fmt, 1)) != SNN_OK) return rc;
+  }
+  SCK(cudaEventRecord(ln->ev[slot][1], ln->stream));
+  ln->ev_pending[slot] = true;
+  ln->ev_m[slot] = m;
+  ln->ev_cur ^= 1;
+  ln->t_last = now;
+  ln->m_last = m;
+  ln->steps += 1;
+  ln->intervals += m;
+  ln->launches += 2ull * m;
+  *launched = true;
+  // bookkeeping; retire nets that finished
+  std::vector<Req*> finished, keep;
+  std::vector<int> keep_steps;
+  for (size_t k = 0; k < ln->active.size(); ++k) {
+    Req& q = *ln->active[k];
+    q.steps_left -= (int64_t)m * ln->active_steps[k];
+    if (q.steps_left <= 0) {
+      finished.push_back(ln->active[k]);
+    } else {
+      keep.push_back(ln->active[k]);
+      keep_steps.push_back(ln->active_steps[k]);
+    }
+  }
+  if (!finished.empty()) {
+    ln->active.swap(keep);
+    ln->active_steps.swap(keep_steps);
+    ln->dirty = true;
+    ln->t_last = 0;  // retiring (a synchronisation) is not a steady step
+    if ((rc = retire(sv, ln, finished)) != SNN_OK) return rc;
+  }
+  return SNN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -397,24 +517,33 @@ int snn_server_create(uint64_t mem_budget, int32_t weight_format, void* stream,
     delete sv;
     return sfail(SNN_E_CUDA, "no CUDA device");
   }
-  if (stream) {
-    sv->stream = static_cast<cudaStream_t>(stream);
-  } else {
-    if (cudaStreamCreate(&sv->stream) != cudaSuccess) {
-      delete sv;
+  // smaller nets get higher stream priority: when SMs free up, the CTA
+  // scheduler serves the short intervals of small nets first and the large
+  // nets take the remaining capacity
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  for (int k = 0; k < kLanes; ++k) {
+    Lane& ln = sv->lanes[k];
+    const int prio = prio_greatest + (prio_least - prio_greatest) * k / (kLanes - 1);
+    if (k == 0 && stream) {
+      ln.stream = static_cast<cudaStream_t>(stream);
+    } else if (cudaStreamCreateWithPriority(&ln.stream, cudaStreamDefault, prio) !=
+               cudaSuccess) {
+      snn_server_destroy(sv);
       return sfail(SNN_E_CUDA, "stream creation failed");
+    } else {
+      ln.own_stream = true;
     }
-    sv->own_stream = true;
+    for (auto& pair : ln.ev)
+      for (cudaEvent_t& e : pair)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+          snn_server_destroy(sv);
+          return sfail(SNN_E_CUDA, "event creation failed");
+        }
+    ln.ips = kTuneCandidates[0];
   }
-  if (cudaEventCreate(&sv->ev[0][0]) != cudaSuccess ||
-      cudaEventCreate(&sv->ev[0][1]) != cudaSuccess ||
-      cudaEventCreate(&sv->ev[1][0]) != cudaSuccess ||
-      cudaEventCreate(&sv->ev[1][1]) != cudaSuccess) {
-    snn_server_destroy(sv);
-    return sfail(SNN_E_CUDA, "event creation failed");
-  }
-  sv->ips = kTuneCandidates[0];
-  sv->builder = std::thread(builder_main, sv);
+  sv->builder[0] = std::thread(builder_main, sv, 0);
+  sv->builder[1] = std::thread(builder_main, sv, 1);
   *out = sv;
   return SNN_OK;
 }
@@ -457,8 +586,10 @@ int snn_server_submit(snn_server* sv, const snn_request* req, uint64_t* id) {
   q.res.t_admit = q.res.t_start = q.res.t_done = -1;
   q.res.bytes = q.est;
   *id = q.id;
+  const uint64_t n_syn = ((uint64_t)req->params.n_exc + req->params.n_inh) *
+                         ((uint64_t)req->conn.k_exc + req->conn.k_inh);
   sv->reqs.emplace(q.id, std::move(q));
-  sv->queue.push_back(*id);
+  sv->queue[n_syn >= kLaneBound[0] ? 1 : 0].push_back(*id);
   sv->submitted += 1;
   sv->cv.notify_all();
   return SNN_OK;
@@ -467,79 +598,30 @@ int snn_server_submit(snn_server* sv, const snn_request* req, uint64_t* id) {
 int snn_server_step(snn_server* sv, int32_t* n_active) {
   SREQ(sv, SNN_E_ARG, "null server");
   SCK(cudaSetDevice(sv->device));
-  // fold in the GPU time of finished steps, oldest first; the pair this
-  // step reuses must be finished
-  int rc;
-  for (int k = 0; k < 2; ++k) {
-    const int slot = sv->ev_cur ^ k;
-    if ((rc = fold_step_time(sv, slot, k == 0)) != SNN_OK) return rc;
-  }
-  // admit nets the builder finished
+  // admit nets the builder finished, each into the lane of its size
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     for (Req* q : sv->ready) {
       q->res.state = SNN_REQ_RUNNING;
       q->res.t_start = now_s() - sv->t0;
-      sv->active.push_back(q);
-      sv->active_steps.push_back(-1);
-      sv->dirty = true;
+      Lane& ln = sv->lanes[lane_of(q->net)];
+      ln.active.push_back(q);
+      ln.active_steps.push_back(-1);
+      ln.dirty = true;
     }
     sv->ready.clear();
   }
-  if (sv->active.empty()) {
-    if (n_active) *n_active = 0;
-    return SNN_OK;
+  bool any = false;
+  int32_t act = 0;
+  for (int k = 0; k < kLanes; ++k) {
+    bool launched = false;
+    int rc = lane_step(sv, &sv->lanes[k], &launched);
+    if (rc != SNN_OK) return rc;
+    any = any || launched;
+    act += (int32_t)sv->lanes[k].active.size();
   }
-  // this step's intervals: m if every net has m full intervals left
-  int m = sv->ips;
-  for (size_t k = 0; k < sv->active.size(); ++k) {
-    const Req& q = *sv->active[k];
-    const int iv = q.net->interval;
-    const int next = (int)std::min<int64_t>(iv, q.steps_left);
-    if (q.steps_left < (int64_t)m * iv) m = 1;
-    if (sv->active_steps[k] != next) {
-      sv->active_steps[k] = next;
-      sv->dirty = true;
-    }
-  }
-  if (sv->dirty && (rc = rebuild_tables(sv)) != SNN_OK) return rc;
-  if (m > 1 && (!sv->graph || sv->graph_m != m) &&
-      (rc = capture(sv, m)) != SNN_OK)
-    return rc;
-  const int slot = sv->ev_cur;
-  SCK(cudaEventRecord(sv->ev[slot][0], sv->stream));
-  if (m > 1) {
-    SCK(cudaGraphLaunch(sv->graph, sv->stream));
-  } else {
-    if ((rc = launch_intervals(sv, 1)) != SNN_OK) return rc;
-  }
-  SCK(cudaEventRecord(sv->ev[slot][1], sv->stream));
-  sv->ev_pending[slot] = true;
-  sv->ev_m[slot] = m;
-  sv->ev_cur ^= 1;
-  sv->steps += 1;
-  sv->intervals += m;
-  sv->launches += 2ull * m;
-  // bookkeeping; retire nets that finished
-  std::vector<Req*> finished, keep;
-  std::vector<int> keep_steps;
-  for (size_t k = 0; k < sv->active.size(); ++k) {
-    Req& q = *sv->active[k];
-    q.steps_left -= (int64_t)m * sv->active_steps[k];
-    if (q.steps_left <= 0) {
-      finished.push_back(sv->active[k]);
-    } else {
-      keep.push_back(sv->active[k]);
-      keep_steps.push_back(sv->active_steps[k]);
-    }
-  }
-  if (!finished.empty()) {
-    sv->active.swap(keep);
-    sv->active_steps.swap(keep_steps);
-    sv->dirty = true;
-    if ((rc = retire(sv, finished)) != SNN_OK) return rc;
-  }
-  if (n_active) *n_active = (int32_t)sv->active.size();
+  if (any) sv->steps += 1;
+  if (n_active) *n_active = act;
   return SNN_OK;
 }
 
@@ -592,18 +674,24 @@ int snn_server_get_stats(snn_server* sv, snn_server_stats* out) {
   out->submitted = sv->submitted;
   out->done = sv->done;
   out->failed = sv->failed;
-  out->active = sv->active.size();
-  out->queued = sv->queue.size();
+  out->queued = sv->queue[0].size() + sv->queue[1].size();
   out->steps = sv->steps;
-  out->intervals = sv->intervals;
-  out->kernel_launches = sv->launches;
+  int tuned = 1, busiest = 0;
+  for (int k = 0; k < kLanes; ++k) {
+    const Lane& ln = sv->lanes[k];
+    out->active += ln.active.size();
+    out->intervals += ln.intervals;
+    out->kernel_launches += ln.launches;
+    out->gpu_ms += ln.gpu_ms;
+    if (ln.steps && !ln.tuned) tuned = 0;
+    if (ln.intervals > sv->lanes[busiest].intervals) busiest = k;
+  }
   out->events = sv->events;
   out->spikes = sv->spikes;
   out->mem_budget = sv->budget;
   out->mem_used = sv->used;
-  out->intervals_per_step = sv->ips;
-  out->tuned = sv->tuned;
-  out->gpu_ms = sv->gpu_ms;
+  out->intervals_per_step = sv->lanes[busiest].ips;
+  out->tuned = tuned && sv->steps > 0;
   return SNN_OK;
 }
 
@@ -614,20 +702,27 @@ int snn_server_destroy(snn_server* sv) {
     sv->stop = true;
   }
   sv->cv.notify_all();
-  if (sv->builder.joinable()) sv->builder.join();
+  for (std::thread& b : sv->builder)
+    if (b.joinable()) b.join();
   cudaSetDevice(sv->device);
-  if (sv->stream) cudaStreamSynchronize(sv->stream);
+  for (Lane& ln : sv->lanes)
+    if (ln.stream) cudaStreamSynchronize(ln.stream);
   for (auto& kv : sv->reqs)
     if (kv.second.net) snn_destroy(kv.second.net);
-  if (sv->graph) cudaGraphExecDestroy(sv->graph);
-  for (auto& pair : sv->ev)
-    for (cudaEvent_t e : pair)
-      if (e) cudaEventDestroy(e);
-  pool_free(sv->d_nets, sv->stream);
-  pool_free(sv->d_umap, sv->stream);
-  pool_free(sv->d_dmap, sv->stream);
-  if (sv->stream) cudaStreamSynchronize(sv->stream);
-  if (sv->own_stream) cudaStreamDestroy(sv->stream);
+  for (Lane& ln : sv->lanes) {
+    for (cudaGraphExec_t g : ln.graph)
+      if (g) cudaGraphExecDestroy(g);
+    for (auto& pair : ln.ev)
+      for (cudaEvent_t e : pair)
+        if (e) cudaEventDestroy(e);
+    if (ln.stream) {
+      pool_free(ln.d_nets, ln.stream);
+      pool_free(ln.d_umap, ln.stream);
+      pool_free(ln.d_dmap, ln.stream);
+      cudaStreamSynchronize(ln.stream);
+      if (ln.own_stream) cudaStreamDestroy(ln.stream);
+    }
+  }
   delete sv;
   return SNN_OK;
 }

@@ -62,7 +62,7 @@ class snn_params(C.Structure):
                 ("n_slots", C.c_int32), ("interval", C.c_int32),
                 ("init_v_random", C.c_int32), ("count_events", C.c_int32),
                 ("deliver_mode", C.c_int32), ("spike_log_capacity", C.c_uint64),
-                ("tile_width", C.c_int32), ("reserved_", C.c_int32),
+                ("tile_width", C.c_int32), ("stream_priority", C.c_int32),
                 ("part_lo", C.c_uint32), ("part_hi", C.c_uint32)]
 
 
