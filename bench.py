@@ -63,6 +63,12 @@ WORKLOADS = {
     "stdp-20000-bf16": (W.Balanced("balanced-20000", 16000, 4000, 9000,
                                    2250, 15, 15, "bf16", 0.0, 150.0),
                         1, 150.0, "simulate"),
+    # profiling case with the per-CTA shape of the 562,500-neuron delivery
+    # (tiles of 1,234 targets, 20-step window, runs of ~25 records; replay
+    # at 46.6 Hz gives its ~4,400 runs per tile) on a 1.4 GB store
+    "deliver-93750-k1900-bf16": (W.Balanced("balanced-93750-k1900", 75000,
+                                            18750, 1520, 380, 10, 20, "bf16",
+                                            0.1, 100.0), 1, 100.0, "deliver"),
     # profiling case: the same segment length and launch size as the
     # 112,500-neuron delivery, with a store of 2.7 GB
     "deliver-20000-fp32": (W.Balanced("balanced-20000", 16000, 4000, 9000,
