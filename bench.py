@@ -95,7 +95,7 @@ def stdp_config(w_e):
 # It stands for the kernel it was measured on: the entry is used only while
 # the kernel sources hash to the recorded prefix.
 TRAFFIC_B_PER_EVENT = {
-    "balanced-112500-fp32": (12.550, "9acc9eb59ec9b11d", "d40e515e507ce391"),
+    "balanced-112500-fp32": (12.550, "00845e2b7663d542", "98fd69d359453942"),
 }
 # serving: a Poisson stream of independent balanced nets (BF16 records,
 # N log-uniform in [1,250, 112,500], 100 ms - 1 s each), mean rate in req/s
