@@ -289,14 +289,18 @@ void snn::tile_geometry(uint32_t n, int window, int32_t hint, uint32_t* tile_w,
 
 namespace {
 
-size_t stdp_bytes_per_target(const snn_net* net) {
-  return net->stdp_on ? (size_t)net->stdp.history * 8 + 4 : 0;
+// shared-memory bytes per target of the plastic delivery beyond the
+// accumulator: spike-time ring, spike count, post trace at each of the
+// window's horizons
+size_t stdp_bytes_per_target(const snn_net* net, int window) {
+  return net->stdp_on ? (size_t)net->stdp.history * 4 + 4 + 4 * (size_t)window : 0;
 }
 
 bool use_tiled(const snn_net* net) {
   return net->p.deliver_mode == SNN_DELIVER_TILED && net->n_syn > 0 &&
          net->tile_off &&
-         (size_t)net->tile_w * ((size_t)net->window * 8 + stdp_bytes_per_target(net)) <=
+         (size_t)net->tile_w *
+                 ((size_t)net->window * 8 + stdp_bytes_per_target(net, net->window)) <=
              kTileSmemBudget;
 }
 
@@ -348,8 +352,8 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
   // tiles sized for the widest window the interval can reach
   const int iv = net->p.interval ? net->p.interval : d_lo;
   choose_tiles(net->n, iv + (d_hi - d_lo), net->p.tile_width,
-               stdp_bytes_per_target(net), &net->tile_w, &net->lo_bits,
-               &net->n_tiles);
+               stdp_bytes_per_target(net, iv + (d_hi - d_lo)), &net->tile_w,
+               &net->lo_bits, &net->n_tiles);
   CK(dalloc(&net->tile_off, (uint64_t)n * (net->n_tiles + 1) * sizeof(uint32_t), net->stream));
   // keys; for 8-byte records the key array becomes the record array
   uint64_t* keys = nullptr;

@@ -654,10 +654,11 @@ __device__ FixScale fix_scale(const NetView& v, uint64_t n_sp,
 // in time order, then the depression by the post trace at t; weights stay in
 // [0, w_max].  tprev / kprev: the previous pre spike and the presynaptic
 // trace right after it.  The post spikes of target j come from the CTA's
-// copy of the last hist spikes (rt, rk: [hist][TW]; n: spikes so far).
+// copy of its last hist spike times (rt: [hist][TW]; n: spikes so far); km
+// is its post trace at t - d (from the CTA's table).
 // Compiled once (not inlined into every unrolled record slot: the code would
 // no longer fit the instruction cache).  .trunc = 1 when the potentiation
-// window or the depression trace reached past the kept spikes.
+// window reached past the kept spikes.
 struct StdpConst {
   float c_pot, c_dep, mu, w_max, l2_plus, l2_minus;
   uint32_t hmask;
@@ -670,37 +671,38 @@ struct StdpOut {
 __device__ __noinline__ StdpOut stdp_weight(float w, int32_t t, uint32_t d,
                                             int32_t tprev, float kprev,
                                             uint32_t j, uint32_t TW,
-                                            const int32_t* rt, const float* rk,
+                                            const int32_t* rt, float km,
                                             uint32_t n, StdpConst c) {
-  const uint32_t H = c.hmask + 1u;
-  const int32_t horizon = t - (int32_t)d;  // post spikes seen by step t
-  const bool has_prev = tprev != kNoSpike;
-  const int32_t after = has_prev ? tprev - (int32_t)d : 0;
-  const int32_t k_min = n > H ? (int32_t)(n - H) : 0;
-  int32_t k_dep = -1, k_lo = -1, k = (int32_t)n - 1;
-  for (; k >= k_min; --k) {
-    const int32_t tp = rt[((uint32_t)k & c.hmask) * TW + j];
-    if (tp > horizon) continue;
-    if (k_dep < 0) k_dep = k;
-    if (!has_prev || tp <= after) break;
-    k_lo = k;
-  }
   StdpOut o;
-  o.trunc = (k < k_min && n > H && (has_prev || k_dep < 0)) ? 1u : 0u;
-  if (k_lo >= 0) {
-    for (int32_t q = k_lo; q <= k_dep; ++q) {
-      const int32_t tp = rt[((uint32_t)q & c.hmask) * TW + j];
-      const float kp = kprev * exp2f(-(float)(tp + (int32_t)d - tprev) * c.l2_plus);
-      const float wm = w > 0.f ? exp2f(c.mu * log2f(w)) : 0.f;
-      w = fminf(w + c.c_pot * wm * kp, c.w_max);
+  o.trunc = 0u;
+  if (tprev != kNoSpike) {
+    // post spikes seen in (previous pre spike, t]: newest first to find
+    // the window, then applied oldest first
+    const uint32_t H = c.hmask + 1u;
+    const int32_t horizon = t - (int32_t)d;
+    const int32_t after = tprev - (int32_t)d;
+    const int32_t k_min = n > H ? (int32_t)(n - H) : 0;
+    int32_t k_hi = -1, k_lo = -1, k = (int32_t)n - 1;
+    for (; k >= k_min; --k) {
+      const int32_t tp = rt[((uint32_t)k & c.hmask) * TW + j];
+      if (tp > horizon) continue;
+      if (tp <= after) break;
+      if (k_hi < 0) k_hi = k;
+      k_lo = k;
+    }
+    o.trunc = (k < k_min && n > H) ? 1u : 0u;
+    if (k_lo >= 0) {
+      for (int32_t q = k_lo; q <= k_hi; ++q) {
+        const int32_t tp = rt[((uint32_t)q & c.hmask) * TW + j];
+        const float kp =
+            kprev * exp2f(-(float)(tp + (int32_t)d - tprev) * c.l2_plus);
+        const float wm = w > 0.f ? exp2f(c.mu * log2f(w)) : 0.f;
+        w = fminf(w + c.c_pot * wm * kp, c.w_max);
+      }
     }
   }
-  if (k_dep >= 0) {
-    const uint32_t e = ((uint32_t)k_dep & c.hmask) * TW + j;
-    const float km = rk[e] * exp2f(-(float)(horizon - rt[e]) * c.l2_minus);
-    w = fmaxf(w - c.c_dep * w * km, 0.f);
-  }
-  o.w = w;
+  // depression by the post trace at t (from the CTA's table)
+  o.w = fmaxf(w - c.c_dep * w * km, 0.f);
   return o;
 }
 
@@ -748,12 +750,15 @@ __device__ __forceinline__ void deliver_tile_body(
   int* accL = acc_mem + cells;                        // fixed: lo parts
   float* accF = reinterpret_cast<float*>(acc_mem);    // FP32 fallback
   for (uint32_t x = threadIdx.x; x < 2 * cells; x += blockDim.x) acc_mem[x] = 0;
-  // plastic nets: the post-spike rings of this tile's targets
+  // plastic nets: the post-spike times of this tile's targets (rings) and
+  // their post traces at the W horizons (t - d) this interval can ask for
   int32_t* s_rt = acc_mem + 2 * cells;                           // [hist][TW]
-  float* s_rk = reinterpret_cast<float*>(s_rt + (PL ? v.sp.hist * TW : 0));
-  uint32_t* s_rn = reinterpret_cast<uint32_t*>(s_rk + (PL ? v.sp.hist * TW : 0));
+  uint32_t* s_rn = reinterpret_cast<uint32_t*>(s_rt + (PL ? v.sp.hist * TW : 0));
+  float* s_km = reinterpret_cast<float*>(s_rn + (PL ? TW : 0));  // [W][TW]
   const bool tile_plastic = PL && tgt_lo < v.sp.n_exc;
   uint32_t my_pl = 0, my_trunc = 0;
+  // first horizon: (interval start) - d_max
+  const long long h_lo = s_base - v.d_min - v.d_max;
   if (PL) {
     if (threadIdx.x < 2) s_pl[threadIdx.x] = 0ull;
     if (tile_plastic) {
@@ -761,10 +766,32 @@ __device__ __forceinline__ void deliver_tile_body(
         s_rn[x] = tgt_lo + x < v.n ? v.sp.ring_n[tgt_lo + x] : 0u;
       for (uint32_t x = threadIdx.x; x < v.sp.hist * TW; x += blockDim.x) {
         const uint32_t q = x / TW, jj = x - q * TW;
-        if (tgt_lo + jj < v.n) {
+        if (tgt_lo + jj < v.n)
           s_rt[x] = v.sp.ring_t[(size_t)q * v.pitch + tgt_lo + jj];
-          s_rk[x] = v.sp.ring_k[(size_t)q * v.pitch + tgt_lo + jj];
+      }
+      __syncthreads();
+      // post trace of target j at horizon h: the trace right after its
+      // latest spike at or before h, decayed to h (0 if it never fired)
+      const uint32_t hm = v.sp.hist - 1u;
+      for (uint32_t x = threadIdx.x; x < W * TW; x += blockDim.x) {
+        const uint32_t hi = x / TW, jj = x - hi * TW;
+        const int32_t h = (int32_t)(h_lo + hi);
+        const uint32_t n = s_rn[jj];
+        const int32_t k_min = n > v.sp.hist ? (int32_t)(n - v.sp.hist) : 0;
+        float km = 0.f;
+        int32_t k = (int32_t)n - 1;
+        for (; k >= k_min; --k) {
+          const int32_t tp = s_rt[((uint32_t)k & hm) * TW + jj];
+          if (tp <= h) {
+            km = v.sp.ring_k[(size_t)((uint32_t)k & hm) * v.pitch + tgt_lo + jj] *
+                 exp2f(-(float)(h - tp) * v.sp.l2_minus);
+            break;
+          }
         }
+        // every kept spike is after h but older ones were dropped: the
+        // trace at h is unknown (-1; an update that needs it is counted
+        // with the truncated windows)
+        s_km[x] = (k < k_min && n > v.sp.hist) ? -1.f : km;
       }
     }
   }
@@ -809,11 +836,12 @@ __device__ __forceinline__ void deliver_tile_body(
   auto plastic = [&](uint32_t tgt, uint32_t k_run, int32_t t, uint32_t d,
                      float w, uint64_t r) -> float {
     const uint32_t j = tgt - tgt_lo;
+    const float km = s_km[(uint32_t)((long long)t - (long long)d - h_lo) * TW + j];
     const StdpOut o = stdp_weight(w, t, d, s_tprev[k_run], s_kprev[k_run], j,
-                                  TW, s_rt, s_rk, s_rn[j], sc);
+                                  TW, s_rt, fmaxf(km, 0.f), s_rn[j], sc);
     v.sp.wp[r] = o.w;
     ++my_pl;
-    my_trunc += o.trunc;
+    my_trunc += o.trunc | (km < 0.f ? 1u : 0u);
     return o.w;
   };
   auto load_pass = [&](Rec1<FMT> (&r)[U][PER], float (&wv)[U][PER], uint32_t k0,
@@ -1136,9 +1164,10 @@ cudaError_t launch_deliver(const NetView& v, unsigned long long* pair,
 }
 
 size_t tiled_smem_bytes(const NetView& v) {
+  // accumulator; plastic nets: spike-time rings, counts, post-trace table
   return (size_t)v.tile_w *
          (2 * (size_t)v.window * sizeof(int) +
-          (v.plastic ? (size_t)v.sp.hist * 8 + sizeof(uint32_t) : 0));
+          (v.plastic ? (size_t)v.sp.hist * 4 + 4 + (size_t)v.window * 4 : 0));
 }
 
 template <int FMT, bool COUNT, bool PL>
