@@ -441,19 +441,28 @@ int snn_destroy(snn_net* net);
  * update/deliver cycle.)
  *
  * A server owns a device-memory budget.  Submitted requests queue in
- * arrival order; a builder thread admits the head request once its
- * estimated footprint fits the budget and builds its connection store while
- * the admitted nets keep running.  Each snn_server_step advances every
- * admitted net by its next interval in ONE batched update launch and ONE
- * batched tiled-delivery launch for all nets together (block -> net lookup
- * table; per-net clock, state, store and interval), graph-captured while the
- * batch is unchanged; a small autotuner picks how many intervals one step
- * runs (1, 2, 4 or 8) from measured time per interval.  Nets that reached
- * their step count are retired: their counters (and spikes, if recorded)
- * move to the request's result and their memory is released.
+ * arrival order in one of two size classes (below 2^24 synapses, and the
+ * rest); each class has a builder thread that admits its oldest request
+ * once the estimated footprint fits the budget, and builds the connection
+ * store on the net's own stream at the lowest stream priority while the
+ * admitted nets keep running, so a small request never waits behind the
+ * build of a large one.  Running nets are grouped into three lanes by
+ * synapse count (< 2^24, < 2^27, the rest); each lane has its own stream
+ * (smaller nets: higher priority), block -> net lookup tables and a wall-time
+ * autotuner that picks how many intervals one step runs (1, 2, 4, 8 or 16).
+ * Each snn_server_step advances every lane's nets by that many intervals in
+ * ONE batched update launch and ONE batched tiled-delivery launch per
+ * interval for all nets of the lane (per-net clock, state, store and
+ * interval), replayed from a graph cached per interval count while the lane
+ * is unchanged.  Nets that reached their step count are retired: their
+ * counters (and spikes, if recorded) move to the request's result and their
+ * memory is released.
  * Results do not depend on the mix: delivery sums are exact fixed point and
  * every random draw is keyed by (neuron, step), so a request's spikes are
  * bit-identical alone and batched.
+ * Threads: submit, poll, spikes, release and get_stats may be called from
+ * any thread; snn_server_step and snn_server_destroy from one thread at a
+ * time (the serving loop).
  * ---------------------------------------------------------------------- */
 typedef struct snn_server snn_server;
 
@@ -494,8 +503,9 @@ typedef struct snn_server_stats {
   uint64_t steps, intervals, kernel_launches;
   uint64_t events, spikes;  /* of finished requests */
   uint64_t mem_budget, mem_used;
-  int32_t intervals_per_step; /* current choice of the autotuner */
-  int32_t tuned;              /* 1 once the autotuner settled */
+  int32_t intervals_per_step; /* autotuner's choice for the lane that
+                                 ran the most intervals */
+  int32_t tuned;              /* 1 once every lane that stepped settled */
   double gpu_ms;              /* CUDA-event time of the batched launches */
 } snn_server_stats;
 
@@ -510,9 +520,10 @@ int snn_server_create(uint64_t mem_budget, int32_t weight_format,
  * (about one per 4.2e6, at most one per SM), since all served nets share
  * each delivery launch. */
 int snn_server_submit(snn_server* sv, const snn_request* req, uint64_t* id);
-/* Admit built nets, advance all running nets by one step (the autotuned
- * number of intervals), retire finished ones.  *n_active (optional): nets
- * running after the step.  Returns immediately when nothing is running. */
+/* Admit built nets, advance every lane by one step (its autotuned number
+ * of intervals), retire finished nets.  *n_active (optional): nets running
+ * after the step.  Returns immediately when nothing is running.  Not
+ * reentrant: call it from one thread. */
 int snn_server_step(snn_server* sv, int32_t* n_active);
 /* State and counters of a request (thread-safe). */
 int snn_server_poll(snn_server* sv, uint64_t id, snn_result* out);
@@ -523,7 +534,7 @@ int snn_server_spikes(snn_server* sv, uint64_t id, uint32_t* src, int32_t* t,
 /* Forget a finished request's result. */
 int snn_server_release(snn_server* sv, uint64_t id);
 int snn_server_get_stats(snn_server* sv, snn_server_stats* out);
-/* Stop the builder, free all nets; sv may be NULL. */
+/* Stop the builder threads, free all nets; sv may be NULL. */
 int snn_server_destroy(snn_server* sv);
 
 #ifdef __cplusplus

@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "snn_internal.cuh"
@@ -1100,7 +1101,8 @@ k_prepare_external(NetView v, const uint32_t* __restrict__ src,
   }
 }
 
-int g_deliver_blocks[2] = {0, 0};
+// grid of the atomic delivery (SMs x resident blocks), computed on first use
+std::atomic<int> g_deliver_blocks[2];
 
 template <int FMT>
 int deliver_blocks_for() {
@@ -1116,12 +1118,14 @@ int deliver_blocks_for() {
 }  // namespace
 
 int deliver_grid_size(int fmt) {
-  int k = fmt == SNN_W_FP32_12B ? 0 : 1;
-  if (g_deliver_blocks[k] == 0)
-    g_deliver_blocks[k] = fmt == SNN_W_FP32_12B
-                              ? deliver_blocks_for<SNN_W_FP32_12B>()
+  const int k = fmt == SNN_W_FP32_12B ? 0 : 1;
+  int b = g_deliver_blocks[k].load(std::memory_order_relaxed);
+  if (b == 0) {
+    b = fmt == SNN_W_FP32_12B ? deliver_blocks_for<SNN_W_FP32_12B>()
                               : deliver_blocks_for<SNN_W_BF16_8B>();
-  return g_deliver_blocks[k];
+    g_deliver_blocks[k].store(b, std::memory_order_relaxed);
+  }
+  return b;
 }
 
 cudaError_t launch_init_v(const NetView& v, const UpdConst* c, int random,
@@ -1170,20 +1174,31 @@ size_t tiled_smem_bytes(const NetView& v) {
           (v.plastic ? (size_t)v.sp.hist * 4 + 4 + (size_t)v.window * 4 : 0));
 }
 
+// Raise a tiled-delivery kernel's dynamic shared-memory limit once per
+// device (the attribute belongs to the kernel on the current device; `done`
+// is one bit per device, safe to set from several threads).
+template <class Kernel>
+cudaError_t allow_tile_smem(Kernel kernel, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           200 * 1024);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
+
 template <int FMT, bool COUNT, bool PL>
 cudaError_t launch_tiled_t(const NetView& v, unsigned long long* pair,
                            unsigned int* done, const SpikeEntry* list,
                            int from_list_range, int advance_time,
                            cudaStream_t s) {
   const size_t smem = tiled_smem_bytes(v);
-  static int configured = 0;   // per-process attribute, set once
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(
-        k_deliver_tiled<FMT, COUNT, PL>,
-        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    configured = 1;
-  }
+  static std::atomic<uint64_t> configured{0};
+  cudaError_t e = allow_tile_smem(k_deliver_tiled<FMT, COUNT, PL>, configured);
+  if (e != cudaSuccess) return e;
   k_deliver_tiled<FMT, COUNT, PL><<<v.n_tiles, kTileThreads, smem, s>>>(
       v, pair, done, list, from_list_range, advance_time);
   return cudaGetLastError();
@@ -1237,19 +1252,12 @@ cudaError_t launch_deliver_tiled_batch(int fmt, const BatchNet* nets,
                                        const uint2* bmap, uint32_t n_ctas,
                                        size_t smem, cudaStream_t s) {
   if (n_ctas == 0) return cudaSuccess;
-  static int configured[2] = {0, 0};
+  static std::atomic<uint64_t> configured[2];
   const int k = fmt == SNN_W_FP32_12B ? 0 : 1;
-  if (!configured[k]) {
-    cudaError_t e = k == 0
-        ? cudaFuncSetAttribute(k_deliver_tiled_batch<SNN_W_FP32_12B>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               200 * 1024)
-        : cudaFuncSetAttribute(k_deliver_tiled_batch<SNN_W_BF16_8B>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               200 * 1024);
-    if (e != cudaSuccess) return e;
-    configured[k] = 1;
-  }
+  cudaError_t e = k == 0
+      ? allow_tile_smem(k_deliver_tiled_batch<SNN_W_FP32_12B>, configured[0])
+      : allow_tile_smem(k_deliver_tiled_batch<SNN_W_BF16_8B>, configured[1]);
+  if (e != cudaSuccess) return e;
   if (k == 0)
     k_deliver_tiled_batch<SNN_W_FP32_12B><<<n_ctas, kTileThreads, smem, s>>>(nets, bmap);
   else
