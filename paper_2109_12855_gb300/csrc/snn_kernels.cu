@@ -547,14 +547,15 @@ k_deliver(NetView v, unsigned long long* pair_p, unsigned int* done_p,
 // short, about 74 records, so per-run synchronisation dominates.)
 //
 // Accumulation is exact fixed point: a weight w becomes x = w 2^(q-s),
-// split into hi = floor(x) and lo = round((x - hi) 2^s) in [0, 2^s]; hi and
-// lo are summed in two int32 arrays with shared-memory integer atomics, so
-// the sum is order-independent and the cell value is (H 2^s + L) 2^-q.
-// The scales come from bounds on one launch: a cell receives at most
-// E = min(spikes x max synapse multiplicity, max in-degree x spikes per
-// neuron per interval) events of magnitude <= max|w|; s makes E 2^s < 2^31
-// and q makes E max|w| 2^(q-s) + E < 2^31, so neither sum can overflow, and
-// the rounding error (<= 2^-(q+1) per event) is below that of FP32
+// split into hi = rint(x) and lo = rint((x - hi) 2^s) in [-2^(s-1), 2^(s-1)]
+// (hi 2^s + lo = rint(w 2^q)); hi and lo are summed in two int32 arrays
+// with shared-memory integer atomics, so the sum is order-independent and
+// the cell value is (H 2^s + L) 2^-q.  The scales come from bounds on one
+// launch: a cell receives at most E = min(spikes x max synapse
+// multiplicity, max in-degree x spikes per neuron per interval) events of
+// magnitude <= max|w|; s makes E 2^s < 2^31 and q makes
+// E max|w| 2^(q-s) + E < 2^31, so neither sum can overflow, and the
+// rounding error (<= 2^-(q+1) per event) is below that of FP32
 // accumulation.  If no such scales exist the CTA falls back to FP32
 // shared-memory atomics.  The CTA then adds its cells into the ring buffer
 // with plain coalesced read-modify-writes: no other CTA touches them.
@@ -563,7 +564,6 @@ k_deliver(NetView v, unsigned long long* pair_p, unsigned int* done_p,
 // ---------------------------------------------------------------------------
 constexpr int kTileThreads = 1024;
 constexpr int kTileWarps = kTileThreads / 32;
-constexpr int kDescBatch = 1024;   // spike runs described per pass
 
 template <int FMT> struct Rec1;
 template <> struct Rec1<SNN_W_FP32_12B> { uint32_t a, b, c; };
@@ -621,6 +621,23 @@ struct FixScale {
   double inv_q;    // 2^-q
 };
 
+// 2^k from the exponent bits (k inside the normal range of the type), and
+// floor(log2 x) of a positive normal double.
+__device__ __forceinline__ float pow2f(int k) {
+  return __int_as_float((k + 127) << 23);
+}
+__device__ __forceinline__ double pow2d(int k) {
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+__device__ __forceinline__ int ilog2d(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF) - 1023;
+}
+
+// Largest s <= 23 and q - s <= 21 - ceil(log2 max|w|): a scaled weight
+// x = w 2^(q-s) then has |x| < 2^22 and |(x - rint x) 2^s| <= 2^22, the
+// range in which adding 1.5 2^23 rounds to an integer (fixed_split).
+constexpr int kFixMaxShift = 23;
+
 __device__ FixScale fix_scale(const NetView& v, uint64_t n_sp,
                               bool per_interval) {
   FixScale f{0, 0, 1.f, 1.f, 1.0};
@@ -629,24 +646,45 @@ __device__ FixScale fix_scale(const NetView& v, uint64_t n_sp,
     const uint64_t e2 = (uint64_t)v.k_in_max * (v.spikes_per_iv ? v.spikes_per_iv : 1u);
     if (e2 < e) e = e2;
   }
-  if (e == 0 || e >= (1ull << 30) || !(v.max_abs_w > 0.f)) return f;
+  if (e == 0 || e >= (1ull << 30) || !(v.max_abs_w > 0.f) ||
+      !(v.max_abs_w <= 3.0e38f))
+    return f;
   const int lg = 63 - __clzll((long long)e);  // 2^lg <= e < 2^(lg+1)
-  const int sh = 30 - lg;                     // e 2^sh < 2^31
-  const double lim = (2147483647.0 - (double)e) / ((double)e * v.max_abs_w);
-  if (!(lim >= 1.0)) return f;
-  int qs = (int)floor(log2(lim));             // 2^(q - s) <= lim
-  // keep max|w| 2^q below 2^62 and the scales inside float's range
-  const int wexp = (int)ceil(log2((double)v.max_abs_w));
-  int q = sh + qs;
-  if (q > 62 - wexp) q = 62 - wexp;
-  if (q - sh > 100) q = sh + 100;
-  if (q - sh < -100) return f;
+  const int sh = min(30 - lg, kFixMaxShift);  // e 2^sh < 2^31
+  // largest qs with e max|w| 2^qs <= 2^31 - 1 - e: the hi sums (each
+  // |hi| <= |x| + 1/2) cannot overflow
+  const double A = 2147483647.0 - (double)e;
+  const double B = (double)e * (double)v.max_abs_w;
+  int qs = ilog2d(A) - ilog2d(B);  // floor(log2(A / B)) is qs or qs - 1
+  if (B * pow2d(qs) > A) --qs;
+  const uint32_t wb = __float_as_uint(v.max_abs_w);
+  const int wexp = (int)((wb >> 23) & 0xFFu) - 127 + ((wb & 0x7FFFFFu) ? 1 : 0);
+  qs = min(qs, 21 - wexp);
+  if (qs < 0) return f;
+  qs = min(qs, 100);
+  const int q = sh + qs;
   f.fixed = 1;
   f.sh = sh;
-  f.scale_hs = (float)ldexp(1.0, q - sh);
-  f.scale_s = (float)ldexp(1.0, sh);
-  f.inv_q = ldexp(1.0, -q);
+  f.scale_hs = pow2f(qs);
+  f.scale_s = pow2f(sh);
+  f.inv_q = pow2d(-q);
   return f;
+}
+
+// Exact split of x = w 2^(q-s) (|x| < 2^22, s <= 23): hi = rint(x),
+// lo = rint((x - hi) 2^s), so hi 2^s + lo = rint(w 2^q).  Adding
+// M = 1.5 2^23 puts a value of magnitude <= 2^22 into [2^23, 2^24], where
+// the float spacing is 1: the sum is rounded to an integer (to nearest,
+// ties to even) whose value is the bit pattern minus M's.  Only FMA-pipe
+// arithmetic and integer subtractions; x - hi is exact.
+__device__ __forceinline__ void fixed_split(float w, const FixScale& fx,
+                                            int& hi, int& lo) {
+  constexpr float kM = 12582912.0f;  // 1.5 * 2^23
+  const float x = __fmul_rn(w, fx.scale_hs);
+  const float y = __fadd_rn(x, kM);
+  hi = __float_as_int(y) - __float_as_int(kM);
+  const float fr = __fsub_rn(x, __fsub_rn(y, kM));
+  lo = __float_as_int(__fmaf_rn(fr, fx.scale_s, kM)) - __float_as_int(kM);
 }
 
 // Plastic weight of an E->E synapse at its presynaptic spike t with delay
@@ -711,19 +749,19 @@ template <int FMT, bool COUNT, bool PL>
 __device__ __forceinline__ void deliver_tile_body(
     const NetView& v, unsigned long long* pair_p, unsigned int* done_p,
     const SpikeEntry* __restrict__ list, int from_list_range, int advance_time,
-    uint32_t tile, int* acc_mem) {
+    uint32_t tile, int* acc_mem, uint32_t desc_off, uint32_t desc_cap) {
   // U runs per warp pass, PER records per lane of each loaded before use
   // (plastic nets also hold each record's plastic weight: fewer runs)
   constexpr int U = PL ? (FMT == SNN_W_FP32_12B ? 1 : 2)
                        : (FMT == SNN_W_FP32_12B ? 2 : 4);
   constexpr int PER = 3;
-  __shared__ SegDesc s_desc[kDescBatch];
-  __shared__ int32_t s_tprev[PL ? kDescBatch : 1];   // previous pre spike
-  __shared__ float s_kprev[PL ? kDescBatch : 1];     // its trace; < 0: static
+  // run descriptors of one batch (desc_cap spikes), after the accumulator
+  SegDesc* const s_desc =
+      reinterpret_cast<SegDesc*>(reinterpret_cast<char*>(acc_mem) + desc_off);
+  int32_t* const s_tprev = reinterpret_cast<int32_t*>(s_desc + desc_cap);  // PL
+  float* const s_kprev = reinterpret_cast<float*>(s_tprev + desc_cap);     // PL
   __shared__ unsigned long long s_pl[2];             // plastic updates, truncations
-  __shared__ unsigned long long s_pair;
-  __shared__ long long s_base;
-  __shared__ int s_inwin;
+  __shared__ uint32_t s_next;                        // next run of the batch
   __shared__ FixScale s_fx;
   const uint32_t TW = v.tile_w;
   const uint32_t W = (uint32_t)v.window;
@@ -731,22 +769,25 @@ __device__ __forceinline__ void deliver_tile_body(
   const uint32_t tgt_lo = tile * TW;
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
-    const unsigned long long pr =
-        *reinterpret_cast<volatile unsigned long long*>(pair_p);
-    s_pair = pr;
-    if (from_list_range) {
-      const long long tmin = v.ctl->ext_tmin, tmax = v.ctl->ext_tmax;
-      s_base = tmin + v.d_min;
-      s_inwin = (tmax - tmin) + (v.d_max - v.d_min) + 1 <= (long long)W;
-    } else {
-      s_base = v.ctl->t_now + v.d_min;
-      s_inwin = 1;
-    }
-    s_fx = fix_scale(v, pr >> 32, !from_list_range);
+  // every thread reads the launch's list size and window (same addresses);
+  // thread 0 derives the fixed-point scales meanwhile
+  const unsigned long long pr =
+      *reinterpret_cast<volatile unsigned long long*>(pair_p);
+  const uint32_t n_sp = (uint32_t)(pr >> 32);
+  long long base;
+  bool inwin;
+  if (from_list_range) {
+    const long long tmin = v.ctl->ext_tmin, tmax = v.ctl->ext_tmax;
+    base = tmin + v.d_min;
+    inwin = (tmax - tmin) + (v.d_max - v.d_min) + 1 <= (long long)W;
+  } else {
+    base = v.ctl->t_now + v.d_min;
+    inwin = true;
   }
-  __syncthreads();
-  const FixScale fx = s_fx;
+  if (threadIdx.x == 0) {
+    s_fx = fix_scale(v, n_sp, !from_list_range);
+    s_next = 0u;
+  }
   int* accH = acc_mem;                                // fixed: hi parts
   int* accL = acc_mem + cells;                        // fixed: lo parts
   float* accF = reinterpret_cast<float*>(acc_mem);    // FP32 fallback
@@ -759,7 +800,7 @@ __device__ __forceinline__ void deliver_tile_body(
   const bool tile_plastic = PL && tgt_lo < v.sp.n_exc;
   uint32_t my_pl = 0, my_trunc = 0;
   // first horizon: (interval start) - d_max
-  const long long h_lo = s_base - v.d_min - v.d_max;
+  const long long h_lo = base - v.d_min - v.d_max;
   if (PL) {
     if (threadIdx.x < 2) s_pl[threadIdx.x] = 0ull;
     if (tile_plastic) {
@@ -796,21 +837,20 @@ __device__ __forceinline__ void deliver_tile_body(
       }
     }
   }
-  __syncthreads();
-  const uint32_t n_sp = (uint32_t)(s_pair >> 32);
-  const long long base = s_base;
-  const bool inwin = s_inwin != 0;
   const uint32_t row_stride = v.n_tiles + 1;
+  FixScale fx{};  // thread 0's s_fx, read after the first barrier
 
   // one event: cell = d TW + tgt + off, off = (t - base) TW - tgt_lo per run
   auto add = [&](uint32_t tgt, int32_t t, int32_t off, uint32_t d, float w) {
     if (inwin) {
       const uint32_t cell = d * TW + tgt + (uint32_t)off;
       if (fx.fixed) {
-        const float xw = w * fx.scale_hs;
-        const float hf = floorf(xw);
-        atomicAdd(&accH[cell], (int)hf);
-        atomicAdd(&accL[cell], __float2int_rn((xw - hf) * fx.scale_s));
+        int hi, lo;
+        fixed_split(w, fx, hi, lo);
+        atomicAdd(&accH[cell], hi);
+        // BF16 weights have 8 significant bits: their scaled value is
+        // usually an integer, and a zero low part needs no addition
+        if (FMT == SNN_W_FP32_12B || lo != 0) atomicAdd(&accL[cell], lo);
       } else {
         atomicAdd(&accF[cell], w);
       }
@@ -896,36 +936,77 @@ __device__ __forceinline__ void deliver_tile_body(
     }
   };
 
-  for (uint32_t j0 = 0; j0 < n_sp; j0 += kDescBatch) {
-    const uint32_t nb = n_sp - j0 < (uint32_t)kDescBatch ? n_sp - j0
-                                                         : (uint32_t)kDescBatch;
-    // (A) describe this batch's runs: independent loads across threads
-    for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) {
-      const SpikeEntry e = list[j0 + k];
-      SegDesc sd{0, 0u, e.t};
-      if (e.src < v.n_src) {
-        const uint32_t* to = v.tile_off + (uint64_t)e.src * row_stride + tile;
-        const uint32_t a = to[0], b = to[1];
-        sd.beg = v.row_ptr[e.src] + a;
-        sd.len = b - a;
+  // (A) describe the runs of spikes [j0, j0 + nb): kDU list entries per
+  // thread in flight, then their tile-index words and row starts
+  constexpr int kDU = PL ? 1 : 4;
+  auto describe = [&](uint32_t j0, uint32_t nb) {
+    for (uint32_t k0 = threadIdx.x; k0 < nb; k0 += kDU * blockDim.x) {
+      SpikeEntry e[kDU];
+#pragma unroll
+      for (int u = 0; u < kDU; ++u) {
+        const uint32_t k = k0 + u * blockDim.x;
+        if (k < nb) e[u] = list[j0 + k];
       }
-      s_desc[k] = sd;
-      if (PL) {
-        const bool exc = e.src < v.sp.n_exc;
-        s_tprev[k] = exc ? v.sp.prev_t[e.src] : kNoSpike;
-        s_kprev[k] = exc ? v.sp.prev_k[e.src] : -1.f;
+#pragma unroll
+      for (int u = 0; u < kDU; ++u) {
+        const uint32_t k = k0 + u * blockDim.x;
+        if (k < nb) {
+          SegDesc sd{0, 0u, e[u].t};
+          if (e[u].src < v.n_src) {
+            const uint32_t* to = v.tile_off + (uint64_t)e[u].src * row_stride + tile;
+            const uint32_t a = to[0], b = to[1];
+            sd.beg = v.row_ptr[e[u].src] + a;
+            sd.len = b - a;
+          }
+          s_desc[k] = sd;
+          if (PL) {
+            const bool exc = e[u].src < v.sp.n_exc;
+            s_tprev[k] = exc ? v.sp.prev_t[e[u].src] : kNoSpike;
+            s_kprev[k] = exc ? v.sp.prev_k[e[u].src] : -1.f;
+          }
+        }
       }
     }
+  };
+  // next U runs for this warp (shared counter: warps that met short runs or
+  // fast loads take more)
+  auto grab = [&]() {
+    uint32_t k = 0u;
+    if (lane == 0) k = atomicAdd(&s_next, (uint32_t)U);
+    return __shfl_sync(kFull, k, 0);
+  };
+
+  uint32_t j0 = 0;
+  do {
+    const uint32_t nb = min(desc_cap, n_sp - j0);
+    describe(j0, nb);
+    if (threadIdx.x == 0) s_next = 0u;
     __syncthreads();
-    // (B) each warp takes U runs per pass: all loads first, then the adds
-    for (uint32_t k = warp * U; k < nb; k += kTileWarps * U) {
-      Rec1<FMT> r[U][PER];
-      float wv[U][PER];
-      load_pass(r, wv, k, nb);
-      add_pass(r, wv, k, nb);
+    fx = s_fx;
+    // (B) each warp takes U runs at a time: all loads first, then the adds
+    // (plastic nets: a fixed share per warp, the registers being spent on
+    // the weight update)
+    if constexpr (PL) {
+      for (uint32_t k = warp * U; k < nb; k += kTileWarps * U) {
+        Rec1<FMT> r[U][PER];
+        float wv[U][PER];
+        load_pass(r, wv, k, nb);
+        add_pass(r, wv, k, nb);
+      }
+    } else {
+      uint32_t k = grab();
+      while (k < nb) {
+        Rec1<FMT> r[U][PER];
+        float wv[U][PER];
+        load_pass(r, wv, k, nb);
+        const uint32_t k_next = grab();
+        add_pass(r, wv, k, nb);
+        k = k_next;
+      }
     }
+    j0 += nb;
     __syncthreads();  // s_desc is rewritten by the next batch
-  }
+  } while (j0 < n_sp);
   if (inwin) {
     // each thread owns whole target columns; the ring-buffer reads of
     // kFlush slots are issued together, then the sums are written back
@@ -998,10 +1079,11 @@ template <int FMT, bool COUNT, bool PL>
 __global__ void __launch_bounds__(kTileThreads, 1)
 k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
                 const SpikeEntry* __restrict__ list, int from_list_range,
-                int advance_time) {
+                int advance_time, uint32_t desc_off, uint32_t desc_cap) {
   extern __shared__ __align__(16) int acc_mem[];
   deliver_tile_body<FMT, COUNT, PL>(v, pair_p, done_p, list, from_list_range,
-                                    advance_time, blockIdx.x, acc_mem);
+                                    advance_time, blockIdx.x, acc_mem, desc_off,
+                                    desc_cap);
 }
 
 // All nets of a batch in one launch: CTA b delivers tile bmap[b].y of net
@@ -1009,12 +1091,13 @@ k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
 template <int FMT>
 __global__ void __launch_bounds__(kTileThreads, 1)
 k_deliver_tiled_batch(const BatchNet* __restrict__ nets,
-                      const uint2* __restrict__ bmap) {
+                      const uint2* __restrict__ bmap, uint32_t desc_off,
+                      uint32_t desc_cap) {
   extern __shared__ __align__(16) int acc_mem[];
   const uint2 m = bmap[blockIdx.x];
   const NetView v = nets[m.x].v;
   deliver_tile_body<FMT, false, false>(v, &v.ctl->pair, &v.ctl->done, v.list,
-                                       0, 1, m.y, acc_mem);
+                                       0, 1, m.y, acc_mem, desc_off, desc_cap);
 }
 
 // ---------------------------------------------------------------------------
@@ -1174,20 +1257,55 @@ size_t tiled_smem_bytes(const NetView& v) {
           (v.plastic ? (size_t)v.sp.hist * 4 + 4 + (size_t)v.window * 4 : 0));
 }
 
-// Raise a tiled-delivery kernel's dynamic shared-memory limit once per
-// device (the attribute belongs to the kernel on the current device; `done`
-// is one bit per device, safe to set from several threads).
+// Raise a tiled-delivery kernel's dynamic shared-memory limit to all that
+// its static shared memory leaves, once per device (the attribute belongs to
+// the kernel on the current device); returns that limit.  `lim` holds one
+// entry per device and is safe to fill from several threads.
 template <class Kernel>
-cudaError_t allow_tile_smem(Kernel kernel, std::atomic<uint64_t>& done) {
+cudaError_t allow_tile_smem(Kernel kernel, std::atomic<uint32_t>* lim,
+                            size_t* dyn_max) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  const uint64_t bit = 1ull << (dev & 63);
-  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           200 * 1024);
-  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
-  return e;
+  std::atomic<uint32_t>& slot = lim[dev & 63];
+  const uint32_t have = slot.load(std::memory_order_acquire);
+  if (have) {
+    *dyn_max = have;
+    return cudaSuccess;
+  }
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  const int dyn = optin - (int)fa.sharedSizeBytes;
+  if (dyn <= 0) return cudaErrorInvalidConfiguration;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  if (e != cudaSuccess) return e;
+  slot.store((uint32_t)dyn, std::memory_order_release);
+  *dyn_max = (size_t)dyn;
+  return cudaSuccess;
+}
+
+// Run descriptors go after the accumulator (and the plastic state): as
+// many as the remaining shared memory holds, within kDescBytes (a larger
+// shared-memory carve-out would take L1 capacity from the record loads).
+constexpr size_t kDescBytes = 32 * 1024;
+struct DescLayout {
+  uint32_t off, cap;
+  size_t smem;
+};
+cudaError_t desc_layout(size_t used, size_t dyn_max, bool plastic,
+                        DescLayout* out) {
+  const size_t per = sizeof(SegDesc) + (plastic ? 8u : 0u);
+  const size_t off = (used + 15u) & ~(size_t)15u;
+  if (dyn_max < off + 32u * per) return cudaErrorInvalidConfiguration;
+  const size_t cap = std::min(kDescBytes, dyn_max - off) / per;
+  out->off = (uint32_t)off;
+  out->cap = (uint32_t)cap;
+  out->smem = off + cap * per;
+  return cudaSuccess;
 }
 
 template <int FMT, bool COUNT, bool PL>
@@ -1195,12 +1313,15 @@ cudaError_t launch_tiled_t(const NetView& v, unsigned long long* pair,
                            unsigned int* done, const SpikeEntry* list,
                            int from_list_range, int advance_time,
                            cudaStream_t s) {
-  const size_t smem = tiled_smem_bytes(v);
-  static std::atomic<uint64_t> configured{0};
-  cudaError_t e = allow_tile_smem(k_deliver_tiled<FMT, COUNT, PL>, configured);
+  static std::atomic<uint32_t> lim[64];
+  size_t dm = 0;
+  cudaError_t e = allow_tile_smem(k_deliver_tiled<FMT, COUNT, PL>, lim, &dm);
   if (e != cudaSuccess) return e;
-  k_deliver_tiled<FMT, COUNT, PL><<<v.n_tiles, kTileThreads, smem, s>>>(
-      v, pair, done, list, from_list_range, advance_time);
+  DescLayout dl;
+  e = desc_layout(tiled_smem_bytes(v), dm, PL, &dl);
+  if (e != cudaSuccess) return e;
+  k_deliver_tiled<FMT, COUNT, PL><<<v.n_tiles, kTileThreads, dl.smem, s>>>(
+      v, pair, done, list, from_list_range, advance_time, dl.off, dl.cap);
   return cudaGetLastError();
 }
 
@@ -1252,16 +1373,22 @@ cudaError_t launch_deliver_tiled_batch(int fmt, const BatchNet* nets,
                                        const uint2* bmap, uint32_t n_ctas,
                                        size_t smem, cudaStream_t s) {
   if (n_ctas == 0) return cudaSuccess;
-  static std::atomic<uint64_t> configured[2];
+  static std::atomic<uint32_t> lim[2][64];
   const int k = fmt == SNN_W_FP32_12B ? 0 : 1;
+  size_t dm = 0;
   cudaError_t e = k == 0
-      ? allow_tile_smem(k_deliver_tiled_batch<SNN_W_FP32_12B>, configured[0])
-      : allow_tile_smem(k_deliver_tiled_batch<SNN_W_BF16_8B>, configured[1]);
+      ? allow_tile_smem(k_deliver_tiled_batch<SNN_W_FP32_12B>, lim[0], &dm)
+      : allow_tile_smem(k_deliver_tiled_batch<SNN_W_BF16_8B>, lim[1], &dm);
+  if (e != cudaSuccess) return e;
+  DescLayout dl;  // after the largest accumulator of the batch
+  e = desc_layout(smem, dm, false, &dl);
   if (e != cudaSuccess) return e;
   if (k == 0)
-    k_deliver_tiled_batch<SNN_W_FP32_12B><<<n_ctas, kTileThreads, smem, s>>>(nets, bmap);
+    k_deliver_tiled_batch<SNN_W_FP32_12B><<<n_ctas, kTileThreads, dl.smem, s>>>(
+        nets, bmap, dl.off, dl.cap);
   else
-    k_deliver_tiled_batch<SNN_W_BF16_8B><<<n_ctas, kTileThreads, smem, s>>>(nets, bmap);
+    k_deliver_tiled_batch<SNN_W_BF16_8B><<<n_ctas, kTileThreads, dl.smem, s>>>(
+        nets, bmap, dl.off, dl.cap);
   return cudaGetLastError();
 }
 
