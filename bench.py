@@ -93,9 +93,9 @@ def stdp_config(w_e):
 # ncu over all 667 launches of one timed step of the workload and divided by
 # that step's events (profiles/dram_k_deliver_tiled_balanced-112500-fp32.md).
 # It stands for the kernel it was measured on: the entry is used only while
-# the kernel sources hash to the recorded prefix.
+# the kernel sources (comments aside) hash to the recorded prefixes.
 TRAFFIC_B_PER_EVENT = {
-    "balanced-112500-fp32": (12.550, "00845e2b7663d542", "98fd69d359453942"),
+    "balanced-112500-fp32": (12.549, "7fab6757283fd352", "da2deec8b483e222"),
 }
 # serving: a Poisson stream of independent balanced nets (BF16 records,
 # N log-uniform in [1,250, 112,500], 100 ms - 1 s each), mean rate in req/s
@@ -312,11 +312,21 @@ def build_net(wl, fmt, nu_ext, seed, stream, log_cap=0, deliver_mode=0,
     return net, w_e
 
 
+def _code_only(text):
+    """Source text without comments and with whitespace collapsed: edits of
+    comments leave the compiled kernel, and so the hash, unchanged."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_sources_hash():
     import hashlib
     csrc = os.path.join(ROOT, "paper_2109_12855_gb300", "csrc")
-    return tuple(hashlib.sha256(open(os.path.join(csrc, f), "rb").read())
-                 .hexdigest()[:16] for f in ("snn_kernels.cu", "snn_internal.cuh"))
+    return tuple(hashlib.sha256(_code_only(open(os.path.join(csrc, f)).read())
+                                .encode()).hexdigest()[:16]
+                 for f in ("snn_kernels.cu", "snn_internal.cuh"))
 
 
 def measured_traffic(workload, events_per_launch):

@@ -540,11 +540,13 @@ k_deliver(NetView v, unsigned long long* pair_p, unsigned int* done_p,
 // base .. base + window - 1 that one interval can reach (base = interval
 // start + min delay).  Rows are sorted by target tile, so the records of
 // spike j for tile tau are one contiguous run, located by the row's tile
-// index.  (A) the CTA describes a batch of runs in shared memory; (B) each
-// of its 32 warps takes U runs per pass and loads up to PER records per lane
-// of each before adding any (independent loads in flight).  (Staging the
-// runs into shared memory with bulk copies was measured slower: the runs are
-// short, about 74 records, so per-run synchronisation dominates.)
+// index.  (A) the CTA describes a batch of runs in shared memory; (B) its 32
+// warps take U runs at a time from a shared counter and load up to PER
+// records per lane of each before adding any (independent loads in flight).
+// (Staging the runs through shared memory, with bulk copies or per-lane
+// asynchronous copies, was measured slower: each record then passes through
+// shared memory twice beside its two atomics, and every run of ~74 records
+// pays a copy and a wait.)
 //
 // Accumulation is exact fixed point: a weight w becomes x = w 2^(q-s),
 // split into hi = rint(x) and lo = rint((x - hi) 2^s) in [-2^(s-1), 2^(s-1)]
