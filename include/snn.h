@@ -139,6 +139,15 @@ typedef struct snn_params {
                              snn_read_pending) and agree on the accumulation
                              bounds (snn_get_bounds / snn_set_bounds) so that
                              their union equals the whole net bit for bit. */
+  int32_t acc_words;      /* words per cell of the tiled delivery's exact
+                             accumulator: 0 = automatic (one word for a BF16
+                             store when the connection rule proves that every
+                             stored weight is a multiple of the smallest
+                             fixed-point step an interval's spike list can
+                             need, which halves the shared memory per target;
+                             else two), 2 = always two.  Both give the same
+                             sums. */
+  int32_t reserved_;      /* 0 */
 } snn_params;
 
 /* Fixed in-degree connection rule (the benchmark model's random
@@ -184,6 +193,8 @@ typedef struct snn_stats {
                                    past the kept history (see snn_set_stdp) */
   uint32_t first_neuron;        /* global index of local neuron 0 */
   uint32_t n_sources;           /* rows of the store (the whole population) */
+  int32_t acc_words;            /* words per accumulator cell (1 or 2) */
+  int32_t reserved_;
 } snn_stats;
 
 /* Bounds of one delivery launch's exact accumulation (see snn_set_bounds). */

@@ -5,6 +5,7 @@
 // captures full intervals into CUDA graphs, and implements the read-back,
 // state and statistics calls.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdint.h>
@@ -252,14 +253,17 @@ int set_device(snn_net* net) {
 // would not fit them, the width is rounded up to a power of two.
 // per_target: shared-memory bytes a tile needs per target beyond its
 // accumulator (the post-spike rings of a plastic net)
+// acc_words: int32 words per accumulator cell (1 or 2).
 void choose_tiles(uint32_t n, int window, int32_t hint, size_t per_target,
-                  uint32_t* tile_w, int* lo_bits, uint32_t* n_tiles) {
+                  int acc_words, uint32_t* tile_w, int* lo_bits,
+                  uint32_t* n_tiles) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms < 1) sms = 1;
   const uint64_t tw_max = std::max<uint64_t>(
-      32, kTileSmemBudget / (8ull * std::max(window, 1) + per_target));
+      32, kTileSmemBudget /
+              (4ull * acc_words * std::max(window, 1) + per_target));
   uint64_t tw = n;
   for (uint64_t k = 1; k <= 4096; ++k) {
     tw = (n + k * sms - 1) / (k * sms);
@@ -284,7 +288,7 @@ void choose_tiles(uint32_t n, int window, int32_t hint, size_t per_target,
 
 void snn::tile_geometry(uint32_t n, int window, int32_t hint, uint32_t* tile_w,
                         int* lo_bits, uint32_t* n_tiles) {
-  choose_tiles(n, window, hint, 0, tile_w, lo_bits, n_tiles);
+  choose_tiles(n, window, hint, 0, 2, tile_w, lo_bits, n_tiles);
 }
 
 namespace {
@@ -300,8 +304,110 @@ bool use_tiled(const snn_net* net) {
   return net->p.deliver_mode == SNN_DELIVER_TILED && net->n_syn > 0 &&
          net->tile_off &&
          (size_t)net->tile_w *
-                 ((size_t)net->window * 8 + stdp_bytes_per_target(net, net->window)) <=
+                 ((size_t)net->window * 4 * net->acc_words +
+                  stdp_bytes_per_target(net, net->window)) <=
              kTileSmemBudget;
+}
+
+// ---- one-word accumulator cells -----------------------------------------
+// The tiled delivery sums x = w 2^(q-s) split as hi = rint(x) and
+// lo = rint((x - hi) 2^s).  When every stored weight is a multiple of 2^-g
+// and q - s >= g, x is an integer and lo = 0: a cell needs one word.  The
+// scales of a launch follow from its event bound E and max|w| (the kernel's
+// fix_scale); q - s only grows as E or max|w| shrink, so the bounds of the
+// interval lists (E <= max in-degree x spikes per neuron per interval) and
+// an upper bound of max|w| give the smallest q - s any interval can get.
+
+// q - s of the kernel's fix_scale for event bound e and max|w| (-1: FP32).
+int fixed_qs_host(uint64_t e, double max_abs_w) {
+  const float mw = (float)max_abs_w;
+  if (e == 0 || e >= (1ull << 30) || !(mw > 0.f) || !(mw <= 3.0e38f)) return -1;
+  const double A = 2147483647.0 - (double)e;
+  const double B = (double)e * (double)mw;
+  int qs = ilogb(A) - ilogb(B);
+  if (B * ldexp(1.0, qs) > A) --qs;
+  uint32_t wb;
+  memcpy(&wb, &mw, 4);
+  const int wexp = (int)((wb >> 23) & 0xFFu) - 127 + ((wb & 0x7FFFFFu) ? 1 : 0);
+  qs = std::min(qs, 21 - wexp);
+  if (qs < 0) return -1;
+  return std::min(qs, 100);
+}
+
+// Exponent of the lowest set bit of a nonzero double (exact for the float
+// and bfloat16 values the store holds).
+int lowbit_exp(double v) {
+  int e = 0;
+  const double m = frexp(fabs(v), &e);           // |v| = m 2^e, m in [0.5, 1)
+  uint64_t i = (uint64_t)ldexp(m, 53);           // integer, exact
+  return e - 53 + __builtin_ctzll(i);
+}
+
+// The value a weight is stored as.
+double stored_weight(double w, int fmt) {
+  if (fmt == SNN_W_FP32_12B) return (double)(float)w;
+  return (double)bf16_to_f32(bf16_bits_rne(w));
+}
+
+// Bounds of the stored weights: every nonzero one is a multiple of 2^g_min
+// (g_min = INT_MAX: all zero) and at most w_max in magnitude.
+struct WeightBounds {
+  int g_min = INT_MAX;
+  double w_max = 0.0;
+  bool ok = true;  // false: no useful bound (weights may come near zero)
+  void add_value(double stored) {
+    if (stored == 0.0) return;
+    g_min = std::min(g_min, lowbit_exp(stored));
+    w_max = std::max(w_max, fabs(stored));
+  }
+};
+
+// One population of the fixed-in-degree rule: mean + sd z, |z| <= 6.7 for
+// the Box-Muller draw of two 32-bit uniforms (u1 >= 2^-32), clipped at 0 on
+// the side the rule clips.
+void add_population(WeightBounds* b, double mean, double sd, bool clip_neg,
+                    bool clip_pos, int fmt) {
+  if (sd == 0.0) {
+    double x = mean;
+    if (clip_neg && x < 0.0) x = 0.0;
+    if (clip_pos && x > 0.0) x = 0.0;
+    b->add_value(stored_weight(x, fmt));
+    return;
+  }
+  const double span = 6.7 * fabs(sd);
+  if (!(fabs(mean) > span)) {  // the draws can come arbitrarily near zero
+    b->ok = false;
+    return;
+  }
+  const double lo = (fabs(mean) - span) * (1.0 - 0x1p-7);  // after rounding
+  const double hi = (fabs(mean) + span) * (1.0 + 0x1p-7);
+  int e = 0;
+  frexp(lo, &e);  // 2^(e-1) <= lo: a stored value >= lo has its lowest set
+                  // bit at or above 2^(e - 1 - fraction bits)
+  b->g_min = std::min(b->g_min, e - 1 - (fmt == SNN_W_FP32_12B ? 23 : 7));
+  b->w_max = std::max(b->w_max, hi);
+}
+
+// Decide the accumulator cells of a net about to build its store.
+void decide_acc_words(snn_net* net, const WeightBounds& b, uint32_t k_in_max,
+                      int max_interval) {
+  net->acc_words = 2;
+  net->acc_qs_min = 0;
+  if (net->p.acc_words == 2 || net->stdp_on || !b.ok ||
+      net->fmt != SNN_W_BF16_8B)
+    return;
+  if (b.g_min == INT_MAX) {  // every weight is zero
+    net->acc_words = 1;
+    return;
+  }
+  const uint32_t refr = (uint32_t)net->uc.refr_steps;
+  const uint64_t spikes = ((uint64_t)max_interval + refr) / (refr + 1u);
+  const int qs = fixed_qs_host((uint64_t)k_in_max * std::max<uint64_t>(spikes, 1),
+                               b.w_max);
+  if (qs >= 0 && qs >= -b.g_min) {
+    net->acc_words = 1;
+    net->acc_qs_min = -b.g_min;
+  }
 }
 
 cudaError_t launch_deliver_any(snn_net* net, unsigned long long* pair,
@@ -352,8 +458,8 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
   // tiles sized for the widest window the interval can reach
   const int iv = net->p.interval ? net->p.interval : d_lo;
   choose_tiles(net->n, iv + (d_hi - d_lo), net->p.tile_width,
-               stdp_bytes_per_target(net, iv + (d_hi - d_lo)), &net->tile_w,
-               &net->lo_bits, &net->n_tiles);
+               stdp_bytes_per_target(net, iv + (d_hi - d_lo)), net->acc_words,
+               &net->tile_w, &net->lo_bits, &net->n_tiles);
   CK(dalloc(&net->tile_off, (uint64_t)n * (net->n_tiles + 1) * sizeof(uint32_t), net->stream));
   // keys; for 8-byte records the key array becomes the record array
   uint64_t* keys = nullptr;
@@ -548,6 +654,8 @@ int snn_create(const snn_params* p, void* stream, snn_net** out) {
   REQ(p->deliver_mode == SNN_DELIVER_TILED || p->deliver_mode == SNN_DELIVER_ATOMIC,
       SNN_E_ARG, "bad deliver_mode %d", p->deliver_mode);
   REQ(p->tile_width >= 0, SNN_E_ARG, "bad tile_width %d", p->tile_width);
+  REQ(p->acc_words == 0 || p->acc_words == 2, SNN_E_ARG,
+      "acc_words must be 0 (automatic) or 2, not %d", p->acc_words);
   const bool part = p->part_hi != 0 || p->part_lo != 0;
   REQ(!part || (p->part_lo < p->part_hi && p->part_hi <= n), SNN_E_ARG,
       "partition [%u, %u) outside [0, %llu)", p->part_lo, p->part_hi,
@@ -666,6 +774,13 @@ int snn_connect_fixed_indegree(snn_net* net, const snn_conn_params* c) {
     CK(e);
   }
   cudaStream_t s = net->stream;
+  {
+    WeightBounds wb;
+    if (c->k_exc) add_population(&wb, c->w_exc, c->sd_exc, c->clip_exc != 0, false, net->fmt);
+    if (c->k_inh) add_population(&wb, c->w_inh, c->sd_inh, false, c->clip_inh != 0, net->fmt);
+    decide_acc_words(net, wb, c->k_exc + c->k_inh,
+                     net->p.interval ? net->p.interval : c->d_hi);
+  }
   rc = build_store(
       net, deg,
       [&](const uint64_t* rp, uint32_t* cur, uint64_t* keys, uint32_t tw,
@@ -745,6 +860,11 @@ int snn_connect_edges(snn_net* net, const uint32_t* src, const uint32_t* tgt,
   }
   CK(cudaMemsetAsync(deg, 0, net->n * sizeof(uint32_t), s));
   CK(build_count_edges(d_src, n, deg, s));
+  {
+    WeightBounds wb;
+    for (uint64_t e = 0; e < n; ++e) wb.add_value(stored_weight(pw[e], net->fmt));
+    decide_acc_words(net, wb, k_in_max, net->p.interval ? net->p.interval : e_hi);
+  }
   rc = build_store(
       net, deg,
       [&](const uint64_t* rp, uint32_t* cur, uint64_t* keys, uint32_t tw,
@@ -1407,6 +1527,7 @@ int snn_get_stats(snn_net* net, snn_stats* out) {
   out->stdp_truncated = c.stdp_truncated;
   out->first_neuron = net->g0;
   out->n_sources = net->n_src;
+  out->acc_words = net->acc_words;
   return SNN_OK;
 }
 

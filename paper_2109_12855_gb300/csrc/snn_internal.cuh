@@ -66,20 +66,26 @@ struct SpikeEntry {
 };
 
 // Per-net control block in device memory.
+// The four counters that every update block adds to (pair, spikes,
+// log_count, pending_events) sit on separate 128-byte lines: atomics on one
+// line are serialised in its L2 slice, and hundreds of blocks reach them at
+// the same moment.
 struct Ctl {
-  unsigned long long pair;      // (spikes << 32) | chunks of the pending list
+  alignas(128) unsigned long long pair;  // (spikes << 32) | chunks of the
+                                         // pending list
   unsigned int done;            // CTAs finished in the current delivery
   unsigned int error_flags;     // SNN_ERRF_*
   unsigned long long events;    // events delivered (accumulated)
-  unsigned long long spikes;    // spikes emitted (accumulated)
-  unsigned long long log_count; // entries in the spike log
-  long long t_now;              // next step to update
+  alignas(128) unsigned long long spikes;     // spikes emitted (accumulated)
+  alignas(128) unsigned long long log_count;  // entries in the spike log
+  alignas(128) unsigned long long pending_events;  // events of the pending
+                                // list (moved to events when that list is
+                                // delivered)
+  alignas(128) long long t_now; // next step to update
   int iv_steps;                 // steps of the pending interval
   unsigned int ext_done;        // CTAs finished delivering an external list
   unsigned long long ext_pair;  // (spikes << 32) | chunks of an external list
   int ext_tmin, ext_tmax;       // emission-step range of an external list
-  unsigned long long pending_events;  // events of the pending list (moved to
-                                      // events when that list is delivered)
   unsigned long long plastic_events;  // plastic synapse updates (accumulated)
   unsigned long long stdp_truncated;  // updates whose post-spike window
                                       // reached past the kept history
@@ -222,6 +228,11 @@ struct NetView {
   uint32_t k_in_max;        // largest in-degree
   uint32_t spikes_per_iv;   // most spikes one neuron emits per interval
   float max_abs_w;          // largest |stored weight|
+  // words per accumulator cell: 2 (hi, lo), or 1 (hi only) when every
+  // stored weight is a multiple of 2^-acc_qs_min, so that a launch whose
+  // scale has q - s >= acc_qs_min has lo = 0 for every event
+  int acc_words;
+  int acc_qs_min;
   SpikeEntry* list;         // interval list, capacity list_cap
   uint64_t list_cap;
   uint32_t* log_src;        // spike log, capacity log_cap

@@ -293,16 +293,19 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
       block_scan2(cnt, cnt * nch, (unsigned long long)cnt * deg, &ex_cnt,
                   &ex_ch, &tot_cnt, &tot_ch, &tot_deg);
       if (threadIdx.x == 0) {
-        unsigned long long old =
+        // all four counters first (separate lines, both returning atomics
+        // in flight together), then the overflow check on the list's one
+        const unsigned long long old =
             atomicAdd(&v.ctl->pair, ((unsigned long long)tot_cnt << 32) | tot_ch);
-        if ((uint32_t)old + (unsigned long long)tot_ch > 0xFFFFFFFFull)
-          atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_CHUNKS);
+        const unsigned long long logb =
+            v.log_cap ? atomicAdd(&v.ctl->log_count, (unsigned long long)tot_cnt)
+                      : 0ull;
         atomicAdd(&v.ctl->pending_events, tot_deg);
         atomicAdd(&v.ctl->spikes, (unsigned long long)tot_cnt);
+        if ((uint32_t)old + (unsigned long long)tot_ch > 0xFFFFFFFFull)
+          atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_CHUNKS);
         s_base[0] = old;
-        s_base[1] = v.log_cap
-                        ? atomicAdd(&v.ctl->log_count, (unsigned long long)tot_cnt)
-                        : 0ull;
+        s_base[1] = logb;
       }
       __syncthreads();
       const unsigned long long old = s_base[0], logb = s_base[1];
@@ -664,6 +667,8 @@ __device__ FixScale fix_scale(const NetView& v, uint64_t n_sp,
   qs = min(qs, 21 - wexp);
   if (qs < 0) return f;
   qs = min(qs, 100);
+  // one-word cells hold hi only: lo must be zero for every weight
+  if (v.acc_words == 1 && qs < v.acc_qs_min) return f;
   const int q = sh + qs;
   f.fixed = 1;
   f.sh = sh;
@@ -768,6 +773,10 @@ __device__ __forceinline__ void deliver_tile_body(
   const uint32_t TW = v.tile_w;
   const uint32_t W = (uint32_t)v.window;
   const uint32_t cells = W * TW;
+  // hi and lo words per cell (FP32 stores always use two: their 24-bit
+  // significands never sit on a grid as coarse as a launch's step)
+  const bool two = FMT == SNN_W_FP32_12B || v.acc_words == 2;
+  const uint32_t acc_len = two ? 2 * cells : cells;
   const uint32_t tgt_lo = tile * TW;
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
@@ -791,12 +800,12 @@ __device__ __forceinline__ void deliver_tile_body(
     s_next = 0u;
   }
   int* accH = acc_mem;                                // fixed: hi parts
-  int* accL = acc_mem + cells;                        // fixed: lo parts
+  int* accL = acc_mem + cells;                        // fixed: lo parts (two)
   float* accF = reinterpret_cast<float*>(acc_mem);    // FP32 fallback
-  for (uint32_t x = threadIdx.x; x < 2 * cells; x += blockDim.x) acc_mem[x] = 0;
+  for (uint32_t x = threadIdx.x; x < acc_len; x += blockDim.x) acc_mem[x] = 0;
   // plastic nets: the post-spike times of this tile's targets (rings) and
   // their post traces at the W horizons (t - d) this interval can ask for
-  int32_t* s_rt = acc_mem + 2 * cells;                           // [hist][TW]
+  int32_t* s_rt = acc_mem + acc_len;                             // [hist][TW]
   uint32_t* s_rn = reinterpret_cast<uint32_t*>(s_rt + (PL ? v.sp.hist * TW : 0));
   float* s_km = reinterpret_cast<float*>(s_rn + (PL ? TW : 0));  // [W][TW]
   const bool tile_plastic = PL && tgt_lo < v.sp.n_exc;
@@ -851,8 +860,9 @@ __device__ __forceinline__ void deliver_tile_body(
         fixed_split(w, fx, hi, lo);
         atomicAdd(&accH[cell], hi);
         // BF16 weights have 8 significant bits: their scaled value is
-        // usually an integer, and a zero low part needs no addition
-        if (FMT == SNN_W_FP32_12B || lo != 0) atomicAdd(&accL[cell], lo);
+        // usually an integer, and a zero low part needs no addition (with
+        // one-word cells it is zero for every event)
+        if (two && (FMT == SNN_W_FP32_12B || lo != 0)) atomicAdd(&accL[cell], lo);
       } else {
         atomicAdd(&accF[cell], w);
       }
@@ -1026,7 +1036,8 @@ __device__ __forceinline__ void deliver_tile_body(
           if (sl0 + q < W) {
             const uint32_t c = (sl0 + q) * TW + x;
             if (fx.fixed) {
-              const long long T = ((long long)accH[c] << fx.sh) + (long long)accL[c];
+              const long long T = ((long long)accH[c] << fx.sh) +
+                                  (two ? (long long)accL[c] : 0ll);
               a[q] = (float)((double)T * fx.inv_q);
             } else {
               a[q] = accF[c];
@@ -1255,7 +1266,7 @@ cudaError_t launch_deliver(const NetView& v, unsigned long long* pair,
 size_t tiled_smem_bytes(const NetView& v) {
   // accumulator; plastic nets: spike-time rings, counts, post-trace table
   return (size_t)v.tile_w *
-         (2 * (size_t)v.window * sizeof(int) +
+         ((size_t)v.acc_words * v.window * sizeof(int) +
           (v.plastic ? (size_t)v.sp.hist * 4 + 4 + (size_t)v.window * 4 : 0));
 }
 

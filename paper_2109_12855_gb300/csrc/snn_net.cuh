@@ -48,6 +48,7 @@ struct snn_net {
   int lo_bits = 0;
   int window = 0;
   uint32_t mult_max = 0, k_in_max = 0, spikes_per_iv = 1;
+  int acc_words = 2, acc_qs_min = 0;  // accumulator cells (see NetView)
   float max_abs_w = 0.f;
   SpikeEntry* list = nullptr;
   uint64_t list_cap = 0;
@@ -104,6 +105,8 @@ struct snn_net {
     v.k_in_max = k_in_max;
     v.spikes_per_iv = spikes_per_iv;
     v.max_abs_w = max_abs_w;
+    v.acc_words = acc_words;
+    v.acc_qs_min = acc_qs_min;
     v.list = list;
     v.list_cap = list_cap;
     v.log_src = log_src;

@@ -63,7 +63,8 @@ class snn_params(C.Structure):
                 ("init_v_random", C.c_int32), ("count_events", C.c_int32),
                 ("deliver_mode", C.c_int32), ("spike_log_capacity", C.c_uint64),
                 ("tile_width", C.c_int32), ("stream_priority", C.c_int32),
-                ("part_lo", C.c_uint32), ("part_hi", C.c_uint32)]
+                ("part_lo", C.c_uint32), ("part_hi", C.c_uint32),
+                ("acc_words", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class snn_conn_params(C.Structure):
@@ -87,7 +88,8 @@ class snn_stats(C.Structure):
                 ("tile_width", C.c_uint32), ("window", C.c_int32),
                 ("deliver_mode", C.c_int32), ("plastic_events", C.c_uint64),
                 ("stdp_truncated", C.c_uint64), ("first_neuron", C.c_uint32),
-                ("n_sources", C.c_uint32)]
+                ("n_sources", C.c_uint32), ("acc_words", C.c_int32),
+                ("reserved_", C.c_int32)]
 
 
 class snn_bounds(C.Structure):

@@ -173,3 +173,67 @@ def test_update_then_deliver_pending_matches_oracle(fmt, mode):
     # values: the random ring-buffer contents plus the delivered sums
     tol = 1e-5 * absw + 1e-6 * np.abs(orb)
     assert np.all(np.abs(grb - want) <= tol)
+
+
+def test_one_word_cells_equal_two_word_cells_bit_for_bit():
+    """BF16 weights drawn as mean + sd z with |mean| > 6.7 sd are multiples of
+    a power of two that every interval's fixed-point step divides, so the
+    tiled delivery keeps one int32 per cell (tiles of up to twice the
+    targets); the same net forced to two words per cell (and so to narrower
+    tiles) gives identical ring buffers and spikes.  FP32 weights keep two."""
+    from paper_2109_12855_gb300 import snn
+    kw = dict(fmt=1, sd_e=2.24, sd_i=11.2, tile_width=2048,
+              spike_log_capacity=1 << 20, nu_ext=20000.0,
+              w_ext=O.weight_for_psp(O.Neuron(), 0.1))
+    nets = [fixed_net(3200, 800, 400, 100, 22.4, -112.0, 10, 20, seed=21,
+                      acc_words=a, **kw)[0] for a in (0, 2)]
+    try:
+        st = [net.stats() for net in nets]
+        assert st[0].acc_words == 1 and st[1].acc_words == 2
+        assert st[0].tile_width == 2048 and st[1].tile_width < 2048
+        for k, (lo, hi, cnt) in enumerate(((0, 10, 3000), (5, 6, 1))):
+            src, t = W.random_spikes(4000, cnt, lo, hi, seed=40 + k)
+            rbs = []
+            for net in nets:
+                snn.snn_clear_rb(net.h)
+                net.deliver(src, t.astype(np.int32))
+                rbs.append(net.read_rb())
+            assert np.array_equal(rbs[0].view(np.uint32), rbs[1].view(np.uint32))
+        out = []
+        for net in nets:
+            snn.snn_clear_rb(net.h)
+            snn.snn_simulate(net.h, 600)
+            s, t = net.read_spikes(1 << 20)
+            o = np.lexsort((s, t))
+            out.append((s[o], t[o], net.read_rb(), net.stats()))
+        assert out[0][3].spikes == out[1][3].spikes > 100
+        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+        assert np.array_equal(out[0][2].view(np.uint32), out[1][2].view(np.uint32))
+    finally:
+        for net in nets:
+            net.close()
+    net, _ = fixed_net(400, 100, 40, 10, 22.4, -112.0, 10, 20, seed=3, fmt=0,
+                       sd_e=2.24)
+    with net:
+        assert net.stats().acc_words == 2
+
+
+def test_one_word_cells_fall_back_to_fp32_for_huge_lists():
+    """A caller list so long that its fixed-point step would exceed the
+    weights' common power of two (here 300,000 spikes, E max|w| above 2^28
+    with weights on a 2^-3 grid) is accumulated in FP32 in the one-word
+    cells: values within FP32 summation error of the oracle, counts exact."""
+    from paper_2109_12855_gb300 import snn
+    net, cp = fixed_net(400, 100, 40, 10, 22.4, -1000.0, 10, 20, seed=5, fmt=1)
+    with net:
+        assert net.stats().acc_words == 1
+        store = O.build_fixed_indegree(cp)
+        src, t = W.random_spikes(500, 300000, 0, 8, seed=77)
+        snn.snn_clear_rb(net.h)
+        ev = net.deliver(src, t.astype(np.int32))
+        rb, cnt = net.read_rb(), net.read_counts()
+        rb_o, cnt_o, absw, ev_o = O.deliver_ref(store, S, src, t.astype(np.int64))
+        assert ev == ev_o
+        assert np.array_equal(cnt.astype(np.int64), cnt_o.astype(np.int64))
+        assert np.all(np.abs(rb.astype(np.float64) - rb_o) <= 1e-3 * absw)
+        assert net.stats().error_flags == 0
