@@ -218,6 +218,20 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
     nch = row_chunks(beg, end, v.chunk);
     deg = end - beg;
   }
+  // long-run spike statistics of this neuron, read now so that their
+  // latency overlaps the integration; written back once if it fired
+  const bool isi = PL && v.isi_spikes && live;
+  int32_t isi_last = kNoSpike;
+  uint32_t isi_spk = 0, isi_cnt = 0;
+  double isi_s1 = 0.0, isi_s2 = 0.0;
+  bool isi_dirty = false;
+  if (isi) {
+    isi_last = v.isi_last[i];
+    isi_spk = v.isi_spikes[i];
+    isi_cnt = v.isi_n[i];
+    isi_s1 = v.isi_sum[i];
+    isi_s2 = v.isi_sq[i];
+  }
   U4 rnd{0, 0, 0, 0};
   long long rnd_block = -1;
   float* const rb_i = v.rb + i;  // slot s of neuron i at rb_i[s * pitch]
@@ -336,16 +350,16 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
         }
         if (PL && v.plastic && i < v.sp.n_exc)
           stdp_on_spike(v.sp, i, (int32_t)t, v.pitch);
-        if (PL && v.isi_spikes) {
-          const int32_t tl = v.isi_last[i];
-          if (tl != kNoSpike) {
-            const double d = (double)((int32_t)t - tl);  // exact in FP64
-            v.isi_sum[i] += d;
-            v.isi_sq[i] += d * d;
-            v.isi_n[i] += 1u;
+        if (isi) {
+          if (isi_last != kNoSpike) {
+            const double d = (double)((int32_t)t - isi_last);  // exact in FP64
+            isi_s1 += d;
+            isi_s2 += d * d;
+            isi_cnt += 1u;
           }
-          v.isi_last[i] = (int32_t)t;
-          v.isi_spikes[i] += 1u;
+          isi_last = (int32_t)t;
+          isi_spk += 1u;
+          isi_dirty = true;
         }
         ++k;
       }
@@ -358,16 +372,24 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
     v.J[i] = J;
     v.refr[i] = refr;
   }
+  if (isi_dirty) {
+    v.isi_last[i] = isi_last;
+    v.isi_spikes[i] = isi_spk;
+    v.isi_n[i] = isi_cnt;
+    v.isi_sum[i] = isi_s1;
+    v.isi_sq[i] = isi_s2;
+  }
 }
 
-__global__ void __launch_bounds__(kUpdThreads)
+// (three blocks per SM: a 112,500-neuron net's 440 blocks run in one wave)
+__global__ void __launch_bounds__(kUpdThreads, 3)
 k_update(NetView v, UpdConst c, int n_steps, int from_ctl, long long t0_arg) {
   update_body<true>(v, c, n_steps, from_ctl, t0_arg, blockIdx.x);
 }
 
 // All nets of a batch in one launch: block b updates neuron block bmap[b].y
 // of net bmap[b].x, from that net's clock.
-__global__ void __launch_bounds__(kUpdThreads)
+__global__ void __launch_bounds__(kUpdThreads, 3)
 k_update_batch(const BatchNet* __restrict__ nets, const uint2* __restrict__ bmap) {
   __shared__ UpdConst s_c;
   const uint2 m = bmap[blockIdx.x];
