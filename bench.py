@@ -90,12 +90,13 @@ def stdp_config(w_e):
                 mu=STDP_MU, w0=w_e * STDP_ALPHA ** (1.0 / (1.0 - STDP_MU)),
                 w_max=100.0, history=16)
 # DRAM bytes (read + write) per synaptic event of k_deliver_tiled, summed by
-# ncu over all 667 launches of one timed step of the workload and divided by
-# that step's events (profiles/dram_k_deliver_tiled_balanced-112500-fp32.md).
+# ncu over all launches of one timed step of the workload and divided by
+# that step's events (profiles/dram_k_deliver_tiled_<workload>.md).
 # It stands for the kernel it was measured on: the entry is used only while
 # the kernel sources (comments aside) hash to the recorded prefixes.
 TRAFFIC_B_PER_EVENT = {
-    "balanced-112500-fp32": (12.549, "7fab6757283fd352", "da2deec8b483e222"),
+    "balanced-112500-fp32": (12.549, "01e219126cedd30e", "9a10c063161bcfc9"),
+    "balanced-562500-bf16": (9.177, "01e219126cedd30e", "9a10c063161bcfc9"),
 }
 # serving: a Poisson stream of independent balanced nets (BF16 records,
 # N log-uniform in [1,250, 112,500], 100 ms - 1 s each), mean rate in req/s
