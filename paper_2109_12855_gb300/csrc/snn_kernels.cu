@@ -17,6 +17,13 @@
 //             32-ary search of the prefix sums, then walks spikes and
 //             chunks.  Each lane reads its records with 16-byte loads
 //             (streaming cache hint); additions are red.global.add.f32.
+//  k_deliver_tiled  the default delivery (Section 3.2's target-ordered
+//             access, made tile-local): one CTA per tile of targets sums
+//             the interval's events for its targets in shared memory in
+//             exact fixed point, then adds them into its window of the ring
+//             buffer with plain coalesced read-modify-writes.
+//  k_update_batch, k_deliver_tiled_batch  the same for all nets of a served
+//             batch in one launch each.
 //  k_prepare_external  prefix sum of chunk counts for a caller's list.
 #include <cuda_runtime.h>
 #include <stdint.h>

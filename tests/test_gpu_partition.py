@@ -122,3 +122,14 @@ def test_partition_rejects_bad_ranges_and_features():
         assert e.value.code == snn.SNN_E_ARG
         assert snn.snn_deliver_gathered(net.h, np.array([4999], np.uint32),
                                         np.array([3], np.int32)) > 0
+
+
+def test_accumulator_word_count_parameter_is_checked():
+    """snn_params.acc_words accepts 0 (automatic) and 2 (two words) only."""
+    from paper_2109_12855_gb300 import snn
+    for bad in (1, 3, -1):
+        q = snn.snn_params.from_buffer_copy(_params(1))
+        q.acc_words = bad
+        with pytest.raises(snn.SnnError) as e:
+            snn.Net(q, stream())
+        assert e.value.code == snn.SNN_E_ARG
