@@ -388,8 +388,11 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
   }
 }
 
-// (three blocks per SM: a 112,500-neuron net's 440 blocks run in one wave)
-__global__ void __launch_bounds__(kUpdThreads, 3)
+// MINB blocks per SM: 3 leaves room for spill-free registers (a
+// 112,500-neuron net's 440 blocks run in one wave); nets that need several
+// waves anyway take 4, for more warps per SM.
+template <int MINB>
+__global__ void __launch_bounds__(kUpdThreads, MINB)
 k_update(NetView v, UpdConst c, int n_steps, int from_ctl, long long t0_arg) {
   update_body<true>(v, c, n_steps, from_ctl, t0_arg, blockIdx.x);
 }
@@ -1266,7 +1269,17 @@ cudaError_t launch_update(const NetView& v, const UpdConst& c, int n_steps,
                           int from_ctl_time, long long t0, cudaStream_t s) {
   unsigned blocks = (v.n + kUpdThreads - 1) / kUpdThreads;
   if (blocks == 0) blocks = 1;
-  k_update<<<blocks, kUpdThreads, 0, s>>>(v, c, n_steps, from_ctl_time, t0);
+  static std::atomic<int> sms{0};
+  if (sms.load(std::memory_order_relaxed) == 0) {
+    int dev = 0, m = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      sms.store(m, std::memory_order_relaxed);
+  }
+  if (blocks > 3u * (unsigned)std::max(sms.load(std::memory_order_relaxed), 1))
+    k_update<4><<<blocks, kUpdThreads, 0, s>>>(v, c, n_steps, from_ctl_time, t0);
+  else
+    k_update<3><<<blocks, kUpdThreads, 0, s>>>(v, c, n_steps, from_ctl_time, t0);
   return cudaGetLastError();
 }
 
