@@ -83,8 +83,11 @@ enum {
   SNN_ERRF_SPIKE_LOG = 1u << 1,  /* spike recording log overflowed */
   SNN_ERRF_BAD_SOURCE = 1u << 2, /* external spike with source >= N */
   SNN_ERRF_CHUNKS = 1u << 3,     /* chunk counter of one interval overflowed */
-  SNN_ERRF_TIMEOUT = 1u << 4     /* a bounded device wait gave up (delivery of
+  SNN_ERRF_TIMEOUT = 1u << 4,    /* a bounded device wait gave up (delivery of
                                     that launch is incomplete) */
+  SNN_ERRF_SCALES = 1u << 5      /* internal: an interval's exact-sum scales
+                                    were proven on the host but not found on
+                                    the device (never expected) */
 };
 
 /* Neuron model and simulation parameters (iaf_psc_alpha, resting potential

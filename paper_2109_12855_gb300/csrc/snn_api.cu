@@ -318,22 +318,6 @@ bool use_tiled(const snn_net* net) {
 // interval lists (E <= max in-degree x spikes per neuron per interval) and
 // an upper bound of max|w| give the smallest q - s any interval can get.
 
-// q - s of the kernel's fix_scale for event bound e and max|w| (-1: FP32).
-int fixed_qs_host(uint64_t e, double max_abs_w) {
-  const float mw = (float)max_abs_w;
-  if (e == 0 || e >= (1ull << 30) || !(mw > 0.f) || !(mw <= 3.0e38f)) return -1;
-  const double A = 2147483647.0 - (double)e;
-  const double B = (double)e * (double)mw;
-  int qs = ilogb(A) - ilogb(B);
-  if (B * ldexp(1.0, qs) > A) --qs;
-  uint32_t wb;
-  memcpy(&wb, &mw, 4);
-  const int wexp = (int)((wb >> 23) & 0xFFu) - 127 + ((wb & 0x7FFFFFu) ? 1 : 0);
-  qs = std::min(qs, 21 - wexp);
-  if (qs < 0) return -1;
-  return std::min(qs, 100);
-}
-
 // Exponent of the lowest set bit of a nonzero double (exact for the float
 // and bfloat16 values the store holds).
 int lowbit_exp(double v) {

@@ -278,6 +278,9 @@ int deliver_grid_size(int fmt);
 // Tile-binned delivery (see k_deliver_tiled).  from_list_range: the window
 // starts at the external list's minimum emission step (ctl->ext_tmin) rather
 // than at the interval start ctl->t_now.
+// q - s of the delivery kernel's fixed-point scales for event bound e and
+// max|w| (-1: no fixed point; the kernel sums in FP32).
+int fixed_qs_host(uint64_t e, double max_abs_w);
 cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
                                  unsigned int* done, const SpikeEntry* list,
                                  int from_list_range, int advance_time,

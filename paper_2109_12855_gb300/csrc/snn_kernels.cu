@@ -26,7 +26,9 @@
 //             batch in one launch each.
 //  k_prepare_external  prefix sum of chunk counts for a caller's list.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 #include <atomic>
@@ -784,7 +786,10 @@ __device__ __noinline__ StdpOut stdp_weight(float w, int32_t t, uint32_t d,
   return o;
 }
 
-template <int FMT, bool COUNT, bool PL>
+// FAST: an interval's own list (inside the window) whose fixed-point scales
+// the host has shown to exist for every spike count: no per-event test of
+// either.
+template <int FMT, bool COUNT, bool PL, bool FAST = false>
 __device__ __forceinline__ void deliver_tile_body(
     const NetView& v, unsigned long long* pair_p, unsigned int* done_p,
     const SpikeEntry* __restrict__ list, int from_list_range, int advance_time,
@@ -885,9 +890,9 @@ __device__ __forceinline__ void deliver_tile_body(
 
   // one event: cell = d TW + tgt + off, off = (t - base) TW - tgt_lo per run
   auto add = [&](uint32_t tgt, int32_t t, int32_t off, uint32_t d, float w) {
-    if (inwin) {
+    if (FAST || inwin) {
       const uint32_t cell = d * TW + tgt + (uint32_t)off;
-      if (fx.fixed) {
+      if (FAST || fx.fixed) {
         int hi, lo;
         fixed_split(w, fx, hi, lo);
         atomicAdd(&accH[cell], hi);
@@ -1027,6 +1032,8 @@ __device__ __forceinline__ void deliver_tile_body(
     if (threadIdx.x == 0) s_next = 0u;
     __syncthreads();
     fx = s_fx;
+    if (FAST && !fx.fixed && n_sp > 0 && j0 == 0 && threadIdx.x == 0)
+      atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_SCALES);
     // (B) each warp takes U runs at a time: all loads first, then the adds
     // (plastic nets: a fixed share per warp, the registers being spent on
     // the weight update)
@@ -1120,15 +1127,16 @@ __device__ __forceinline__ void deliver_tile_body(
   }
 }
 
-template <int FMT, bool COUNT, bool PL>
+template <int FMT, bool COUNT, bool PL, bool FAST>
 __global__ void __launch_bounds__(kTileThreads, 1)
 k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
                 const SpikeEntry* __restrict__ list, int from_list_range,
                 int advance_time, uint32_t desc_off, uint32_t desc_cap) {
   extern __shared__ __align__(16) int acc_mem[];
-  deliver_tile_body<FMT, COUNT, PL>(v, pair_p, done_p, list, from_list_range,
-                                    advance_time, blockIdx.x, acc_mem, desc_off,
-                                    desc_cap);
+  deliver_tile_body<FMT, COUNT, PL, FAST>(v, pair_p, done_p, list,
+                                          from_list_range, advance_time,
+                                          blockIdx.x, acc_mem, desc_off,
+                                          desc_cap);
 }
 
 // All nets of a batch in one launch: CTA b delivers tile bmap[b].y of net
@@ -1244,6 +1252,23 @@ int deliver_blocks_for() {
 }
 
 }  // namespace
+
+// q - s of the kernel's fix_scale for event bound e and max|w| (-1: FP32),
+// computed on the host with the same steps.
+int fixed_qs_host(uint64_t e, double max_abs_w) {
+  const float mw = (float)max_abs_w;
+  if (e == 0 || e >= (1ull << 30) || !(mw > 0.f) || !(mw <= 3.0e38f)) return -1;
+  const double A = 2147483647.0 - (double)e;
+  const double B = (double)e * (double)mw;
+  int qs = ilogb(A) - ilogb(B);
+  if (B * ldexp(1.0, qs) > A) --qs;
+  uint32_t wb;
+  memcpy(&wb, &mw, 4);
+  const int wexp = (int)((wb >> 23) & 0xFFu) - 127 + ((wb & 0x7FFFFFu) ? 1 : 0);
+  qs = std::min(qs, 21 - wexp);
+  if (qs < 0) return -1;
+  return std::min(qs, 100);
+}
 
 int deliver_grid_size(int fmt) {
   const int k = fmt == SNN_W_FP32_12B ? 0 : 1;
@@ -1363,19 +1388,19 @@ cudaError_t desc_layout(size_t used, size_t dyn_max, bool plastic,
   return cudaSuccess;
 }
 
-template <int FMT, bool COUNT, bool PL>
+template <int FMT, bool COUNT, bool PL, bool FAST = false>
 cudaError_t launch_tiled_t(const NetView& v, unsigned long long* pair,
                            unsigned int* done, const SpikeEntry* list,
                            int from_list_range, int advance_time,
                            cudaStream_t s) {
   static std::atomic<uint32_t> lim[64];
   size_t dm = 0;
-  cudaError_t e = allow_tile_smem(k_deliver_tiled<FMT, COUNT, PL>, lim, &dm);
+  cudaError_t e = allow_tile_smem(k_deliver_tiled<FMT, COUNT, PL, FAST>, lim, &dm);
   if (e != cudaSuccess) return e;
   DescLayout dl;
   e = desc_layout(tiled_smem_bytes(v), dm, PL, &dl);
   if (e != cudaSuccess) return e;
-  k_deliver_tiled<FMT, COUNT, PL><<<v.n_tiles, kTileThreads, dl.smem, s>>>(
+  k_deliver_tiled<FMT, COUNT, PL, FAST><<<v.n_tiles, kTileThreads, dl.smem, s>>>(
       v, pair, done, list, from_list_range, advance_time, dl.off, dl.cap);
   return cudaGetLastError();
 }
@@ -1392,6 +1417,18 @@ cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
                       : SNN_TILED(SNN_W_FP32_12B, false, true);
     return v.counts ? SNN_TILED(SNN_W_BF16_8B, true, true)
                     : SNN_TILED(SNN_W_BF16_8B, false, true);
+  }
+  // an interval's own list: the scales exist for every spike count when
+  // they exist for the largest (E = max in-degree x spikes per neuron)
+  if (!from_list_range && !v.counts) {
+    const int qs = fixed_qs_host(
+        (uint64_t)v.k_in_max * (v.spikes_per_iv ? v.spikes_per_iv : 1u), v.max_abs_w);
+    if (qs >= 0 && (v.acc_words == 2 || qs >= v.acc_qs_min))
+      return v.fmt == SNN_W_FP32_12B
+                 ? launch_tiled_t<SNN_W_FP32_12B, false, false, true>(
+                       v, pair, done, list, 0, advance_time, s)
+                 : launch_tiled_t<SNN_W_BF16_8B, false, false, true>(
+                       v, pair, done, list, 0, advance_time, s);
   }
   if (v.fmt == SNN_W_FP32_12B)
     return v.counts ? SNN_TILED(SNN_W_FP32_12B, true, false)

@@ -23,6 +23,7 @@ SNN_DELIVER_TILED, SNN_DELIVER_ATOMIC = 0, 1
 SNN_ERRF_SPIKE_LIST, SNN_ERRF_SPIKE_LOG, SNN_ERRF_BAD_SOURCE, SNN_ERRF_CHUNKS = \
     1, 2, 4, 8
 SNN_ERRF_TIMEOUT = 16
+SNN_ERRF_SCALES = 32
 
 EXPORTS = [
     "snn_abi_version", "snn_last_error", "snn_default_params",
