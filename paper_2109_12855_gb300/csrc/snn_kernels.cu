@@ -789,7 +789,8 @@ __device__ __noinline__ StdpOut stdp_weight(float w, int32_t t, uint32_t d,
 // FAST: an interval's own list (inside the window) whose fixed-point scales
 // the host has shown to exist for every spike count: no per-event test of
 // either.
-template <int FMT, bool COUNT, bool PL, bool FAST = false>
+// ONE: one-word cells known at compile time (BF16 stores).
+template <int FMT, bool COUNT, bool PL, bool FAST = false, bool ONE = false>
 __device__ __forceinline__ void deliver_tile_body(
     const NetView& v, unsigned long long* pair_p, unsigned int* done_p,
     const SpikeEntry* __restrict__ list, int from_list_range, int advance_time,
@@ -812,7 +813,7 @@ __device__ __forceinline__ void deliver_tile_body(
   const uint32_t cells = W * TW;
   // hi and lo words per cell (FP32 stores always use two: their 24-bit
   // significands never sit on a grid as coarse as a launch's step)
-  const bool two = FMT == SNN_W_FP32_12B || v.acc_words == 2;
+  const bool two = FMT == SNN_W_FP32_12B || (!ONE && v.acc_words == 2);
   const uint32_t acc_len = two ? 2 * cells : cells;
   const uint32_t tgt_lo = tile * TW;
   const unsigned lane = threadIdx.x & 31u;
@@ -1127,16 +1128,16 @@ __device__ __forceinline__ void deliver_tile_body(
   }
 }
 
-template <int FMT, bool COUNT, bool PL, bool FAST>
+template <int FMT, bool COUNT, bool PL, bool FAST, bool ONE>
 __global__ void __launch_bounds__(kTileThreads, 1)
 k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
                 const SpikeEntry* __restrict__ list, int from_list_range,
                 int advance_time, uint32_t desc_off, uint32_t desc_cap) {
   extern __shared__ __align__(16) int acc_mem[];
-  deliver_tile_body<FMT, COUNT, PL, FAST>(v, pair_p, done_p, list,
-                                          from_list_range, advance_time,
-                                          blockIdx.x, acc_mem, desc_off,
-                                          desc_cap);
+  deliver_tile_body<FMT, COUNT, PL, FAST, ONE>(v, pair_p, done_p, list,
+                                               from_list_range, advance_time,
+                                               blockIdx.x, acc_mem, desc_off,
+                                               desc_cap);
 }
 
 // All nets of a batch in one launch: CTA b delivers tile bmap[b].y of net
@@ -1388,19 +1389,20 @@ cudaError_t desc_layout(size_t used, size_t dyn_max, bool plastic,
   return cudaSuccess;
 }
 
-template <int FMT, bool COUNT, bool PL, bool FAST = false>
+template <int FMT, bool COUNT, bool PL, bool FAST = false, bool ONE = false>
 cudaError_t launch_tiled_t(const NetView& v, unsigned long long* pair,
                            unsigned int* done, const SpikeEntry* list,
                            int from_list_range, int advance_time,
                            cudaStream_t s) {
   static std::atomic<uint32_t> lim[64];
   size_t dm = 0;
-  cudaError_t e = allow_tile_smem(k_deliver_tiled<FMT, COUNT, PL, FAST>, lim, &dm);
+  cudaError_t e =
+      allow_tile_smem(k_deliver_tiled<FMT, COUNT, PL, FAST, ONE>, lim, &dm);
   if (e != cudaSuccess) return e;
   DescLayout dl;
   e = desc_layout(tiled_smem_bytes(v), dm, PL, &dl);
   if (e != cudaSuccess) return e;
-  k_deliver_tiled<FMT, COUNT, PL, FAST><<<v.n_tiles, kTileThreads, dl.smem, s>>>(
+  k_deliver_tiled<FMT, COUNT, PL, FAST, ONE><<<v.n_tiles, kTileThreads, dl.smem, s>>>(
       v, pair, done, list, from_list_range, advance_time, dl.off, dl.cap);
   return cudaGetLastError();
 }
@@ -1423,12 +1425,16 @@ cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
   if (!from_list_range && !v.counts) {
     const int qs = fixed_qs_host(
         (uint64_t)v.k_in_max * (v.spikes_per_iv ? v.spikes_per_iv : 1u), v.max_abs_w);
-    if (qs >= 0 && (v.acc_words == 2 || qs >= v.acc_qs_min))
-      return v.fmt == SNN_W_FP32_12B
-                 ? launch_tiled_t<SNN_W_FP32_12B, false, false, true>(
+    if (qs >= 0 && (v.acc_words == 2 || qs >= v.acc_qs_min)) {
+      if (v.fmt == SNN_W_FP32_12B)
+        return launch_tiled_t<SNN_W_FP32_12B, false, false, true>(
+            v, pair, done, list, 0, advance_time, s);
+      return v.acc_words == 1
+                 ? launch_tiled_t<SNN_W_BF16_8B, false, false, true, true>(
                        v, pair, done, list, 0, advance_time, s)
-                 : launch_tiled_t<SNN_W_BF16_8B, false, false, true>(
+                 : launch_tiled_t<SNN_W_BF16_8B, false, false, true, false>(
                        v, pair, done, list, 0, advance_time, s);
+    }
   }
   if (v.fmt == SNN_W_FP32_12B)
     return v.counts ? SNN_TILED(SNN_W_FP32_12B, true, false)
