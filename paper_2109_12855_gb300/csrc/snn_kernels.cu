@@ -1413,19 +1413,29 @@ cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
                                  cudaStream_t s) {
 #define SNN_TILED(F, C, P) \
   launch_tiled_t<F, C, P>(v, pair, done, list, from_list_range, advance_time, s)
+  // an interval's own list: the scales exist for every spike count when
+  // they exist for the largest (E = max in-degree x spikes per neuron)
+  bool interval_exact = false;
+  if (!from_list_range && !v.counts) {
+    const int qs = fixed_qs_host(
+        (uint64_t)v.k_in_max * (v.spikes_per_iv ? v.spikes_per_iv : 1u), v.max_abs_w);
+    interval_exact = qs >= 0 && (v.acc_words == 2 || qs >= v.acc_qs_min);
+  }
   if (v.plastic) {
+    if (interval_exact)
+      return v.fmt == SNN_W_FP32_12B
+                 ? launch_tiled_t<SNN_W_FP32_12B, false, true, true>(
+                       v, pair, done, list, 0, advance_time, s)
+                 : launch_tiled_t<SNN_W_BF16_8B, false, true, true>(
+                       v, pair, done, list, 0, advance_time, s);
     if (v.fmt == SNN_W_FP32_12B)
       return v.counts ? SNN_TILED(SNN_W_FP32_12B, true, true)
                       : SNN_TILED(SNN_W_FP32_12B, false, true);
     return v.counts ? SNN_TILED(SNN_W_BF16_8B, true, true)
                     : SNN_TILED(SNN_W_BF16_8B, false, true);
   }
-  // an interval's own list: the scales exist for every spike count when
-  // they exist for the largest (E = max in-degree x spikes per neuron)
-  if (!from_list_range && !v.counts) {
-    const int qs = fixed_qs_host(
-        (uint64_t)v.k_in_max * (v.spikes_per_iv ? v.spikes_per_iv : 1u), v.max_abs_w);
-    if (qs >= 0 && (v.acc_words == 2 || qs >= v.acc_qs_min)) {
+  {
+    if (interval_exact) {
       if (v.fmt == SNN_W_FP32_12B)
         return launch_tiled_t<SNN_W_FP32_12B, false, false, true>(
             v, pair, done, list, 0, advance_time, s);
