@@ -74,6 +74,11 @@ WORKLOADS = {
     "deliver-20000-fp32": (W.Balanced("balanced-20000", 16000, 4000, 9000,
                                       2250, 15, 15, "fp32", 0.0, 150.0),
                            0, 150.0, "deliver"),
+    # profiling case of the interval-list delivery: the same in-degree, runs
+    # of ~74 records per spike and tile, a 2.7 GB store, simulated
+    "balanced-20000-fp32": (W.Balanced("balanced-20000", 16000, 4000, 9000,
+                                       2250, 15, 15, "fp32", 0.0, 150.0),
+                            0, 150.0, "simulate"),
 }
 DEFAULT = "balanced-112500-fp32"
 PLASTIC = {"balanced-112500-stdp-bf16", "stdp-20000-bf16"}
