@@ -233,6 +233,7 @@ struct NetView {
   // scale has q - s >= acc_qs_min has lo = 0 for every event
   int acc_words;
   int acc_qs_min;
+  float mean_run;           // synapses per (source, tile): the mean run length
   SpikeEntry* list;         // interval list, capacity list_cap
   uint64_t list_cap;
   uint32_t* log_src;        // spike log, capacity log_cap

@@ -789,8 +789,11 @@ __device__ __noinline__ StdpOut stdp_weight(float w, int32_t t, uint32_t d,
 // FAST: an interval's own list (inside the window) whose fixed-point scales
 // the host has shown to exist for every spike count: no per-event test of
 // either.
-// ONE: one-word cells known at compile time (BF16 stores).
-template <int FMT, bool COUNT, bool PL, bool FAST = false, bool ONE = false>
+// ONE: one-word cells known at compile time (BF16 stores).  SHORT: runs of
+// a few dozen records (BF16, static): more runs per warp pass, fewer slots
+// per run.
+template <int FMT, bool COUNT, bool PL, bool FAST = false, bool ONE = false,
+          bool SHORT = false>
 __device__ __forceinline__ void deliver_tile_body(
     const NetView& v, unsigned long long* pair_p, unsigned int* done_p,
     const SpikeEntry* __restrict__ list, int from_list_range, int advance_time,
@@ -798,8 +801,8 @@ __device__ __forceinline__ void deliver_tile_body(
   // U runs per warp pass, PER records per lane of each loaded before use
   // (plastic nets also hold each record's plastic weight: fewer runs)
   constexpr int U = PL ? (FMT == SNN_W_FP32_12B ? 1 : 2)
-                       : (FMT == SNN_W_FP32_12B ? 2 : 4);
-  constexpr int PER = 3;
+                       : (FMT == SNN_W_FP32_12B ? 2 : (SHORT ? 6 : 4));
+  constexpr int PER = SHORT ? 2 : 3;
   // run descriptors of one batch (desc_cap spikes), after the accumulator
   SegDesc* const s_desc =
       reinterpret_cast<SegDesc*>(reinterpret_cast<char*>(acc_mem) + desc_off);
@@ -1128,16 +1131,15 @@ __device__ __forceinline__ void deliver_tile_body(
   }
 }
 
-template <int FMT, bool COUNT, bool PL, bool FAST, bool ONE>
+template <int FMT, bool COUNT, bool PL, bool FAST, bool ONE, bool SHORT>
 __global__ void __launch_bounds__(kTileThreads, 1)
 k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
                 const SpikeEntry* __restrict__ list, int from_list_range,
                 int advance_time, uint32_t desc_off, uint32_t desc_cap) {
   extern __shared__ __align__(16) int acc_mem[];
-  deliver_tile_body<FMT, COUNT, PL, FAST, ONE>(v, pair_p, done_p, list,
-                                               from_list_range, advance_time,
-                                               blockIdx.x, acc_mem, desc_off,
-                                               desc_cap);
+  deliver_tile_body<FMT, COUNT, PL, FAST, ONE, SHORT>(
+      v, pair_p, done_p, list, from_list_range, advance_time, blockIdx.x,
+      acc_mem, desc_off, desc_cap);
 }
 
 // All nets of a batch in one launch: CTA b delivers tile bmap[b].y of net
@@ -1389,20 +1391,22 @@ cudaError_t desc_layout(size_t used, size_t dyn_max, bool plastic,
   return cudaSuccess;
 }
 
-template <int FMT, bool COUNT, bool PL, bool FAST = false, bool ONE = false>
+template <int FMT, bool COUNT, bool PL, bool FAST = false, bool ONE = false,
+          bool SHORT = false>
 cudaError_t launch_tiled_t(const NetView& v, unsigned long long* pair,
                            unsigned int* done, const SpikeEntry* list,
                            int from_list_range, int advance_time,
                            cudaStream_t s) {
   static std::atomic<uint32_t> lim[64];
   size_t dm = 0;
-  cudaError_t e =
-      allow_tile_smem(k_deliver_tiled<FMT, COUNT, PL, FAST, ONE>, lim, &dm);
+  cudaError_t e = allow_tile_smem(k_deliver_tiled<FMT, COUNT, PL, FAST, ONE, SHORT>,
+                                  lim, &dm);
   if (e != cudaSuccess) return e;
   DescLayout dl;
   e = desc_layout(tiled_smem_bytes(v), dm, PL, &dl);
   if (e != cudaSuccess) return e;
-  k_deliver_tiled<FMT, COUNT, PL, FAST, ONE><<<v.n_tiles, kTileThreads, dl.smem, s>>>(
+  k_deliver_tiled<FMT, COUNT, PL, FAST, ONE, SHORT>
+      <<<v.n_tiles, kTileThreads, dl.smem, s>>>(
       v, pair, done, list, from_list_range, advance_time, dl.off, dl.cap);
   return cudaGetLastError();
 }
@@ -1439,11 +1443,15 @@ cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
       if (v.fmt == SNN_W_FP32_12B)
         return launch_tiled_t<SNN_W_FP32_12B, false, false, true>(
             v, pair, done, list, 0, advance_time, s);
-      return v.acc_words == 1
-                 ? launch_tiled_t<SNN_W_BF16_8B, false, false, true, true>(
-                       v, pair, done, list, 0, advance_time, s)
-                 : launch_tiled_t<SNN_W_BF16_8B, false, false, true, false>(
-                       v, pair, done, list, 0, advance_time, s);
+      if (v.acc_words == 1)
+        // runs of a few dozen records: two slots for six runs per pass
+        return v.mean_run < 48.f
+                   ? launch_tiled_t<SNN_W_BF16_8B, false, false, true, true, true>(
+                         v, pair, done, list, 0, advance_time, s)
+                   : launch_tiled_t<SNN_W_BF16_8B, false, false, true, true>(
+                         v, pair, done, list, 0, advance_time, s);
+      return launch_tiled_t<SNN_W_BF16_8B, false, false, true, false>(
+          v, pair, done, list, 0, advance_time, s);
     }
   }
   if (v.fmt == SNN_W_FP32_12B)

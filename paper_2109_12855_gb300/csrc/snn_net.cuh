@@ -107,6 +107,8 @@ struct snn_net {
     v.max_abs_w = max_abs_w;
     v.acc_words = acc_words;
     v.acc_qs_min = acc_qs_min;
+    v.mean_run = n_src && n_tiles ? (float)((double)n_syn / ((double)n_src * n_tiles))
+                                  : 0.f;
     v.list = list;
     v.list_cap = list_cap;
     v.log_src = log_src;
