@@ -312,7 +312,11 @@ int snn_deliver(snn_net* net, const uint32_t* src, const int32_t* t_emit,
  *  - src, t_emit: n_spikes entries in DEVICE memory (no host staging).
  *  - n_spikes > SNN_NOALLOC_MAX_SPIKES is rejected with SNN_E_ARG.
  *  - The first call on a device looks up the scratch's device address; make
- *    that first call before any stream capture.
+ *    that first call before any stream capture.  The address is kept for
+ *    the life of the process: after cudaDeviceReset on that device the entry
+ *    point must not be called again in the same process.
+ *  - src and t_emit must be device (or managed) memory of the net's device;
+ *    anything else is refused with SNN_E_ARG before any work is queued.
  *  - All calls share the scratch: calls whose GPU work overlaps (different
  *    streams, or other host threads) race and must be serialised by the
  *    caller.  Counters that must start at zero are cleared by every call.

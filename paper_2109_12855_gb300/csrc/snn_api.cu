@@ -1141,6 +1141,21 @@ int snn_deliver_noalloc(snn_net* net, const uint32_t* src,
     if (n_events_out) *n_events_out = 0;
     return SNN_OK;
   }
+  // the kernels read the lists directly: a host pointer would fault on the
+  // device, so only device (or managed) memory of the net's device passes
+  // (cudaPointerGetAttributes allocates nothing)
+  const void* lists[2] = {src, t_emit};
+  for (int k = 0; k < 2; ++k) {
+    cudaPointerAttributes pa;
+    const cudaError_t pe = cudaPointerGetAttributes(&pa, lists[k]);
+    if (pe != cudaSuccess) cudaGetLastError();  // not left for later checks
+    REQ(pe == cudaSuccess, SNN_E_ARG, "%s: not a CUDA pointer (%s)",
+        k ? "t_emit" : "src", cudaGetErrorString(pe));
+    REQ((pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) &&
+            pa.device == net->device,
+        SNN_E_ARG, "%s must be device memory of the net's device",
+        k ? "t_emit" : "src");
+  }
   unsigned long long ev0 = 0, ev1 = 0;
   if (n_events_out) {
     CK(cudaMemcpyAsync(&ev0, &net->ctl->events, 8, cudaMemcpyDeviceToHost, s));

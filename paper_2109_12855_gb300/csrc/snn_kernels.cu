@@ -556,6 +556,7 @@ k_deliver(NetView v, unsigned long long* pair_p, unsigned int* done_p,
   // (every CTA read them before arriving here) and advances the clock.
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     unsigned prev = atomicAdd(done_p, 1u);
     if (prev == gridDim.x - 1) {
       *pair_p = 0ull;

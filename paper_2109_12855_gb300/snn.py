@@ -297,6 +297,8 @@ def snn_deliver(net, src, t_emit, want_events: bool = True):
     return ev.value if want_events else None
 
 
+# the scratch capacity, SNN_NOALLOC_MAX_SPIKES of include/snn.h (a test
+# checks that the two agree)
 SNN_NOALLOC_MAX_SPIKES = 1 << 18
 
 
@@ -304,7 +306,9 @@ def snn_deliver_noalloc(net, src, t_emit, want_events: bool = True):
     """Allocation-free delivery; src/t_emit must be CUDA tensors."""
     ps, ms = _buf(src)
     pt, mt = _buf(t_emit)
-    assert ms == mt == SNN_MEM_DEVICE, "spike arrays must be device memory"
+    if not (ms == mt == SNN_MEM_DEVICE):
+        raise ValueError("snn_deliver_noalloc: spike arrays must be device "
+                         "memory (CUDA tensors)")
     ev = C.c_uint64()
     _check(lib().snn_deliver_noalloc(net, ps, pt, len(src),
                                      C.byref(ev) if want_events else None))

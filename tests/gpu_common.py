@@ -25,8 +25,8 @@ def fixed_net(n_e, n_i, k_e, k_i, w_e, w_i, d_lo, d_hi, seed, fmt=0,
               sd_e=0.0, sd_i=0.0, **pkw):
     """GPU net + matching oracle connection rule (weights rounded as stored)."""
     from paper_2109_12855_gb300 import snn
-    p = snn.params(n_exc=n_e, n_inh=n_i, weight_format=fmt, count_events=1,
-                   **pkw)
+    pkw.setdefault("count_events", 1)
+    p = snn.params(n_exc=n_e, n_inh=n_i, weight_format=fmt, **pkw)
     net = snn.Net(p, stream())
     net.connect_fixed_indegree(snn.conn_params(
         k_exc=k_e, k_inh=k_i, w_exc=w_e, w_inh=w_i, sd_exc=sd_e, sd_inh=sd_i,

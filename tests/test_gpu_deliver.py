@@ -175,6 +175,61 @@ def test_update_then_deliver_pending_matches_oracle(fmt, mode):
     assert np.all(np.abs(grb - want) <= tol)
 
 
+@pytest.mark.parametrize("fmt,kw", [
+    (0, {}),                                  # FP32, two-word cells
+    (1, {}),                                  # BF16 one-word, runs < 48
+    (1, {"tile_width": 2048}),                # BF16 one-word, runs >= 48
+    (1, {"acc_words": 2}),                    # BF16 two-word cells
+], ids=["fp32", "bf16-short-runs", "bf16-long-runs", "bf16-two-words"])
+def test_interval_list_kernels_without_counting_match_oracle(fmt, kw):
+    """With event counting off an interval's own list takes the kernels that
+    skip the per-event window and fixed-point tests (their scales are proven
+    on the host): the FP32 two-word form, and for BF16 one-word cells the
+    short-run shape (mean run under 48 records) or the long-run shape (wide
+    tiles), or two-word cells.  Ring buffer vs Algorithm REF on the oracle's
+    own update of the same state, within 1e-5 of the summed |w| per cell."""
+    from paper_2109_12855_gb300 import snn
+    n = 5000
+    net, cp = fixed_net(4000, 1000, 400, 100, 22.4, -112.0, 10, 20, seed=33,
+                        fmt=fmt, init_v_random=0, count_events=0,
+                        spike_log_capacity=1 << 20, **kw)
+    store = O.build_fixed_indegree(cp)
+    V, I, J, refr = W.random_state(n, seed=91 + fmt)
+    V[::5] = 100.0                       # these fire at the first step
+    with net:
+        st_net = net.stats()
+        if fmt == 1:
+            assert st_net.acc_words == kw.get("acc_words", 1)
+        if "tile_width" in kw:
+            assert st_net.tile_width == kw["tile_width"]
+        # mean run length per (spike, tile): out-degree 500 over the tiles
+        mean_run = 500.0 / st_net.n_tiles
+        if fmt == 1 and "acc_words" not in kw:
+            assert (mean_run >= 48.0) == ("tile_width" in kw), mean_run
+        V32, I32, J32 = (x.astype(np.float32) for x in (V, I, J))
+        net.write_state(V32, I32, J32, refr)
+        t0 = 777
+        snn.snn_update(net.h, t0, 10)
+        gsrc, gt = net.read_spikes()
+        snn.snn_deliver_pending(net.h)
+        grb = net.read_rb().astype(np.float64)
+        st = net.stats()
+        assert st.t_now == t0 + 10 and st.error_flags == 0
+    ost = O.State(V32.astype(np.float64), I32.astype(np.float64),
+                  J32.astype(np.float64), refr.copy())
+    orb = np.zeros((S, n))
+    osrc, ot = O.update(O.Neuron(), ost, orb, t0, 10, 0.0, 0.0, 1)
+    assert len(osrc) >= 1000
+    assert sorted(zip(gsrc.tolist(), gt.tolist())) == \
+        sorted(zip(osrc.tolist(), ot.tolist()))
+    rb_del, cnt, absw, ev = O.deliver_ref(store, S, osrc, ot)
+    assert st.events_delivered == ev
+    err = np.abs(grb - rb_del)
+    assert np.all(err <= 1e-5 * absw), float((err - 1e-5 * absw).max())
+    # exactly the cells that received events are non-zero (or cancel to 0)
+    assert not grb[cnt == 0].any()
+
+
 def test_one_word_cells_equal_two_word_cells_bit_for_bit():
     """BF16 weights drawn as mean + sd z with |mean| > 6.7 sd are multiples of
     a power of two that every interval's fixed-point step divides, so the

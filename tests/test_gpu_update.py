@@ -29,8 +29,12 @@ def _bare_net(n, **kw):
 
 
 def test_closed_form_psp_on_the_gpu():
-    """One input of w at step 3: V at step 3 + n equals w psp(n h) (pin 1 of
-    the exact integration, on the device in FP32)."""
+    """One input of w at step 3: V at step 3 + n equals w psp(n h) within
+    1e-6 of the PSP peak (the closed-form pin of the exact integration, on
+    the device in FP32).  Bound: the float32 rounding of the propagator
+    entries alone moves V by at most 3.3e-7 of the peak over these 400 steps,
+    and float32 arithmetic (with or without fused multiply-adds) by a similar
+    amount."""
     from paper_2109_12855_gb300 import snn
     w, t_kick = 37.5, 3
     with _bare_net(1, v_th=1e9) as net:
@@ -44,7 +48,7 @@ def test_closed_form_psp_on_the_gpu():
             V.append(net.read_state()[0][0])
         for k in range(1, 399):
             want = w * O.psp_unit(NM, k * NM.h)
-            assert abs(V[t_kick + k] - want) <= 2e-6 * peak, k
+            assert abs(V[t_kick + k] - want) <= 1e-6 * peak, k
 
 
 @pytest.mark.parametrize("nu", [8000.0, 30000.0, 120000.0])
