@@ -10,7 +10,7 @@ time (10,000 grid steps = 667 update/deliver intervals) of the whole hot path:
 fused update with spike compaction, then delivery, every interval.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-    python bench.py --impl reference      # the FP64 oracle on the host cores
+    python bench.py --impl reference      # the FP64 oracle on all host cores
 
 Under torchrun (N > 1) every rank simulates its own independent network
 (replicas: the workload does not exchange data between GPUs); the reported
@@ -257,6 +257,133 @@ def oracle_step(ctx, wl, nu_ext, n_intervals, seed=1):
     return events, secs
 
 
+def host_info():
+    """Host facts for the CPU baseline: hardware threads, CPU model, memory."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True,
+                                 timeout=10).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    mem = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    return {"nproc": os.cpu_count(), "cpu": model, "mem_gb": round(mem / 1e9, 1)}
+
+
+def mem_available():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+
+
+def oracle_threaded(wl, nu_ext, threads, n_targets, seed=1, n_lists=50):
+    """The oracle's thread-parallel form on all host threads (each owns a
+    range of neurons and the segments onto them, Section 2.1).  The whole
+    network when its FP64 store (16 B per synapse, twice that while it is
+    built) fits in 60 % of the available host memory; otherwise the targets
+    [0, threads x n_targets) with Bernoulli lists of all sources, as in the
+    single-thread sample."""
+    import oracle as O
+    nm = O.Neuron()
+    w_e = O.weight_for_psp(nm, wl.psp_mv)
+    cp = O.Conn(wl.n_e, wl.n_i, wl.k_e, wl.k_i, w_e, -wl.g * w_e, wl.d_lo,
+                wl.d_hi, seed + 1000, sd_e=wl.sd_rel * w_e,
+                sd_i=wl.sd_rel * wl.g * w_e,
+                wfmt=1 if wl.weight_format == "fp32" else 2)
+    whole = 32 * wl.n_synapses <= 0.6 * mem_available()
+    hi = wl.n if whole else min(wl.n, threads * n_targets)
+    mt = O.Threaded(cp, threads, tgt_hi=hi)
+    st = O.State(O.init_v(nm, wl.n, seed), np.zeros(wl.n), np.zeros(wl.n),
+                 np.zeros(wl.n, np.int32))
+    ctx = {"O": O, "nm": nm, "w_e": w_e, "mt": mt, "state": st,
+           "rb": np.zeros((32, wl.n)), "t": 0, "whole": whole, "hi": hi,
+           "threads": mt.n_threads}
+    if not whole:
+        ctx["lists"] = [W.bernoulli_spikes(wl.n, 0, wl.d_lo, 8.0, 0.1,
+                                           seed=100 + k) for k in range(n_lists)]
+    return ctx
+
+
+def oracle_threaded_step(ctx, wl, nu_ext, bio_ms, seed=1):
+    """bio_ms of biological time: the whole network's time-driven cycle, or
+    per interval the sampled neurons' update and the delivery of one list of
+    all sources onto them.  Returns (events, seconds, spikes)."""
+    D = wl.d_lo
+    n_steps = int(round(bio_ms / 0.1))
+    mt, st, rb = ctx["mt"], ctx["state"], ctx["rb"]
+    if ctx["whole"]:
+        cap = wl.n * (n_steps // 21 + 2)   # one spike per refractory period
+        a = time.perf_counter()
+        src, _, ev = mt.simulate(ctx["nm"], D, st, rb, ctx["t"], n_steps, nu_ext,
+                                 ctx["w_e"], seed, cap=cap)
+        secs = time.perf_counter() - a
+        ctx["t"] += n_steps
+        return ev, secs, len(src)
+    events, secs = 0, 0.0
+    for _ in range(max(1, n_steps // D)):
+        t = ctx["t"]
+        src, tt = ctx["lists"][(t // D) % len(ctx["lists"])]
+        a = time.perf_counter()
+        mt.update(ctx["nm"], st, rb, t, D, nu_ext, ctx["w_e"], seed)
+        _, ev = mt.deliver(src, tt + t, rb)
+        secs += time.perf_counter() - a
+        events += ev
+        ctx["t"] = t + D
+    return events, secs, 0
+
+
+def threaded_text(ctx, wl, bio_ms):
+    if ctx["whole"]:
+        return (f"the whole {wl.name} network ({wl.n_synapses:,} synapses, FP64 "
+                f"store on the host), {bio_ms:g} ms of biological time per "
+                f"step from the initial state: the oracle's time-driven cycle "
+                f"on {ctx['threads']} host threads, each owning a range of "
+                f"neurons and the segments onto them (NEST's thread model)")
+    return (f"targets [0, {ctx['hi']:,}) of {wl.name} "
+            f"({ctx['hi'] * wl.k:,} synapses) on {ctx['threads']} host threads "
+            f"(each owning a range of them): per {wl.d_lo}-step interval the "
+            f"oracle update of those neurons + Algorithm REF delivery of an "
+            f"8 Hz Bernoulli spike list of all {wl.n:,} sources, "
+            f"{bio_ms:g} ms of biological time per step")
+
+
+def cpu_baseline_all_cores(args, wl, nu_ext):
+    """All-cores oracle figures for cpu_baseline: events/s, the real-time
+    factor (measured on the whole network, or extrapolated from the sample
+    by N / sampled neurons), and the host."""
+    threads = args.oracle_threads or os.cpu_count() or 1
+    ctx = oracle_threaded(wl, nu_ext, threads, args.oracle_targets)
+    try:
+        oracle_threaded_step(ctx, wl, nu_ext, 10.0)            # warm-up
+        ev, secs, _ = oracle_threaded_step(ctx, wl, nu_ext, args.oracle_bio_ms)
+    finally:
+        ctx["mt"].close()
+    rtf = secs / (args.oracle_bio_ms * 1e-3)
+    out = {"value": ev / secs, "unit": UNIT, "cores": ctx["threads"],
+           "kind": "oracle", "seconds": secs,
+           "sample": threaded_text(ctx, wl, args.oracle_bio_ms),
+           "real_time_factor": rtf if ctx["whole"] else rtf * wl.n / ctx["hi"],
+           "real_time_factor_kind": "measured on the whole network"
+           if ctx["whole"] else
+           f"extrapolated: sample wall time x {wl.n:,} / {ctx['hi']:,} neurons"}
+    return out
+
+
 def sample_text(wl, n_targets, n_intervals, plastic=False):
     how = ("plastic delivery (STDP of the E->E synapses against the full "
            "spike history)" if plastic else "Algorithm REF delivery")
@@ -268,32 +395,52 @@ def sample_text(wl, n_targets, n_intervals, plastic=False):
 
 
 def run_reference(args, wl, nu_ext):
-    """--impl reference: the oracle as it stands, on the host cores."""
+    """--impl reference: the oracle as it stands, on all host cores (its
+    thread-parallel form); each step a bounded sample of the workload."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    n_targets = args.oracle_targets
     plastic = args.workload in PLASTIC
-    ctx = oracle_sample(wl, nu_ext, n_targets, plastic=plastic)
-    per_step = args.oracle_intervals if not plastic else min(
-        args.oracle_intervals, 20)
-    for _ in range(args.warmup):
-        oracle_step(ctx, wl, nu_ext, per_step)
-    ev, secs = 0, 0.0
-    for _ in range(args.steps):
-        e, s_ = oracle_step(ctx, wl, nu_ext, per_step)
-        ev += e
-        secs += s_
+    if plastic:
+        # the plastic oracle has no thread-parallel form: one core
+        n_targets = args.oracle_targets
+        ctx = oracle_sample(wl, nu_ext, n_targets, plastic=True)
+        per_step = min(args.oracle_intervals, 20)
+        for _ in range(args.warmup):
+            oracle_step(ctx, wl, nu_ext, per_step)
+        ev, secs = 0, 0.0
+        for _ in range(args.steps):
+            e, s_ = oracle_step(ctx, wl, nu_ext, per_step)
+            ev += e
+            secs += s_
+        cores = 1
+        sample = sample_text(wl, n_targets, per_step, True) + " per step"
+    else:
+        threads = args.oracle_threads or os.cpu_count() or 1
+        ctx = oracle_threaded(wl, nu_ext, threads, args.oracle_targets)
+        try:
+            for _ in range(args.warmup):
+                oracle_threaded_step(ctx, wl, nu_ext, args.oracle_bio_ms)
+            ev, secs = 0, 0.0
+            for _ in range(args.steps):
+                e, s_, _ = oracle_threaded_step(ctx, wl, nu_ext,
+                                                args.oracle_bio_ms)
+                ev += e
+                secs += s_
+        finally:
+            ctx["mt"].close()
+        cores = ctx["threads"]
+        sample = threaded_text(ctx, wl, args.oracle_bio_ms)
     value = ev / secs
-    sample = sample_text(wl, n_targets, per_step, plastic) + " per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": args.workload},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1,
-                             "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": sample,
+                             "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -505,7 +652,7 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
             counts["spikes"] += snn.snn_read_spikes(h, hsrc, ht)  # d2h
             snn.snn_read_state(h, hV, hI, hJ, hR)            # d2h
 
-        k_e2e = max(1, min(args.steps, 3))
+        k_e2e = max(1, args.steps)
         a = net.stats()
         ms_e2e = timed(torch, s, e2e_step, k_e2e)
         b = net.stats()
@@ -527,9 +674,16 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
         n_iv = args.cpu_intervals if not plastic else min(args.cpu_intervals, 150)
         oracle_step(ctx, wl, nu_ext, 5)
         e_c, s_c = oracle_step(ctx, wl, nu_ext, n_iv)
-        cpu = {"value": e_c / s_c, "unit": UNIT, "cores": 1, "kind": "oracle",
+        one = {"value": e_c / s_c, "unit": UNIT, "cores": 1, "kind": "oracle",
                "seconds": s_c,
                "sample": sample_text(wl, args.oracle_targets, n_iv, plastic)}
+        del ctx
+        if plastic:   # the plastic oracle has no thread-parallel form
+            cpu = dict(one, host=host_info())
+        else:
+            cpu = cpu_baseline_all_cores(args, wl, nu_ext)
+            cpu["single_core"] = one
+            cpu["host"] = host_info()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
@@ -949,6 +1103,10 @@ def main():
                     help="oracle intervals per --impl reference step")
     ap.add_argument("--cpu-intervals", type=int, default=1500,
                     help="oracle intervals timed for cpu_baseline")
+    ap.add_argument("--oracle-threads", type=int, default=0,
+                    help="host threads of the all-cores oracle (0: all)")
+    ap.add_argument("--oracle-bio-ms", type=float, default=100.0,
+                    help="biological ms per all-cores oracle step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deliver-mode", choices=["tiled", "atomic"],
                     default="tiled")

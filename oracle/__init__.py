@@ -16,6 +16,9 @@ names the passage of the paper it follows:
 * ``update`` / ``simulate``  -- Section 1 and Section 2.1 (time-driven
   cycle: update for one min-delay interval, then deliver; exact
   integration of the linear subthreshold dynamics).
+* ``Threaded``               -- Section 2.1 (the thread model: each thread
+  owns a range of neurons and the segments onto them); bitwise the results
+  of ``simulate`` / ``deliver_ref``, on all host cores.
 * ``deliver_stdp`` / ``simulate_stdp`` -- Section 6 (plasticity as an update
   scheme driven by presynaptic spikes, weights computed at delivery; the
   cited pair-based power-law rule), with the readings stated in the C source.
@@ -47,7 +50,8 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fno-fast-math",
-           "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+           "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm",
+           "-pthread"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -136,6 +140,30 @@ def _declare(lib):
                                  C.c_int64, C.c_double, C.c_double, C.c_uint64,
                                  _P, _P, C.c_uint64, C.POINTER(C.c_uint64)]
     lib.orc_simulate.restype = C.c_uint64
+    lib.orc_update_range.argtypes = [C.POINTER(NeuronC), C.c_uint32,
+                                     C.c_uint32, C.c_uint32, C.c_int32, _P, _P,
+                                     _P, _P, _P, C.c_int64, C.c_int32,
+                                     C.c_double, C.c_double, C.c_uint64, _P,
+                                     _P, C.c_uint64]
+    lib.orc_update_range.restype = C.c_uint64
+    lib.orc_mt_create.argtypes = [C.POINTER(ConnC), C.c_int, C.c_int32,
+                                  C.c_uint32, C.c_uint32]
+    lib.orc_mt_create.restype = C.c_void_p
+    lib.orc_mt_destroy.argtypes = [C.c_void_p]
+    lib.orc_mt_threads.argtypes = [C.c_void_p]
+    lib.orc_mt_threads.restype = C.c_int
+    lib.orc_mt_range.argtypes = [C.c_void_p, C.c_int, _P, _P]
+    lib.orc_mt_simulate.argtypes = [C.c_void_p, C.POINTER(NeuronC), C.c_int32,
+                                    _P, _P, _P, _P, _P, C.c_int64, C.c_int64,
+                                    C.c_double, C.c_double, C.c_uint64, _P, _P,
+                                    C.c_uint64, C.POINTER(C.c_uint64)]
+    lib.orc_mt_simulate.restype = C.c_uint64
+    lib.orc_mt_deliver.argtypes = [C.c_void_p, C.c_uint64, _P, _P, _P]
+    lib.orc_mt_deliver.restype = C.c_uint64
+    lib.orc_mt_update.argtypes = [C.c_void_p, C.POINTER(NeuronC), _P, _P, _P,
+                                  _P, _P, C.c_int64, C.c_int32, C.c_double,
+                                  C.c_double, C.c_uint64]
+    lib.orc_mt_update.restype = C.c_uint64
     _declare_stdp(lib)
 
 
@@ -442,6 +470,93 @@ def simulate(nm: Neuron, store: Store, n_slots: int, interval: int, st: State,
                               C.byref(ev))
     ns = min(int(ns), cap)
     return src[:ns].copy(), tt[:ns].copy(), int(ev.value)
+
+
+class Threaded:
+    """The fixed in-degree network on ``n_threads`` host threads (NEST's
+    thread model, Section 2.1): the threads split the neurons
+    [tgt_lo, tgt_hi) (default: all N) evenly in order and each holds the
+    segments of all sources onto its own neurons.  ``simulate`` (whole
+    population only) and ``deliver`` return bitwise what ``simulate`` /
+    ``deliver_ref`` return on the full store; ``update`` runs the owned
+    neurons.  Close it (or use ``with``) to free the stores."""
+
+    def __init__(self, cp: Conn, n_threads: int, n_slots: int = 32,
+                 tgt_lo: int = 0, tgt_hi: int | None = None):
+        self.n = cp.n_e + cp.n_i
+        self.n_slots = n_slots
+        hi = self.n if tgt_hi is None else tgt_hi
+        self._cp = cp.c()          # kept alive: the C side holds a pointer
+        self._h = _load().orc_mt_create(C.byref(self._cp), n_threads, n_slots,
+                                        tgt_lo, hi)
+        if not self._h:
+            raise MemoryError("oracle: per-thread stores do not fit")
+        self.n_threads = _load().orc_mt_threads(self._h)
+
+    def ranges(self):
+        out = []
+        for k in range(self.n_threads):
+            lo, hi = np.zeros(1, np.uint32), np.zeros(1, np.uint32)
+            _load().orc_mt_range(self._h, k, _ptr(lo), _ptr(hi))
+            out.append((int(lo[0]), int(hi[0])))
+        return out
+
+    def simulate(self, nm: Neuron, interval: int, st: State, rb: np.ndarray,
+                 t0: int, n_steps: int, nu_ext_hz: float, w_ext: float,
+                 seed: int, cap: int = 1 << 24):
+        """Like ``simulate`` (in place on ``st`` and ``rb``); the threads
+        must own the whole population."""
+        rg = self.ranges()
+        if rg[0][0] != 0 or rg[-1][1] != self.n:
+            raise ValueError("a closed-network run needs every neuron")
+        assert rb.shape == (self.n_slots, self.n) and rb.dtype == np.float64
+        src = np.zeros(cap, np.uint32)
+        tt = np.zeros(cap, np.int64)
+        ev = C.c_uint64()
+        ns = _load().orc_mt_simulate(self._h, C.byref(nm.c()), interval,
+                                     _ptr(st.V), _ptr(st.I), _ptr(st.J),
+                                     _ptr(st.refr), _ptr(rb), t0, n_steps,
+                                     nu_ext_hz, w_ext, seed, _ptr(src),
+                                     _ptr(tt), cap, C.byref(ev))
+        if ns == 2 ** 64 - 1:
+            raise MemoryError("oracle: interval lists do not fit")
+        ns = min(int(ns), cap)
+        return src[:ns].copy(), tt[:ns].copy(), int(ev.value)
+
+    def update(self, nm: Neuron, st: State, rb: np.ndarray, t0: int,
+               n_steps: int, nu_ext_hz: float, w_ext: float, seed: int) -> int:
+        """The owned neurons' update (arrays indexed globally, in place);
+        returns the number of spikes (not kept)."""
+        assert rb.shape == (self.n_slots, self.n) and len(st.V) == self.n
+        return int(_load().orc_mt_update(
+            self._h, C.byref(nm.c()), _ptr(st.V), _ptr(st.I), _ptr(st.J),
+            _ptr(st.refr), _ptr(rb), t0, n_steps, nu_ext_hz, w_ext, seed))
+
+    def deliver(self, src, t, rb=None):
+        """Algorithm REF of one list onto all targets; returns (rb, events)."""
+        src, t = _spikes(src, t)
+        if rb is None:
+            rb = np.zeros((self.n_slots, self.n))
+        ev = _load().orc_mt_deliver(self._h, len(src), _ptr(src), _ptr(t),
+                                    _ptr(rb))
+        return rb, int(ev)
+
+    def close(self):
+        if self._h:
+            _load().orc_mt_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # --------------------------------------------------------------------------

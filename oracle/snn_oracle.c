@@ -608,11 +608,15 @@ uint64_t orc_deliver_bwts(const orc_store* st, uint64_t n_sp,
 /* Spikes are written in step-major, neuron-minor order.  Returns the number */
 /* of spikes (which may exceed cap; only cap are stored).                   */
 /* ------------------------------------------------------------------------ */
-uint64_t orc_update(const orc_neuron* nm, uint32_t n, int32_t n_slots,
-                    double* V, double* I, double* J, int32_t* refr, double* rb,
-                    int64_t t0, int32_t n_steps, double nu_ext_hz, double w_ext,
-                    uint64_t seed, uint32_t* sp_src, int64_t* sp_t,
-                    uint64_t cap) {
+/* The same update for the neurons [lo, hi) of a population of n (state and
+ * ring-buffer arrays indexed globally; the drive is keyed by the global
+ * index): a thread that owns those neurons runs exactly these steps. */
+uint64_t orc_update_range(const orc_neuron* nm, uint32_t lo, uint32_t hi,
+                          uint32_t n, int32_t n_slots, double* V, double* I,
+                          double* J, int32_t* refr, double* rb, int64_t t0,
+                          int32_t n_steps, double nu_ext_hz, double w_ext,
+                          uint64_t seed, uint32_t* sp_src, int64_t* sp_t,
+                          uint64_t cap) {
   double P[6];
   orc_propagators(nm, P);
   double psc = M_E / nm->tau_syn;
@@ -623,7 +627,7 @@ uint64_t orc_update(const orc_neuron* nm, uint32_t n, int32_t n_slots,
   for (int32_t s = 0; s < n_steps; ++s) {
     int64_t t = t0 + s;
     size_t row = (size_t)orc_slot(t, n_slots) * n;
-    for (uint32_t i = 0; i < n; ++i) {
+    for (uint32_t i = lo; i < hi; ++i) {
       if (refr[i] == 0)
         V[i] = P[3] * J[i] + P[4] * I[i] + P[5] * V[i];
       else
@@ -644,6 +648,15 @@ uint64_t orc_update(const orc_neuron* nm, uint32_t n, int32_t n_slots,
     }
   }
   return ns;
+}
+
+uint64_t orc_update(const orc_neuron* nm, uint32_t n, int32_t n_slots,
+                    double* V, double* I, double* J, int32_t* refr, double* rb,
+                    int64_t t0, int32_t n_steps, double nu_ext_hz, double w_ext,
+                    uint64_t seed, uint32_t* sp_src, int64_t* sp_t,
+                    uint64_t cap) {
+  return orc_update_range(nm, 0, n, n, n_slots, V, I, J, refr, rb, t0, n_steps,
+                          nu_ext_hz, w_ext, seed, sp_src, sp_t, cap);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -777,4 +790,289 @@ uint64_t orc_deliver_stdp(const orc_store* st, double* w, const orc_stdp* p,
     }
   }
   return events;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Thread-parallel form (Section 2.1: NEST's thread model).  Every thread    */
+/* owns a contiguous range of neurons and holds the target segments of all  */
+/* sources restricted to its targets (synapses live with their target).     */
+/* Per interval each thread updates its own neurons; the threads' spikes    */
+/* are merged into one list in step-major, neuron-minor order (the order of */
+/* orc_update over the whole population); each thread then walks the whole  */
+/* list with Algorithm REF onto its own targets.  A ring-buffer cell is     */
+/* written by one thread only, and its additions come in the same order as  */
+/* in orc_simulate (spikes in list order, synapses in segment order), so    */
+/* the results are bitwise those of the single-thread form.  Used for      */
+/* timing on all host cores and for whole-network runs of large nets.       */
+/* ------------------------------------------------------------------------ */
+#include <pthread.h>
+
+typedef struct {
+  uint32_t lo, hi;   /* owned neurons */
+  uint64_t m;        /* synapses onto them */
+  uint64_t* row_ptr; /* [N+1] */
+  uint32_t* tgt;
+  int32_t* delay;
+  double* w;
+  /* per-interval scratch */
+  uint32_t* sp_src;
+  int64_t* sp_t;
+  uint64_t n_sp, events;
+} orc_part;
+
+typedef struct orc_mt {
+  uint32_t n;
+  int32_t n_slots;
+  int n_threads;
+  orc_part* part;
+  /* merged interval list */
+  uint32_t* m_src;
+  int64_t* m_t;
+  uint64_t m_n;
+  pthread_barrier_t bar;
+  /* the job of the current call */
+  int job; /* 0 build, 1 simulate, 2 deliver, 3 update */
+  const orc_conn* cp;
+  const orc_neuron* nm;
+  int32_t interval;
+  double *V, *I, *J, *rb;
+  int32_t* refr;
+  int64_t t0, n_steps;
+  double nu, w_ext;
+  uint64_t seed;
+  uint32_t* out_src;
+  int64_t* out_t;
+  uint64_t cap, total;
+  const uint32_t* d_src;
+  const int64_t* d_t;
+  int status;
+} orc_mt;
+
+typedef struct {
+  orc_mt* mt;
+  int k;
+} orc_mt_arg;
+
+static void orc_mt_free_part(orc_part* p) {
+  free(p->row_ptr); free(p->tgt); free(p->delay); free(p->w);
+  free(p->sp_src); free(p->sp_t);
+  memset(p, 0, sizeof(*p));
+}
+
+/* Thread k's share of one call. */
+static void* orc_mt_worker(void* a) {
+  orc_mt* mt = ((orc_mt_arg*)a)->mt;
+  const int k = ((orc_mt_arg*)a)->k;
+  orc_part* p = &mt->part[k];
+  const orc_store st = {mt->n, mt->n_slots, p->row_ptr, p->tgt, p->delay, p->w};
+  if (mt->job == 0) { /* the segments of the owned targets */
+    const uint32_t kk = mt->cp->k_e + mt->cp->k_i;
+    p->m = (uint64_t)(p->hi - p->lo) * kk;
+    p->row_ptr = malloc(((size_t)mt->n + 1) * sizeof(uint64_t));
+    p->tgt = malloc(p->m * sizeof(uint32_t) + 1);
+    p->delay = malloc(p->m * sizeof(int32_t) + 1);
+    p->w = malloc(p->m * sizeof(double) + 1);
+    if (!p->row_ptr || !p->tgt || !p->delay || !p->w ||
+        orc_build_fixed_indegree_targets(mt->cp, p->lo, p->hi, p->row_ptr,
+                                         p->tgt, p->delay, p->w) != 0)
+      p->events = 1; /* failure flag of the build */
+    return NULL;
+  }
+  if (mt->job == 3) { /* the owned neurons' update; their spikes dropped */
+    p->n_sp = orc_update_range(mt->nm, p->lo, p->hi, mt->n, mt->n_slots,
+                               mt->V, mt->I, mt->J, mt->refr, mt->rb, mt->t0,
+                               (int32_t)mt->n_steps, mt->nu, mt->w_ext,
+                               mt->seed, NULL, NULL, 0);
+    return NULL;
+  }
+  if (mt->job == 2) { /* one list onto the owned targets */
+    p->events = orc_deliver_ref(&st, mt->m_n, mt->d_src, mt->d_t, mt->rb,
+                                NULL, NULL);
+    return NULL;
+  }
+  /* job 1: the time-driven cycle */
+  p->events = 0;
+  for (int64_t t = mt->t0; t < mt->t0 + mt->n_steps; t += mt->interval) {
+    const int32_t m = (int32_t)((mt->t0 + mt->n_steps - t) < mt->interval
+                                    ? (mt->t0 + mt->n_steps - t)
+                                    : mt->interval);
+    p->n_sp = orc_update_range(mt->nm, p->lo, p->hi, mt->n, mt->n_slots,
+                               mt->V, mt->I, mt->J, mt->refr, mt->rb, t, m,
+                               mt->nu, mt->w_ext, mt->seed, p->sp_src, p->sp_t,
+                               (uint64_t)(p->hi - p->lo) * (uint64_t)m);
+    pthread_barrier_wait(&mt->bar);
+    if (k == 0) { /* merge: step by step, threads in neuron order */
+      uint64_t q = 0;
+      uint64_t* at = calloc((size_t)mt->n_threads, sizeof(uint64_t));
+      for (int32_t s = 0; s < m; ++s)
+        for (int r = 0; r < mt->n_threads; ++r) {
+          const orc_part* pr = &mt->part[r];
+          while (at[r] < pr->n_sp && pr->sp_t[at[r]] == t + s) {
+            mt->m_src[q] = pr->sp_src[at[r]];
+            mt->m_t[q] = pr->sp_t[at[r]];
+            ++q;
+            ++at[r];
+          }
+        }
+      free(at);
+      mt->m_n = q;
+      for (uint64_t e = 0; e < q; ++e, ++mt->total)
+        if (mt->total < mt->cap) {
+          mt->out_src[mt->total] = mt->m_src[e];
+          mt->out_t[mt->total] = mt->m_t[e];
+        }
+    }
+    pthread_barrier_wait(&mt->bar);
+    p->events += orc_deliver_ref(&st, mt->m_n, mt->m_src, mt->m_t, mt->rb,
+                                 NULL, NULL);
+  }
+  return NULL;
+}
+
+static void orc_mt_run(orc_mt* mt) {
+  pthread_t* th = malloc(sizeof(pthread_t) * (size_t)mt->n_threads);
+  orc_mt_arg* args = malloc(sizeof(orc_mt_arg) * (size_t)mt->n_threads);
+  for (int k = 0; k < mt->n_threads; ++k) {
+    args[k].mt = mt;
+    args[k].k = k;
+    pthread_create(&th[k], NULL, orc_mt_worker, &args[k]);
+  }
+  for (int k = 0; k < mt->n_threads; ++k) pthread_join(th[k], NULL);
+  free(th);
+  free(args);
+}
+
+void orc_mt_destroy(orc_mt* mt) {
+  if (!mt) return;
+  for (int k = 0; k < mt->n_threads; ++k) orc_mt_free_part(&mt->part[k]);
+  free(mt->part);
+  free(mt->m_src);
+  free(mt->m_t);
+  pthread_barrier_destroy(&mt->bar);
+  free(mt);
+}
+
+/* Build the per-thread stores of the fixed in-degree rule for n_threads
+ * threads that split the neurons [tgt_lo, tgt_hi) evenly in order (the
+ * whole population: 0, N); rows of every source, only the owned targets.
+ * NULL if memory runs out or the range is invalid. */
+orc_mt* orc_mt_create(const orc_conn* cp, int n_threads, int32_t n_slots,
+                      uint32_t tgt_lo, uint32_t tgt_hi) {
+  const uint32_t n = cp->n_e + cp->n_i;
+  if (tgt_hi > n || tgt_lo > tgt_hi) return NULL;
+  const uint32_t span = tgt_hi - tgt_lo;
+  if (n_threads < 1) n_threads = 1;
+  if ((uint32_t)n_threads > span && span > 0) n_threads = (int)span;
+  orc_mt* mt = calloc(1, sizeof(orc_mt));
+  if (!mt) return NULL;
+  mt->n = n;
+  mt->n_slots = n_slots;
+  mt->n_threads = n_threads;
+  mt->part = calloc((size_t)n_threads, sizeof(orc_part));
+  pthread_barrier_init(&mt->bar, NULL, (unsigned)n_threads);
+  if (!mt->part) { free(mt); return NULL; }
+  for (int k = 0; k < n_threads; ++k) {
+    mt->part[k].lo = tgt_lo + (uint32_t)((uint64_t)span * (uint64_t)k /
+                                         (uint64_t)n_threads);
+    mt->part[k].hi = tgt_lo + (uint32_t)((uint64_t)span * (uint64_t)(k + 1) /
+                                         (uint64_t)n_threads);
+  }
+  mt->job = 0;
+  mt->cp = cp;
+  orc_mt_run(mt);
+  int bad = 0;
+  for (int k = 0; k < n_threads; ++k) bad |= mt->part[k].events != 0;
+  if (bad) { orc_mt_destroy(mt); return NULL; }
+  return mt;
+}
+
+int orc_mt_threads(const orc_mt* mt) { return mt->n_threads; }
+
+/* Bounds of thread k's neurons. */
+void orc_mt_range(const orc_mt* mt, int k, uint32_t* lo, uint32_t* hi) {
+  *lo = mt->part[k].lo;
+  *hi = mt->part[k].hi;
+}
+
+/* orc_simulate on all threads: same arguments and results (bitwise), with
+ * the store given by orc_mt_create.  Returns the number of spikes (stored
+ * up to cap), or UINT64_MAX if memory runs out. */
+uint64_t orc_mt_simulate(orc_mt* mt, const orc_neuron* nm, int32_t interval,
+                         double* V, double* I, double* J, int32_t* refr,
+                         double* rb, int64_t t0, int64_t n_steps,
+                         double nu_ext_hz, double w_ext, uint64_t seed,
+                         uint32_t* sp_src, int64_t* sp_t, uint64_t cap,
+                         uint64_t* events_out) {
+  if (mt->part[0].lo != 0 || mt->part[mt->n_threads - 1].hi != mt->n)
+    return UINT64_MAX; /* a closed network needs every neuron */
+  const uint64_t iv_cap = (uint64_t)mt->n * (uint64_t)interval;
+  free(mt->m_src);
+  free(mt->m_t);
+  mt->m_src = malloc(sizeof(uint32_t) * (iv_cap ? iv_cap : 1));
+  mt->m_t = malloc(sizeof(int64_t) * (iv_cap ? iv_cap : 1));
+  int bad = !mt->m_src || !mt->m_t;
+  for (int k = 0; k < mt->n_threads && !bad; ++k) {
+    orc_part* p = &mt->part[k];
+    const uint64_t c = (uint64_t)(p->hi - p->lo) * (uint64_t)interval;
+    free(p->sp_src);
+    free(p->sp_t);
+    p->sp_src = malloc(sizeof(uint32_t) * (c ? c : 1));
+    p->sp_t = malloc(sizeof(int64_t) * (c ? c : 1));
+    bad |= !p->sp_src || !p->sp_t;
+  }
+  if (bad) return UINT64_MAX;
+  mt->job = 1;
+  mt->nm = nm;
+  mt->interval = interval;
+  mt->V = V; mt->I = I; mt->J = J; mt->refr = refr; mt->rb = rb;
+  mt->t0 = t0;
+  mt->n_steps = n_steps;
+  mt->nu = nu_ext_hz;
+  mt->w_ext = w_ext;
+  mt->seed = seed;
+  mt->out_src = sp_src;
+  mt->out_t = sp_t;
+  mt->cap = cap;
+  mt->total = 0;
+  orc_mt_run(mt);
+  uint64_t events = 0;
+  for (int k = 0; k < mt->n_threads; ++k) events += mt->part[k].events;
+  if (events_out) *events_out = events;
+  return mt->total;
+}
+
+/* Algorithm REF of one spike list onto every thread's targets (rb [S][N]);
+ * returns the events.  Bitwise equal to orc_deliver_ref on the full store. */
+uint64_t orc_mt_deliver(orc_mt* mt, uint64_t n_sp, const uint32_t* sp_src,
+                        const int64_t* sp_t, double* rb) {
+  mt->job = 2;
+  mt->m_n = n_sp;
+  mt->d_src = sp_src;
+  mt->d_t = sp_t;
+  mt->rb = rb;
+  orc_mt_run(mt);
+  uint64_t events = 0;
+  for (int k = 0; k < mt->n_threads; ++k) events += mt->part[k].events;
+  return events;
+}
+
+/* orc_update_range of every thread's neurons for n_steps steps from t0
+ * (state and rb indexed globally, [S][N]); the spikes are counted, not
+ * kept.  Returns the number of spikes. */
+uint64_t orc_mt_update(orc_mt* mt, const orc_neuron* nm, double* V, double* I,
+                       double* J, int32_t* refr, double* rb, int64_t t0,
+                       int32_t n_steps, double nu_ext_hz, double w_ext,
+                       uint64_t seed) {
+  mt->job = 3;
+  mt->nm = nm;
+  mt->V = V; mt->I = I; mt->J = J; mt->refr = refr; mt->rb = rb;
+  mt->t0 = t0;
+  mt->n_steps = n_steps;
+  mt->nu = nu_ext_hz;
+  mt->w_ext = w_ext;
+  mt->seed = seed;
+  orc_mt_run(mt);
+  uint64_t spikes = 0;
+  for (int k = 0; k < mt->n_threads; ++k) spikes += mt->part[k].n_sp;
+  return spikes;
 }
