@@ -362,6 +362,52 @@ def threaded_text(ctx, wl, bio_ms):
             f"{bio_ms:g} ms of biological time per step")
 
 
+def precision_probe(net, wl, nu_ext, w_g, seed, n_sample=3000):
+    """Error of the stored-weight format against the FP64 oracle with the
+    unrounded weights, measured after the timed region from the net's
+    current state: both sides deliver one 8 Hz Bernoulli interval list
+    (emission steps [t0 - D, t0)) and update one interval with the same
+    drive; ring-buffer cells and membrane potentials of the targets
+    [0, n_sample) are compared (max and RMS), neurons whose spike decision
+    differs are counted and left out of the potential figures."""
+    import oracle as O
+    from paper_2109_12855_gb300 import snn
+    D = wl.d_lo
+    src, tt = W.bernoulli_spikes(wl.n, 0, D, 8.0, 0.1, seed=77)
+    t0 = net.stats().t_now
+    V, I, J, refr = net.read_state()
+    snn.snn_clear_rb(net.h)
+    net.deliver(src, (tt + t0 - D).astype(np.int32))
+    rb_g = net.read_rb()[:, :n_sample].astype(np.float64)
+    snn.snn_update(net.h, t0, D)
+    snn.snn_discard_pending(net.h)
+    V_g, _, _, refr_g = net.read_state()
+    nm = O.Neuron()
+    w_o = O.weight_for_psp(nm, wl.psp_mv)
+    cp = O.Conn(wl.n_e, wl.n_i, wl.k_e, wl.k_i, w_o, -wl.g * w_o, wl.d_lo,
+                wl.d_hi, seed + 1000, sd_e=wl.sd_rel * w_o,
+                sd_i=wl.sd_rel * wl.g * w_o, wfmt=0)
+    store = O.build_fixed_indegree_targets(cp, 0, n_sample)
+    rb_o, _, absw, _ = O.deliver_ref(store, 32, src, tt + t0 - D)
+    st = O.State(V.astype(np.float64), I.astype(np.float64),
+                 J.astype(np.float64), refr.copy())
+    O.update_range(nm, st, rb_o.copy(), 0, n_sample, t0, D, nu_ext, w_o, seed)
+    err = rb_g - rb_o[:, :n_sample]
+    absw = absw[:, :n_sample]
+    hit = absw > 0
+    same = refr_g[:n_sample] == st.refr[:n_sample]
+    dv = np.abs(V_g[:n_sample].astype(np.float64) - st.V[:n_sample])
+    return {"against": "FP64 oracle, unrounded weights",
+            "targets": n_sample, "cells": int(hit.sum()),
+            "rb_max_abs_pa": float(np.abs(err).max()),
+            "rb_rms_pa": float(np.sqrt(np.mean(err[hit] ** 2))),
+            "rb_max_rel": float((np.abs(err)[hit] / absw[hit]).max()),
+            "vm_max_abs_mv": float(dv[same].max()) if same.any() else None,
+            "vm_rms_mv": float(np.sqrt(np.mean(dv[same] ** 2)))
+            if same.any() else None,
+            "spike_mismatch": int((~same).sum())}
+
+
 def cpu_baseline_all_cores(args, wl, nu_ext):
     """All-cores oracle figures for cpu_baseline: events/s, the real-time
     factor (measured on the whole network, or extrapolated from the sample
@@ -664,6 +710,9 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
                "steps": k_e2e}
     st = net.stats()
     err = st.error_flags
+    precision = None
+    if ws == 1 and not args.no_cpu_baseline and kind != "deliver" and not plastic:
+        precision = precision_probe(net, wl, nu_ext, w_e, 1 + rank)
     net.close()
 
     if rank != 0:
@@ -730,6 +779,8 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
         "clocks": clk,
         "error_flags": err,
     }
+    if precision:
+        line["precision"] = precision
     if long_run:
         line["long_run"] = long_run
     print(json.dumps(line), flush=True)

@@ -455,6 +455,25 @@ def update(nm: Neuron, st: State, rb: np.ndarray, t0: int, n_steps: int,
     return src[:ns].copy(), tt[:ns].copy()
 
 
+def update_range(nm: Neuron, st: State, rb: np.ndarray, lo: int, hi: int,
+                 t0: int, n_steps: int, nu_ext_hz: float, w_ext: float,
+                 seed: int, cap: int | None = None):
+    """``update`` of the neurons [lo, hi) only (arrays indexed globally, in
+    place; the drive keyed by the global index)."""
+    n = len(st.V)
+    assert 0 <= lo <= hi <= n and rb.shape[1] == n
+    cap = (hi - lo) * max(n_steps, 1) if cap is None else cap
+    src = np.zeros(max(cap, 1), np.uint32)
+    tt = np.zeros(max(cap, 1), np.int64)
+    ns = _load().orc_update_range(C.byref(nm.c()), lo, hi, n, rb.shape[0],
+                                  _ptr(st.V), _ptr(st.I), _ptr(st.J),
+                                  _ptr(st.refr), _ptr(rb), t0, n_steps,
+                                  nu_ext_hz, w_ext, seed, _ptr(src), _ptr(tt),
+                                  cap)
+    ns = min(int(ns), cap)
+    return src[:ns].copy(), tt[:ns].copy()
+
+
 def simulate(nm: Neuron, store: Store, n_slots: int, interval: int, st: State,
              rb: np.ndarray, t0: int, n_steps: int, nu_ext_hz: float,
              w_ext: float, seed: int, cap: int = 1 << 24):
