@@ -658,7 +658,7 @@ struct FixScale {
   int sh;          // s
   float scale_hs;  // 2^(q - s)
   float scale_s;   // 2^s
-  double inv_q;    // 2^-q
+  float inv_q;     // 2^-q (q <= 123: a normal float)
 };
 
 // 2^k from the exponent bits (k inside the normal range of the type), and
@@ -680,7 +680,7 @@ constexpr int kFixMaxShift = 23;
 
 __device__ FixScale fix_scale(const NetView& v, uint64_t n_sp,
                               bool per_interval) {
-  FixScale f{0, 0, 1.f, 1.f, 1.0};
+  FixScale f{0, 0, 1.f, 1.f, 1.f};
   uint64_t e = n_sp * (uint64_t)(v.mult_max ? v.mult_max : 1u);
   if (per_interval) {
     const uint64_t e2 = (uint64_t)v.k_in_max * (v.spikes_per_iv ? v.spikes_per_iv : 1u);
@@ -709,7 +709,7 @@ __device__ FixScale fix_scale(const NetView& v, uint64_t n_sp,
   f.sh = sh;
   f.scale_hs = pow2f(qs);
   f.scale_s = pow2f(sh);
-  f.inv_q = pow2d(-q);
+  f.inv_q = pow2f(-q);
   return f;
 }
 
@@ -1064,36 +1064,26 @@ __device__ __forceinline__ void deliver_tile_body(
     __syncthreads();  // s_desc is rewritten by the next batch
   } while (j0 < n_sp);
   if (inwin) {
-    // each thread owns whole target columns; the ring-buffer reads of
-    // kFlush slots are issued together, then the sums are written back
-    // (one memory round trip per kFlush slots, not one per slot)
-    constexpr uint32_t kFlush = 8;
-    for (uint32_t x = threadIdx.x; x < TW && tgt_lo + x < v.n; x += blockDim.x) {
-      float* const col = v.rb + tgt_lo + x;
-      for (uint32_t sl0 = 0; sl0 < W; sl0 += kFlush) {
-        float a[kFlush], old[kFlush];
-        uint32_t off[kFlush];
-#pragma unroll
-        for (uint32_t q = 0; q < kFlush; ++q) {
-          a[q] = 0.f;
-          off[q] = ((uint32_t)(base + sl0 + q) & v.slot_mask) * v.pitch;
-          if (sl0 + q < W) {
-            const uint32_t c = (sl0 + q) * TW + x;
-            if (fx.fixed) {
-              const long long T = ((long long)accH[c] << fx.sh) +
-                                  (two ? (long long)accL[c] : 0ll);
-              a[q] = (float)((double)T * fx.inv_q);
-            } else {
-              a[q] = accF[c];
-            }
-          }
+    // Every cell of the window belongs to this CTA alone, so its sum goes
+    // into the ring buffer as a fire-and-forget global reduction: the one
+    // addition rb + sum that a read-modify-write would make, without a
+    // memory round trip.  The exact sum T 2^-q is rounded to float once
+    // (int64 -> float, then an exact power-of-two scale: T 2^-q >= 2^-123
+    // stays normal); no FP64 arithmetic, whose rate is low on this part.
+    for (uint32_t sl = 0; sl < W; ++sl) {
+      float* const row = v.rb +
+          (size_t)((uint32_t)(base + sl) & v.slot_mask) * v.pitch + tgt_lo;
+      for (uint32_t x = threadIdx.x; x < TW && tgt_lo + x < v.n; x += blockDim.x) {
+        const uint32_t c = sl * TW + x;
+        float a;
+        if (fx.fixed) {
+          const long long T = ((long long)accH[c] << fx.sh) +
+                              (two ? (long long)accL[c] : 0ll);
+          a = __ll2float_rn(T) * fx.inv_q;
+        } else {
+          a = accF[c];
         }
-#pragma unroll
-        for (uint32_t q = 0; q < kFlush; ++q)
-          old[q] = a[q] != 0.f ? col[off[q]] : 0.f;
-#pragma unroll
-        for (uint32_t q = 0; q < kFlush; ++q)
-          if (a[q] != 0.f) col[off[q]] = old[q] + a[q];
+        if (a != 0.f) red_add_f32(row + x, a);
       }
     }
   }
