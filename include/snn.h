@@ -442,8 +442,11 @@ int snn_load_state(snn_net* net, const void* host_buf, uint64_t size);
 /* Set the step counter (next step to update). */
 int snn_set_time(snn_net* net, int64_t t);
 /* Profiling on: every update and deliver launch is bracketed by CUDA events
- * on the net's stream and graphs are not used; times accumulate into
- * snn_stats.ms_update / ms_deliver. */
+ * on the net's stream; times accumulate into snn_stats.ms_update /
+ * ms_deliver.  snn_simulate keeps its CUDA graphs of whole intervals, with
+ * the events captured as graph nodes, so the kernels are timed in the launch
+ * context of the production path (the host waits after each graph to read
+ * the times); other calls record the events around plain launches. */
 int snn_set_profiling(snn_net* net, int on);
 /* Counters (synchronises). */
 int snn_get_stats(snn_net* net, snn_stats* out);

@@ -540,26 +540,54 @@ int launch_interval(snn_net* net, int steps) {
   return SNN_OK;
 }
 
-int capture_graph(snn_net* net) {
-  if (net->graph) return SNN_OK;
+// kGraphIntervals intervals captured as one graph.  prof: the profiling form,
+// with an event recorded (as a graph node) before each update, between it and
+// its delivery, and after the delivery (events 3k, 3k+1, 3k+2), so that the
+// kernels are timed in the launch context of the production graph.
+int capture_graph(snn_net* net, bool prof) {
+  cudaGraphExec_t* out = prof ? &net->graph_prof : &net->graph;
+  if (*out) return SNN_OK;
+  if (prof)
+    for (int k = 0; k < 3 * kGraphIntervals; ++k)
+      REQ(pool_event(net, (size_t)k), SNN_E_CUDA, "event creation failed");
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
   NetView v = net->view();
   for (int k = 0; k < kGraphIntervals; ++k) {
+    cudaError_t e0 = cudaSuccess, e3 = cudaSuccess, e4 = cudaSuccess;
+    if (prof)
+      e0 = cudaEventRecordWithFlags(net->ev[3 * k], net->stream,
+                                    cudaEventRecordExternal);
     cudaError_t e1 = launch_update(v, net->uc, net->interval, 1, 0, net->stream);
+    if (prof)
+      e3 = cudaEventRecordWithFlags(net->ev[3 * k + 1], net->stream,
+                                    cudaEventRecordExternal);
     cudaError_t e2 = launch_deliver_any(net, &net->ctl->pair, &net->ctl->done,
                                         net->list, 0, 1);
-    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    if (prof)
+      e4 = cudaEventRecordWithFlags(net->ev[3 * k + 2], net->stream,
+                                    cudaEventRecordExternal);
+    const cudaError_t e = e0 != cudaSuccess ? e0 : e1 != cudaSuccess ? e1
+                        : e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4;
+    if (e != cudaSuccess) {
       cudaStreamEndCapture(net->stream, &g);
-      return fail(SNN_E_CUDA, "graph capture failed: %s",
-                  cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+      return fail(SNN_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
     }
   }
   CK(cudaStreamEndCapture(net->stream, &g));
-  cudaError_t e = cudaGraphInstantiate(&net->graph, g, 0);
+  cudaError_t e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   CK(e);
   return SNN_OK;
+}
+
+// Captured graphs hold the net's view and constants: drop them when those
+// change.
+void drop_graphs(snn_net* net) {
+  if (net->graph) cudaGraphExecDestroy(net->graph);
+  if (net->graph_prof) cudaGraphExecDestroy(net->graph_prof);
+  net->graph = nullptr;
+  net->graph_prof = nullptr;
 }
 
 }  // namespace
@@ -1186,6 +1214,29 @@ int snn_simulate(snn_net* net, int64_t n_steps) {
   const int rem = (int)(n_steps % D);
   cudaStream_t s = net->stream;
   if (net->profiling) {
+    // whole graphs of intervals with their timing events, read after each
+    // replay; the remaining intervals one by one between events
+    auto add_times = [&](int64_t n) -> int {
+      for (int64_t k = 0; k < n; ++k) {
+        float mu = 0, md = 0;
+        CK(cudaEventElapsedTime(&mu, net->ev[3 * k], net->ev[3 * k + 1]));
+        CK(cudaEventElapsedTime(&md, net->ev[3 * k + 1], net->ev[3 * k + 2]));
+        net->ms_update += mu;
+        net->ms_deliver += md;
+      }
+      return SNN_OK;
+    };
+    if (full >= kGraphIntervals) {
+      if ((rc = capture_graph(net, true)) != SNN_OK) return rc;
+      for (; full >= kGraphIntervals; full -= kGraphIntervals) {
+        CK(cudaGraphLaunch(net->graph_prof, s));
+        CK(cudaStreamSynchronize(s));
+        if ((rc = add_times(kGraphIntervals)) != SNN_OK) return rc;
+        net->launches += 2 * kGraphIntervals;
+        net->upd_launches += kGraphIntervals;
+        net->del_launches += kGraphIntervals;
+      }
+    }
     const int64_t n_iv = full + (rem ? 1 : 0);
     for (int64_t k = 0; k < n_iv; ++k) {
       const int steps = k < full ? D : rem;
@@ -1205,16 +1256,10 @@ int snn_simulate(snn_net* net, int64_t n_steps) {
       net->del_launches += 1;
     }
     CK(cudaStreamSynchronize(s));
-    for (int64_t k = 0; k < n_iv; ++k) {
-      float mu = 0, md = 0;
-      CK(cudaEventElapsedTime(&mu, net->ev[3 * k], net->ev[3 * k + 1]));
-      CK(cudaEventElapsedTime(&md, net->ev[3 * k + 1], net->ev[3 * k + 2]));
-      net->ms_update += mu;
-      net->ms_deliver += md;
-    }
+    if ((rc = add_times(n_iv)) != SNN_OK) return rc;
   } else {
     if (full >= kGraphIntervals) {
-      if ((rc = capture_graph(net)) != SNN_OK) return rc;
+      if ((rc = capture_graph(net, false)) != SNN_OK) return rc;
       for (; full >= kGraphIntervals; full -= kGraphIntervals) {
         CK(cudaGraphLaunch(net->graph, s));
         net->launches += 2 * kGraphIntervals;
@@ -1468,10 +1513,7 @@ int snn_set_drive(snn_net* net, double nu_ext, double w_ext) {
       "Poisson drive rate too high for the inversion table");
   net->p = p;
   net->uc = uc;
-  if (net->graph) {  // the captured graph holds the old constants
-    cudaGraphExecDestroy(net->graph);
-    net->graph = nullptr;
-  }
+  drop_graphs(net);  // the captured graphs hold the old constants
   return SNN_OK;
 }
 
@@ -1581,10 +1623,7 @@ int snn_set_bounds(snn_net* net, const snn_bounds* b) {
   net->mult_max = std::max(net->mult_max, b->mult_max);
   net->k_in_max = std::max(net->k_in_max, b->k_in_max);
   net->max_abs_w = std::max(net->max_abs_w, b->max_abs_w);
-  if (net->graph) {  // the captured intervals hold the old view
-    cudaGraphExecDestroy(net->graph);
-    net->graph = nullptr;
-  }
+  drop_graphs(net);  // the captured intervals hold the old view
   return SNN_OK;
 }
 
@@ -1684,7 +1723,7 @@ int snn_destroy(snn_net* net) {
   if (!net) return SNN_OK;
   cudaSetDevice(net->device);
   if (net->stream) cudaStreamSynchronize(net->stream);
-  if (net->graph) cudaGraphExecDestroy(net->graph);
+  drop_graphs(net);
   for (cudaEvent_t e : net->ev) cudaEventDestroy(e);
   void* bufs[] = {net->V,        net->I,        net->J,       net->refr,
                   net->rb,       net->counts,   net->ctl,     net->row_ptr,

@@ -191,6 +191,17 @@ __device__ __forceinline__ void stdp_on_spike(const StdpView& sp, uint32_t i,
   sp.ring_n[i] = n + 1u;
 }
 
+// L2 prefetch of source src's row of the tile index, line by line.
+__device__ __forceinline__ void prefetch_row_l2(const NetView& v, uint32_t src) {
+  const char* a = reinterpret_cast<const char*>(
+      v.tile_off + (uint64_t)src * (v.n_tiles + 1u));
+  const char* e = a + 4ull * (v.n_tiles + 1u);
+  for (const char* p = reinterpret_cast<const char*>(
+           reinterpret_cast<uintptr_t>(a) & ~(uintptr_t)127);
+       p < e; p += 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Body of the update for neuron block `block` of net v (one thread per
 // neuron); shared by the single-net and the batched kernels.
 // PL: the single-net update, which also keeps the plasticity state and the
@@ -345,6 +356,9 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
           e.choff = (uint32_t)old + ex_ch + k * nch;
           e.pad = 0;
           v.list[idx] = e;
+          // the tiled delivery that follows reads this source's row of the
+          // tile index (two words per CTA): bring the row into L2 now
+          if (v.tile_off && k == 0) prefetch_row_l2(v, v.g0 + i);
         } else {
           atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_SPIKE_LIST);
         }
@@ -659,6 +673,7 @@ struct FixScale {
   float scale_hs;  // 2^(q - s)
   float scale_s;   // 2^s
   float inv_q;     // 2^-q (q <= 123: a normal float)
+  float scale_sq;  // 2^(s-q)
 };
 
 // 2^k from the exponent bits (k inside the normal range of the type), and
@@ -680,7 +695,7 @@ constexpr int kFixMaxShift = 23;
 
 __device__ FixScale fix_scale(const NetView& v, uint64_t n_sp,
                               bool per_interval) {
-  FixScale f{0, 0, 1.f, 1.f, 1.f};
+  FixScale f{0, 0, 1.f, 1.f, 1.f, 1.f};
   uint64_t e = n_sp * (uint64_t)(v.mult_max ? v.mult_max : 1u);
   if (per_interval) {
     const uint64_t e2 = (uint64_t)v.k_in_max * (v.spikes_per_iv ? v.spikes_per_iv : 1u);
@@ -710,6 +725,7 @@ __device__ FixScale fix_scale(const NetView& v, uint64_t n_sp,
   f.scale_hs = pow2f(qs);
   f.scale_s = pow2f(sh);
   f.inv_q = pow2f(-q);
+  f.scale_sq = pow2f(-qs);
   return f;
 }
 
@@ -822,6 +838,20 @@ __device__ __forceinline__ void deliver_tile_body(
   const uint32_t tgt_lo = tile * TW;
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
+  // An interval's own list (capacity list_cap): this thread's first list
+  // entries are read together with the list's length, not after it (one
+  // memory round trip fewer before the runs can be described); entries past
+  // the length are never used.
+  constexpr int kDU = PL ? 1 : 4;
+  SpikeEntry pre[kDU];
+  const bool spec = !from_list_range;
+  if (spec) {
+#pragma unroll
+    for (int u = 0; u < kDU; ++u) {
+      const uint32_t k = threadIdx.x + u * blockDim.x;
+      if (k < desc_cap && k < v.list_cap) pre[u] = list[k];
+    }
+  }
   // every thread reads the launch's list size and window (same addresses);
   // thread 0 derives the fixed-point scales meanwhile
   const unsigned long long pr =
@@ -991,15 +1021,16 @@ __device__ __forceinline__ void deliver_tile_body(
   };
 
   // (A) describe the runs of spikes [j0, j0 + nb): kDU list entries per
-  // thread in flight, then their tile-index words and row starts
-  constexpr int kDU = PL ? 1 : 4;
+  // thread in flight (the first ones already read), then their tile-index
+  // words and row starts
   auto describe = [&](uint32_t j0, uint32_t nb) {
     for (uint32_t k0 = threadIdx.x; k0 < nb; k0 += kDU * blockDim.x) {
       SpikeEntry e[kDU];
+      const bool have = spec && j0 == 0 && k0 == threadIdx.x;
 #pragma unroll
       for (int u = 0; u < kDU; ++u) {
         const uint32_t k = k0 + u * blockDim.x;
-        if (k < nb) e[u] = list[j0 + k];
+        if (k < nb) e[u] = have ? pre[u] : list[j0 + k];
       }
 #pragma unroll
       for (int u = 0; u < kDU; ++u) {
@@ -1067,9 +1098,11 @@ __device__ __forceinline__ void deliver_tile_body(
     // Every cell of the window belongs to this CTA alone, so its sum goes
     // into the ring buffer as a fire-and-forget global reduction: the one
     // addition rb + sum that a read-modify-write would make, without a
-    // memory round trip.  The exact sum T 2^-q is rounded to float once
-    // (int64 -> float, then an exact power-of-two scale: T 2^-q >= 2^-123
-    // stays normal); no FP64 arithmetic, whose rate is low on this part.
+    // memory round trip.  The exact sum (H 2^s + L) 2^-q becomes
+    // H 2^(s-q) + L 2^-q in FP32: both products are exact while |H| and |L|
+    // are below 2^24 (then only the addition rounds, so the result is the
+    // correctly rounded sum; larger words round once more), no 64-bit
+    // conversion or FP64 arithmetic, whose rate is low on this part.
     for (uint32_t sl = 0; sl < W; ++sl) {
       float* const row = v.rb +
           (size_t)((uint32_t)(base + sl) & v.slot_mask) * v.pitch + tgt_lo;
@@ -1077,9 +1110,8 @@ __device__ __forceinline__ void deliver_tile_body(
         const uint32_t c = sl * TW + x;
         float a;
         if (fx.fixed) {
-          const long long T = ((long long)accH[c] << fx.sh) +
-                              (two ? (long long)accL[c] : 0ll);
-          a = __ll2float_rn(T) * fx.inv_q;
+          a = __fmul_rn(__int2float_rn(accH[c]), fx.scale_sq);
+          if (two) a = __fadd_rn(a, __fmul_rn(__int2float_rn(accL[c]), fx.inv_q));
         } else {
           a = accF[c];
         }

@@ -67,6 +67,7 @@ struct snn_net {
   double ms_update = 0, ms_deliver = 0;
   uint64_t launches = 0, upd_launches = 0, del_launches = 0;
   cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph_prof = nullptr;  // the same intervals with timing events
   // STDP (snn_set_stdp): parameters and device state (StdpView)
   bool stdp_on = false;
   snn_stdp_params stdp{};
