@@ -1103,10 +1103,13 @@ __device__ __forceinline__ void deliver_tile_body(
     // are below 2^24 (then only the addition rounds, so the result is the
     // correctly rounded sum; larger words round once more), no 64-bit
     // conversion or FP64 arithmetic, whose rate is low on this part.
-    for (uint32_t sl = 0; sl < W; ++sl) {
-      float* const row = v.rb +
-          (size_t)((uint32_t)(base + sl) & v.slot_mask) * v.pitch + tgt_lo;
-      for (uint32_t x = threadIdx.x; x < TW && tgt_lo + x < v.n; x += blockDim.x) {
+    // (the slots of a column are independent: unrolled, so that their
+    // shared-memory reads and conversions overlap)
+    const uint32_t x_end = tgt_lo < v.n ? min(TW, v.n - tgt_lo) : 0u;
+    for (uint32_t x = threadIdx.x; x < x_end; x += blockDim.x) {
+      float* const col = v.rb + tgt_lo + x;
+#pragma unroll 4
+      for (uint32_t sl = 0; sl < W; ++sl) {
         const uint32_t c = sl * TW + x;
         float a;
         if (fx.fixed) {
@@ -1115,7 +1118,8 @@ __device__ __forceinline__ void deliver_tile_body(
         } else {
           a = accF[c];
         }
-        if (a != 0.f) red_add_f32(row + x, a);
+        if (a != 0.f)
+          red_add_f32(col + (size_t)((uint32_t)(base + sl) & v.slot_mask) * v.pitch, a);
       }
     }
   }
