@@ -79,7 +79,25 @@ WORKLOADS = {
     "balanced-20000-fp32": (W.Balanced("balanced-20000", 16000, 4000, 9000,
                                        2250, 15, 15, "fp32", 0.0, 150.0),
                             0, 150.0, "simulate"),
+    # the same network driven to ~45 Hz: ~1,350 spikes per 15-step interval,
+    # the launch shape of the 1.27e9-synapse delivery (152 tiles, runs of ~74
+    # records) on a 2.7 GB store, simulated (interval-list kernel, update
+    # prefetch included)
+    "balanced-20000-fp32-45hz": (W.Balanced("balanced-20000", 16000, 4000,
+                                            9000, 2250, 15, 15, "fp32", 0.0,
+                                            150.0), 0, 150.0, "simulate"),
+    # 93,750 neurons, in-degree 1,900, delays 10..20, BF16 with spread,
+    # driven to ~47 Hz: ~4,400 spikes per 10-step interval and runs of ~25
+    # records, the per-CTA shape of the 6.3e9-synapse delivery, on a 1.4 GB
+    # store, simulated
+    "balanced-93750-k1900-bf16": (W.Balanced("balanced-93750-k1900", 75000,
+                                             18750, 1520, 380, 10, 20, "bf16",
+                                             0.1, 100.0), 1, 100.0, "simulate"),
 }
+# drive of the profiling cases above (found with paper_2109_12855_gb300.tune
+# on a GB300 for the rates stated; all other workloads use NU_EXT_8HZ)
+NU_EXT_OF = {"balanced-20000-fp32-45hz": 89526.3671875,
+             "balanced-93750-k1900-bf16": 35632.32421875}
 DEFAULT = "balanced-112500-fp32"
 PLASTIC = {"balanced-112500-stdp-bf16", "stdp-20000-bf16"}
 # STDP of the plastic workload: tau 20 ms, lambda 0.1, alpha 0.0513, mu 0.4;
@@ -582,6 +600,28 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
     st0 = net.stats()
     st_tiles = st0
     D = st0.interval
+
+    if args.launch_bytes:
+        # per-launch algorithmic bytes of the delivery kernel, for comparison
+        # with a profiler's per-launch DRAM counters on the same (bitwise
+        # reproducible) launches: --launch-skip intervals, then one interval
+        # per call with the counters read after each
+        snn.snn_simulate(h, args.launch_skip * D)
+        rows = []
+        for _ in range(args.launch_bytes):
+            a = net.stats()
+            snn.snn_simulate(h, D)
+            b = net.stats()
+            ev, sp = b.events_delivered - a.events_delivered, b.spikes - a.spikes
+            pl = b.plastic_events - a.plastic_events
+            rows.append({"events": ev, "spikes": sp,
+                         "bytes": rec_bytes * ev + 32 * sp + 8 * pl})
+        net.close()
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "skip": args.launch_skip,
+                              "kernel": "k_deliver_tiled", "launches": rows}),
+                  flush=True)
+        return
 
     if kind == "deliver":
         # record one step of the whole network's spikes (or draw Bernoulli
@@ -1159,13 +1199,19 @@ def main():
     ap.add_argument("--oracle-bio-ms", type=float, default=100.0,
                     help="biological ms per all-cores oracle step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch-bytes", type=int, default=0,
+                    help="print the algorithmic bytes of this many delivery "
+                         "launches (one interval each) and exit")
+    ap.add_argument("--launch-skip", type=int, default=200,
+                    help="intervals simulated before --launch-bytes")
     ap.add_argument("--deliver-mode", choices=["tiled", "atomic"],
                     default="tiled")
     ap.add_argument("--replay-rate", type=float, default=0.0,
                     help="deliver workloads: Bernoulli lists at this rate "
                          "instead of a recorded run")
     args = ap.parse_args()
-    nu_ext = args.nu_ext if args.nu_ext is not None else NU_EXT_8HZ
+    nu_ext = args.nu_ext if args.nu_ext is not None else \
+        NU_EXT_OF.get(args.workload, NU_EXT_8HZ)
     if args.workload in SERVE_WORKLOADS:
         if args.impl == "reference":
             big = max(W.serving_stream(args.requests), key=lambda r:
