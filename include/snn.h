@@ -150,7 +150,14 @@ typedef struct snn_params {
                              need, which halves the shared memory per target;
                              else two), 2 = always two.  Both give the same
                              sums. */
-  int32_t reserved_;      /* 0 */
+  int32_t build_yield;    /* 1: the connection-store build runs as short
+                             CTAs that each fill a whole SM, so that an SM
+                             is entirely free whenever one ends and kernels
+                             of higher-priority streams (nets already
+                             running, whose delivery CTAs need a whole SM)
+                             get it first; the build itself is somewhat
+                             slower.  0: the normal shape.  The server sets 1
+                             for the nets it builds beside running ones. */
 } snn_params;
 
 /* Fixed in-degree connection rule (the benchmark model's random

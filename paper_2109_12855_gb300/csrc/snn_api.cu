@@ -193,14 +193,23 @@ cudaMemPool_t device_pool(int dev) {
   return P.pool[dev];
 }
 
+// Nets (and servers, which hold the pool for their lifetime) alive per
+// device; the pool's unused memory goes back to the device when the count
+// reaches zero.  The wait and the trim happen outside the lock, so that
+// other threads' allocations never queue behind them (a trim releases only
+// unused memory and may run beside allocations).
 void count_net(int dev, int delta, cudaStream_t s) {
   if (dev < 0 || dev >= 64) return;
   DevicePools& P = pools();
-  std::lock_guard<std::mutex> lk(P.mu);
-  P.live[dev] += delta;
-  if (P.live[dev] == 0 && P.pool[dev]) {
+  cudaMemPool_t trim = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(P.mu);
+    P.live[dev] += delta;
+    if (P.live[dev] == 0) trim = P.pool[dev];
+  }
+  if (trim) {
     cudaStreamSynchronize(s);  // its frees are done
-    cudaMemPoolTrimTo(P.pool[dev], 0);
+    cudaMemPoolTrimTo(trim, 0);
   }
 }
 
@@ -220,6 +229,8 @@ cudaError_t snn::pool_alloc(void** p, size_t bytes, cudaStream_t s) {
 void snn::pool_free(void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
+
+void snn::pool_hold(int dev, int delta) { count_net(dev, delta, nullptr); }
 
 namespace {
 
@@ -668,6 +679,8 @@ int snn_create(const snn_params* p, void* stream, snn_net** out) {
   REQ(p->tile_width >= 0, SNN_E_ARG, "bad tile_width %d", p->tile_width);
   REQ(p->acc_words == 0 || p->acc_words == 2, SNN_E_ARG,
       "acc_words must be 0 (automatic) or 2, not %d", p->acc_words);
+  REQ(p->build_yield == 0 || p->build_yield == 1, SNN_E_ARG,
+      "build_yield must be 0 or 1, not %d", p->build_yield);
   const bool part = p->part_hi != 0 || p->part_lo != 0;
   REQ(!part || (p->part_lo < p->part_hi && p->part_hi <= n), SNN_E_ARG,
       "partition [%u, %u) outside [0, %llu)", p->part_lo, p->part_hi,
@@ -749,9 +762,19 @@ int snn_create(const snn_params* p, void* stream, snn_net** out) {
   return SNN_OK;
 }
 
+// The build kernels of the calling thread take the net's build_yield shape
+// while this object lives.
+struct BuildShapeScope {
+  explicit BuildShapeScope(const snn_net* net) {
+    set_build_yield(net->p.build_yield != 0 ? 1u : 0u);
+  }
+  ~BuildShapeScope() { set_build_yield(0); }
+};
+
 int snn_connect_fixed_indegree(snn_net* net, const snn_conn_params* c) {
   REQ(net && c, SNN_E_ARG, "null argument");
   REQ(!net->connected && !net->finalized, SNN_E_STATE, "net already connected");
+  BuildShapeScope confine(net);
   const snn_params& p = net->p;
   REQ(c->d_lo >= 1 && c->d_hi >= c->d_lo && c->d_hi <= net->n_slots &&
           c->d_hi <= 255,
@@ -814,6 +837,7 @@ int snn_connect_edges(snn_net* net, const uint32_t* src, const uint32_t* tgt,
   REQ(check_mem(mem), SNN_E_ARG, "bad mem kind");
   REQ(n < (1ull << 32), SNN_E_ARG, "too many edges");
   REQ(n == 0 || (src && tgt && delay && w), SNN_E_ARG, "null edge array");
+  BuildShapeScope confine(net);
   int rc;
   if ((rc = set_device(net)) != SNN_OK) return rc;
   cudaStream_t s = net->stream;
@@ -943,6 +967,7 @@ int setup_stdp(snn_net* net) {
 int snn_finalize(snn_net* net) {
   REQ(net, SNN_E_ARG, "null net");
   REQ(!net->finalized, SNN_E_STATE, "already finalized");
+  BuildShapeScope confine(net);
   int rc;
   if ((rc = set_device(net)) != SNN_OK) return rc;
   cudaStream_t s = net->stream;

@@ -23,6 +23,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "snn_internal.cuh"
 
 namespace snn {
@@ -52,27 +54,30 @@ __device__ __forceinline__ uint32_t fixed_source(const BuildFixed& b,
   return k < b.k_e ? scale_u32(u, b.n_e) : b.n_e + scale_u32(u, b.n_i);
 }
 
+// One block per local target (the draws use its global index); a grid
+// smaller than the targets walks them in strides (a build confined to some
+// SMs, see BuildShape).
 __global__ void k_count_fixed(BuildFixed b, uint32_t* deg) {
-  const uint32_t tgt = blockIdx.x;  // local target; draws use the global one
   const uint32_t kk = b.k_e + b.k_i;
-  for (uint32_t k = threadIdx.x; k < kk; k += blockDim.x) {
-    U4 r = draw(b.seed, b.tgt0 + tgt, k, 0u);
-    atomicAdd(&deg[fixed_source(b, k, r.x)], 1u);
-  }
+  for (uint32_t tgt = blockIdx.x; tgt < b.n_tgt; tgt += gridDim.x)
+    for (uint32_t k = threadIdx.x; k < kk; k += blockDim.x) {
+      U4 r = draw(b.seed, b.tgt0 + tgt, k, 0u);
+      atomicAdd(&deg[fixed_source(b, k, r.x)], 1u);
+    }
 }
 
 __global__ void k_scatter_fixed(BuildFixed b, const uint64_t* row_ptr,
                                 uint32_t* cursor, uint64_t* keys, TileGeom g) {
-  const uint32_t tgt = blockIdx.x;
   const uint32_t kk = b.k_e + b.k_i;
   const uint32_t span = (uint32_t)(b.d_hi - b.d_lo + 1);
-  for (uint32_t k = threadIdx.x; k < kk; k += blockDim.x) {
-    U4 r = draw(b.seed, b.tgt0 + tgt, k, 0u);
-    uint32_t src = fixed_source(b, k, r.x);
-    uint32_t d = (uint32_t)b.d_lo + scale_u32(r.y, span);
-    uint32_t pos = atomicAdd(&cursor[src], 1u);
-    keys[row_ptr[src] + pos] = make_key(d, tgt, k, g);
-  }
+  for (uint32_t tgt = blockIdx.x; tgt < b.n_tgt; tgt += gridDim.x)
+    for (uint32_t k = threadIdx.x; k < kk; k += blockDim.x) {
+      U4 r = draw(b.seed, b.tgt0 + tgt, k, 0u);
+      uint32_t src = fixed_source(b, k, r.x);
+      uint32_t d = (uint32_t)b.d_lo + scale_u32(r.y, span);
+      uint32_t pos = atomicAdd(&cursor[src], 1u);
+      keys[row_ptr[src] + pos] = make_key(d, tgt, k, g);
+    }
 }
 
 __global__ void k_count_edges(const uint32_t* src, uint64_t n, uint32_t* deg) {
@@ -230,23 +235,27 @@ __global__ void k_sort_pack(uint32_t n, const uint64_t* row_ptr,
 }
 
 template <int FMT, int WMODE>
-__global__ void k_sort_long(const uint32_t* rows, const uint64_t* row_ptr,
+__global__ void k_sort_long(const uint32_t* rows, uint32_t n_long,
+                            const uint64_t* row_ptr,
                             uint64_t* keys, void* recs, BuildFixed b,
                             const double* edge_w, uint64_t* scratch,
                             const uint64_t* scratch_off, TileGeom g,
                             uint32_t n_tiles, uint32_t* tile_off,
                             uint32_t* stats) {
-  const uint32_t row = rows[blockIdx.x];
-  const uint64_t beg = row_ptr[row];
-  const uint32_t len = (uint32_t)(row_ptr[row + 1] - beg);
-  uint64_t* a = scratch + scratch_off[blockIdx.x];
-  const uint32_t P = pow2_ceil(len);
-  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
-    a[i] = i < len ? keys[beg + i] : ~0ull;
-  __syncthreads();
-  bitonic(a, P);
-  pack_row<FMT, WMODE>(a, len, row, beg, recs, b, edge_w, g, n_tiles,
-                       tile_off, stats);
+  for (uint32_t j = blockIdx.x; j < n_long; j += gridDim.x) {
+    const uint32_t row = rows[j];
+    const uint64_t beg = row_ptr[row];
+    const uint32_t len = (uint32_t)(row_ptr[row + 1] - beg);
+    uint64_t* a = scratch + scratch_off[j];
+    const uint32_t P = pow2_ceil(len);
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+      a[i] = i < len ? keys[beg + i] : ~0ull;
+    __syncthreads();
+    bitonic(a, P);
+    pack_row<FMT, WMODE>(a, len, row, beg, recs, b, edge_w, g, n_tiles,
+                         tile_off, stats);
+    __syncthreads();
+  }
 }
 
 template <int FMT>
@@ -300,6 +309,48 @@ unsigned grid_for(uint64_t n, unsigned threads) {
   return b ? (unsigned)b : 1u;
 }
 
+// Build mode of the calling thread, set around a build by the API
+// (snn_params.build_yield).
+thread_local unsigned t_build_yield = 0;
+
+// Launch shape of a build kernel.  Normal: the kernel's own grid.
+// Yielding: the same grid of short CTAs (one target or one row each), but of
+// 1024 threads and with more than half of an SM's shared memory, so that no
+// two share an SM.  Each SM then becomes entirely free whenever one of its
+// build CTAs ends (every few to a few hundred microseconds), and the CTA
+// scheduler hands it to pending work of higher-priority streams first: the
+// kernels of running nets, whose delivery CTAs need a whole SM and would
+// otherwise wait for the build to end, since small build CTAs keep refilling
+// partly free SMs.
+struct BuildShape {
+  unsigned blocks, threads;
+  size_t smem;
+};
+
+template <class Kernel>
+cudaError_t build_shape(Kernel kernel, unsigned blocks, unsigned threads,
+                        size_t smem, BuildShape* out) {
+  *out = BuildShape{blocks, threads, smem};
+  int dev = 0, per_sm = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  // the kernel's dynamic shared-memory limit is always raised to the whole
+  // opt-in amount: one value for every caller, so that builds on several
+  // host threads never lower it under one another's launch
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin);
+  if (e != cudaSuccess) return e;
+  if (!t_build_yield) return cudaSuccess;
+  const size_t excl = std::min<size_t>((size_t)per_sm / 2 + 2048, (size_t)optin);
+  out->threads = threads > 1024 ? threads : 1024;
+  out->smem = std::max(smem, excl);
+  return cudaSuccess;
+}
+
 template <int FMT, int WMODE>
 cudaError_t sort_pack_t(uint32_t n, const uint64_t* row_ptr, uint64_t* keys,
                         void* recs, const BuildFixed* b, const double* edge_w,
@@ -312,30 +363,41 @@ cudaError_t sort_pack_t(uint32_t n, const uint64_t* row_ptr, uint64_t* keys,
   uint32_t P = 1;
   while (P < cap) P <<= 1;
   size_t smem = (size_t)P * sizeof(uint64_t);
-  cudaError_t e = cudaFuncSetAttribute(
-      k_sort_pack<FMT, WMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)smem);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   unsigned threads = P >= 1024 ? 1024 : (P >= 128 ? P : 128);
   unsigned blocks = n < (1u << 20) ? n : (1u << 20);
-  if (blocks)
-    k_sort_pack<FMT, WMODE><<<blocks, threads, smem, s>>>(
+  BuildShape sh;
+  if (blocks) {
+    if ((e = build_shape(k_sort_pack<FMT, WMODE>, blocks, threads, smem, &sh)) !=
+        cudaSuccess)
+      return e;
+    k_sort_pack<FMT, WMODE><<<sh.blocks, sh.threads, sh.smem, s>>>(
         n, row_ptr, keys, recs, bb, edge_w, kSortCap, g, n_tiles, tile_off,
         stats);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (n_long)
-    k_sort_long<FMT, WMODE><<<n_long, 1024, 0, s>>>(
-        long_rows, row_ptr, keys, recs, bb, edge_w, long_scratch, long_off, g,
-        n_tiles, tile_off, stats);
+  if (n_long) {
+    if ((e = build_shape(k_sort_long<FMT, WMODE>, n_long, 1024, 0, &sh)) !=
+        cudaSuccess)
+      return e;
+    k_sort_long<FMT, WMODE><<<sh.blocks, sh.threads, sh.smem, s>>>(
+        long_rows, n_long, row_ptr, keys, recs, bb, edge_w, long_scratch,
+        long_off, g, n_tiles, tile_off, stats);
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
+void set_build_yield(unsigned on) { t_build_yield = on; }
+
 cudaError_t build_count_fixed(const BuildFixed& b, uint32_t* deg,
                               cudaStream_t s) {
   if (b.n_tgt == 0 || b.k_e + b.k_i == 0) return cudaSuccess;
-  k_count_fixed<<<b.n_tgt, 256, 0, s>>>(b, deg);
+  BuildShape sh;
+  cudaError_t e = build_shape(k_count_fixed, b.n_tgt, 256, 0, &sh);
+  if (e != cudaSuccess) return e;
+  k_count_fixed<<<sh.blocks, sh.threads, sh.smem, s>>>(b, deg);
   return cudaGetLastError();
 }
 
@@ -343,8 +405,11 @@ cudaError_t build_scatter_fixed(const BuildFixed& b, const uint64_t* row_ptr,
                                 uint32_t* cursor, uint64_t* keys,
                                 uint32_t tile_w, int lo_bits, cudaStream_t s) {
   if (b.n_tgt == 0 || b.k_e + b.k_i == 0) return cudaSuccess;
-  k_scatter_fixed<<<b.n_tgt, 256, 0, s>>>(b, row_ptr, cursor, keys,
-                                    TileGeom{tile_w, lo_bits});
+  BuildShape sh;
+  cudaError_t e = build_shape(k_scatter_fixed, b.n_tgt, 256, 0, &sh);
+  if (e != cudaSuccess) return e;
+  k_scatter_fixed<<<sh.blocks, sh.threads, sh.smem, s>>>(
+      b, row_ptr, cursor, keys, TileGeom{tile_w, lo_bits});
   return cudaGetLastError();
 }
 
@@ -402,12 +467,21 @@ cudaError_t unpack_store(int fmt, const void* recs, uint64_t n_syn,
 cudaError_t delay_range(int fmt, const void* recs, uint64_t n_syn,
                         unsigned int* dmin_dmax, cudaStream_t s) {
   if (n_syn == 0) return cudaSuccess;
-  if (fmt == SNN_W_FP32_12B)
-    k_delay_range<SNN_W_FP32_12B><<<grid_for(n_syn, 256), 256, 0, s>>>(
+  BuildShape sh;
+  cudaError_t e;
+  if (fmt == SNN_W_FP32_12B) {
+    if ((e = build_shape(k_delay_range<SNN_W_FP32_12B>, grid_for(n_syn, 256), 256,
+                         0, &sh)) != cudaSuccess)
+      return e;
+    k_delay_range<SNN_W_FP32_12B><<<sh.blocks, sh.threads, sh.smem, s>>>(
         recs, n_syn, dmin_dmax);
-  else
-    k_delay_range<SNN_W_BF16_8B><<<grid_for(n_syn, 256), 256, 0, s>>>(
+  } else {
+    if ((e = build_shape(k_delay_range<SNN_W_BF16_8B>, grid_for(n_syn, 256), 256,
+                         0, &sh)) != cudaSuccess)
+      return e;
+    k_delay_range<SNN_W_BF16_8B><<<sh.blocks, sh.threads, sh.smem, s>>>(
         recs, n_syn, dmin_dmax);
+  }
   return cudaGetLastError();
 }
 

@@ -307,6 +307,9 @@ struct BuildFixed {
   uint64_t seed;
   int clip_e, clip_i;
 };
+// Build kernels launched by the calling thread run as short whole-SM CTAs
+// (1) or in their normal shape (0); see snn_params.build_yield.
+void set_build_yield(unsigned on);
 cudaError_t build_count_fixed(const BuildFixed& b, uint32_t* deg,
                               cudaStream_t s);
 cudaError_t build_scatter_fixed(const BuildFixed& b, const uint64_t* row_ptr,

@@ -22,6 +22,11 @@ void tile_geometry(uint32_t n, int window, int32_t hint, uint32_t* tile_w,
 // the last use.
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
 void pool_free(void* p, cudaStream_t s);
+// Keep (+1) or let go (-1) of the device's pool: while held, memory freed by
+// destroyed nets stays in the pool for the next ones (a server holds it for
+// its lifetime, so that admitting a request never waits for memory to be
+// mapped again).
+void pool_hold(int dev, int delta);
 }  // namespace snn
 
 // The net: parameters, device buffers and host bookkeeping.

@@ -22,6 +22,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -70,6 +71,9 @@ constexpr uint64_t kSynPerTile = 1ull << 22;
 constexpr uint64_t kServeMaxTiles = 120;
 // Graphs cached per lane for steps of 2^1 .. 2^kMaxGraphLog intervals.
 constexpr int kMaxGraphLog = 4;
+// Device memory mapped into the pool when a server is created (at most its
+// budget).
+constexpr uint64_t kPoolWarmBytes = 64ull << 30;
 // Lanes by synapse count: below 2^24, below 2^27, and the rest.
 constexpr int kLanes = 3;
 constexpr uint64_t kLaneBound[kLanes - 1] = {1ull << 24, 1ull << 27};
@@ -92,21 +96,44 @@ struct Req {
 
 }  // namespace
 
-// One lane: a batch of running nets advanced together on its own stream.
-struct Lane {
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  std::vector<Req*> active;
-  std::vector<int> active_steps;       // n_steps per net in the tables
+// Device tables of one batch shape: each net's view and constants, and the
+// block maps of the batched update and delivery launches; with the graphs
+// captured for them.  A lane keeps two, so that it rewrites one while steps
+// that read the other may still run.
+struct LaneTables {
   BatchNet* d_nets = nullptr;
   uint2* d_umap = nullptr;
   uint2* d_dmap = nullptr;
   size_t cap_nets = 0, cap_umap = 0, cap_dmap = 0;
   uint32_t n_ublocks = 0, n_dctas = 0;
   size_t dsmem = 0;
-  bool dirty = true;
-  // captured steps of 2, 4, 8 and 16 intervals for the current tables
+  // host copies, kept until the next rewrite (the copies to the device are
+  // asynchronous)
+  std::vector<BatchNet> h_nets;
+  std::vector<uint2> h_umap, h_dmap;
+  // captured steps of 2, 4, 8 and 16 intervals for these tables
   cudaGraphExec_t graph[kMaxGraphLog + 1] = {};
+  cudaEvent_t last_use = nullptr;  // after the last step that read them
+  bool used = false;
+};
+
+// One lane: a batch of running nets advanced together on its own stream.
+// Nothing in a lane's step waits for the GPU: a lane whose earlier work is
+// still needed (an event pair to reuse, tables to rewrite) is skipped for
+// that step, and finished nets are retired once the event recorded after
+// their last interval has completed.  One slow lane therefore never holds
+// up the stepping of the others.
+struct Lane {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<Req*> active;
+  std::vector<int> active_steps;       // n_steps per net in the tables
+  LaneTables tab[2];
+  int cur = 0;                         // tables of the current batch shape
+  bool dirty = true;
+  // nets whose last interval is launched, with the event after it
+  std::vector<std::pair<Req*, cudaEvent_t>> retiring;
+  std::vector<cudaEvent_t> spare_events;
   // GPU time per step: two event pairs used in turn, so that the host
   // prepares step k+1 while step k runs and reads step k's time afterwards
   cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -148,6 +175,11 @@ struct snn_server {
   uint64_t steps = 0;
 
   std::thread builder[2];
+  bool holds_pool = false;
+  // builds in flight: while any runs, the stepping thread instantiates no
+  // CUDA graph (instantiation waits for the build's kernels; it launches
+  // the intervals directly meanwhile, or replays a graph it already has)
+  std::atomic<int> building{0};
 };
 
 namespace {
@@ -215,6 +247,9 @@ void builder_main(snn_server* sv, int cls) {
     sv->used += q.est;
     snn_request r = q.r;
     r.params.stream_priority = prio_least;
+    // builds hand SMs back to the running nets every few microseconds
+    r.params.build_yield = 1;
+    sv->building.fetch_add(1);
     lk.unlock();
     // build outside the lock, on the net's own stream
     snn_net* net = nullptr;
@@ -225,6 +260,7 @@ void builder_main(snn_server* sv, int cls) {
                           net->p.deliver_mode == SNN_DELIVER_TILED))
       rc = SNN_E_ARG;
     if (rc == SNN_OK) rc = snn_sync(net);
+    sv->building.fetch_sub(1);
     lk.lock();
     Req& q2 = sv->reqs[id];
     if (rc == SNN_OK) {
@@ -261,57 +297,76 @@ int lane_of(const snn_net* net) {
   return k;
 }
 
-// Rebuild a lane's batch table and block maps for its active nets.
-int rebuild_tables(Lane* ln) {
-  // earlier steps may still read the tables: finish them first
-  SCK(cudaStreamSynchronize(ln->stream));
-  std::vector<BatchNet> nets(ln->active.size());
-  std::vector<uint2> umap, dmap;
+// Whether the GPU work recorded by event e (nullptr: none) has completed.
+int event_done(cudaEvent_t e, bool* done) {
+  *done = true;
+  if (!e) return SNN_OK;
+  const cudaError_t q = cudaEventQuery(e);
+  if (q == cudaErrorNotReady) {
+    *done = false;
+    return SNN_OK;
+  }
+  SCK(q);
+  return SNN_OK;
+}
+
+// Write the lane's active nets into its other table set (if no running step
+// still reads that set; else *busy = true and nothing changes).
+int rebuild_tables(Lane* ln, bool* busy) {
+  LaneTables& t = ln->tab[ln->cur ^ 1];
+  int rc;
+  bool done = true;
+  if (t.used && (rc = event_done(t.last_use, &done)) != SNN_OK) return rc;
+  *busy = !done;
+  if (!done) return SNN_OK;
+  t.h_nets.assign(ln->active.size(), BatchNet{});
+  t.h_umap.clear();
+  t.h_dmap.clear();
   size_t smem = 0;
   const uint32_t ut = update_threads();
   for (size_t k = 0; k < ln->active.size(); ++k) {
     snn_net* net = ln->active[k]->net;
-    nets[k].v = net->view();
-    nets[k].c = net->uc;
-    nets[k].n_steps = ln->active_steps[k];
-    nets[k].pad_ = 0;
+    t.h_nets[k].v = net->view();
+    t.h_nets[k].c = net->uc;
+    t.h_nets[k].n_steps = ln->active_steps[k];
+    t.h_nets[k].pad_ = 0;
     const uint32_t nb = (net->n + ut - 1) / ut;
-    for (uint32_t b = 0; b < nb; ++b) umap.push_back(make_uint2((uint32_t)k, b));
-    for (uint32_t t = 0; t < net->n_tiles; ++t)
-      dmap.push_back(make_uint2((uint32_t)k, t));
-    smem = std::max(smem, tiled_smem_bytes(nets[k].v));
+    for (uint32_t b = 0; b < nb; ++b) t.h_umap.push_back(make_uint2((uint32_t)k, b));
+    for (uint32_t tl = 0; tl < net->n_tiles; ++tl)
+      t.h_dmap.push_back(make_uint2((uint32_t)k, tl));
+    smem = std::max(smem, tiled_smem_bytes(t.h_nets[k].v));
   }
-  int rc;
-  if ((rc = ensure_dev(&ln->d_nets, &ln->cap_nets, nets.size(), ln->stream)) != SNN_OK)
+  if ((rc = ensure_dev(&t.d_nets, &t.cap_nets, t.h_nets.size(), ln->stream)) != SNN_OK)
     return rc;
-  if ((rc = ensure_dev(&ln->d_umap, &ln->cap_umap, umap.size(), ln->stream)) != SNN_OK)
+  if ((rc = ensure_dev(&t.d_umap, &t.cap_umap, t.h_umap.size(), ln->stream)) != SNN_OK)
     return rc;
-  if ((rc = ensure_dev(&ln->d_dmap, &ln->cap_dmap, dmap.size(), ln->stream)) != SNN_OK)
+  if ((rc = ensure_dev(&t.d_dmap, &t.cap_dmap, t.h_dmap.size(), ln->stream)) != SNN_OK)
     return rc;
-  SCK(cudaMemcpyAsync(ln->d_nets, nets.data(), nets.size() * sizeof(BatchNet),
+  SCK(cudaMemcpyAsync(t.d_nets, t.h_nets.data(), t.h_nets.size() * sizeof(BatchNet),
                       cudaMemcpyHostToDevice, ln->stream));
-  SCK(cudaMemcpyAsync(ln->d_umap, umap.data(), umap.size() * sizeof(uint2),
+  SCK(cudaMemcpyAsync(t.d_umap, t.h_umap.data(), t.h_umap.size() * sizeof(uint2),
                       cudaMemcpyHostToDevice, ln->stream));
-  SCK(cudaMemcpyAsync(ln->d_dmap, dmap.data(), dmap.size() * sizeof(uint2),
+  SCK(cudaMemcpyAsync(t.d_dmap, t.h_dmap.data(), t.h_dmap.size() * sizeof(uint2),
                       cudaMemcpyHostToDevice, ln->stream));
-  SCK(cudaStreamSynchronize(ln->stream));  // host vectors go out of scope
-  ln->n_ublocks = (uint32_t)umap.size();
-  ln->n_dctas = (uint32_t)dmap.size();
-  ln->dsmem = smem;
-  for (cudaGraphExec_t& g : ln->graph)
+  t.n_ublocks = (uint32_t)t.h_umap.size();
+  t.n_dctas = (uint32_t)t.h_dmap.size();
+  t.dsmem = smem;
+  for (cudaGraphExec_t& g : t.graph)
     if (g) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  ln->cur ^= 1;
   ln->dirty = false;
   return SNN_OK;
 }
 
 int launch_intervals(Lane* ln, int fmt, int m) {
+  const LaneTables& t = ln->tab[ln->cur];
   for (int i = 0; i < m; ++i) {
-    SCK(launch_update_batch(ln->d_nets, ln->d_umap, ln->n_ublocks, ln->stream));
-    SCK(launch_deliver_tiled_batch(fmt, ln->d_nets, ln->d_dmap, ln->n_dctas,
-                                   ln->dsmem, ln->stream));
+    SCK(launch_update_batch(t.d_nets, t.d_umap, t.n_ublocks, ln->stream));
+    SCK(launch_deliver_tiled_batch(fmt, t.d_nets, t.d_dmap, t.n_dctas, t.dsmem,
+                                   ln->stream));
   }
   return SNN_OK;
 }
@@ -323,21 +378,26 @@ int log2_of(int m) {
 }
 
 // The lane's graph of m intervals (m a power of two, 2 .. 2^kMaxGraphLog),
-// captured on first use for the current tables.
-int graph_for(Lane* ln, int fmt, int m, cudaGraphExec_t* out) {
+// captured on first use for the current tables; *out = nullptr (launch the
+// intervals directly) when it is not there yet and may_instantiate is false.
+int graph_for(Lane* ln, int fmt, int m, bool may_instantiate,
+              cudaGraphExec_t* out) {
   const int l = log2_of(m);
-  if (!ln->graph[l]) {
+  cudaGraphExec_t* slot = &ln->tab[ln->cur].graph[l];
+  *out = nullptr;
+  if (!*slot && !may_instantiate) return SNN_OK;
+  if (!*slot) {
     cudaGraph_t g;
     SCK(cudaStreamBeginCapture(ln->stream, cudaStreamCaptureModeThreadLocal));
     int rc = launch_intervals(ln, fmt, m);
     cudaError_t e = cudaStreamEndCapture(ln->stream, &g);
     if (rc != SNN_OK) return rc;
     SCK(e);
-    e = cudaGraphInstantiate(&ln->graph[l], g, 0);
+    e = cudaGraphInstantiate(slot, g, 0);
     cudaGraphDestroy(g);
     SCK(e);
   }
-  *out = ln->graph[l];
+  *out = *slot;
   return SNN_OK;
 }
 
@@ -363,17 +423,13 @@ void tune_observe(Lane* ln, double ms, int m) {
   }
 }
 
-// Add the GPU time of the step recorded in event pair `slot` if it has
-// finished (or wait for it when `wait`).
-int fold_step_time(Lane* ln, int slot, bool wait) {
+// Add the GPU time of the step recorded in event pair `slot` once it has
+// finished; *done = false while it runs.
+int fold_step_time(Lane* ln, int slot, bool* done) {
+  *done = true;
   if (!ln->ev_pending[slot]) return SNN_OK;
-  if (wait) {
-    SCK(cudaEventSynchronize(ln->ev[slot][1]));
-  } else {
-    const cudaError_t q = cudaEventQuery(ln->ev[slot][1]);
-    if (q == cudaErrorNotReady) return SNN_OK;
-    SCK(q);
-  }
+  int rc;
+  if ((rc = event_done(ln->ev[slot][1], done)) != SNN_OK || !*done) return rc;
   float ms = 0;
   SCK(cudaEventElapsedTime(&ms, ln->ev[slot][0], ln->ev[slot][1]));
   ln->gpu_ms += ms;
@@ -381,14 +437,24 @@ int fold_step_time(Lane* ln, int slot, bool wait) {
   return SNN_OK;
 }
 
-int retire(snn_server* sv, Lane* ln, std::vector<Req*>& finished) {
-  if (finished.empty()) return SNN_OK;
-  SCK(cudaStreamSynchronize(ln->stream));
-  for (Req* q : finished) {
+// Retire the lane's finished nets whose last interval has completed: read
+// their counters and spikes, free them, publish the results.
+int retire_done(snn_server* sv, Lane* ln) {
+  std::vector<std::pair<Req*, cudaEvent_t>> keep;
+  for (auto& fe : ln->retiring) {
+    bool done = true;
+    int rc = event_done(fe.second, &done);
+    if (rc != SNN_OK) return rc;
+    if (!done) {
+      keep.push_back(fe);
+      continue;
+    }
+    ln->spare_events.push_back(fe.second);
+    Req* q = fe.first;
     snn_net* net = q->net;
     const bool rec = q->r.record_spikes != 0;
     snn_stats st;
-    int rc = snn_get_stats(net, &st);
+    rc = snn_get_stats(net, &st);
     std::vector<uint32_t> src;
     std::vector<int32_t> t;
     if (rc == SNN_OK && rec && net->log_cap) {
@@ -420,22 +486,29 @@ int retire(snn_server* sv, Lane* ln, std::vector<Req*>& finished) {
       q->res.error = rc;
       sv->failed += 1;
     }
+    sv->cv.notify_all();
   }
-  sv->cv.notify_all();
+  ln->retiring.swap(keep);
   return SNN_OK;
 }
 
-// One step of one lane: launch its nets' next intervals (several in one
-// graph when the autotuner chose so), then retire the nets that finished.
+// One step of one lane: retire what finished, then launch its nets' next
+// intervals (several in one graph when the autotuner chose so) unless the
+// GPU still needs the lane's event pair or its other table set.
 int lane_step(snn_server* sv, Lane* ln, bool* launched) {
   *launched = false;
   int rc;
+  if ((rc = retire_done(sv, ln)) != SNN_OK) return rc;
   // fold in the GPU time of finished steps, oldest first; the pair this
-  // step reuses must be finished
+  // step reuses must be finished, else the lane sits this step out
+  bool reuse_done = true;
   for (int k = 0; k < 2; ++k) {
     const int slot = ln->ev_cur ^ k;
-    if ((rc = fold_step_time(ln, slot, k == 0)) != SNN_OK) return rc;
+    bool done = true;
+    if ((rc = fold_step_time(ln, slot, &done)) != SNN_OK) return rc;
+    if (k == 0) reuse_done = done;
   }
+  if (!reuse_done) return SNN_OK;
   const double now = now_s();
   if (ln->t_last > 0 && ln->m_last > 0)
     tune_observe(ln, 1e3 * (now - ln->t_last), ln->m_last);
@@ -455,17 +528,27 @@ int lane_step(snn_server* sv, Lane* ln, bool* launched) {
       ln->dirty = true;
     }
   }
-  if (ln->dirty && (rc = rebuild_tables(ln)) != SNN_OK) return rc;
+  if (ln->dirty) {
+    bool busy = false;
+    if ((rc = rebuild_tables(ln, &busy)) != SNN_OK) return rc;
+    if (busy) return SNN_OK;
+  }
   cudaGraphExec_t gx = nullptr;
-  if (m > 1 && (rc = graph_for(ln, sv->fmt, m, &gx)) != SNN_OK) return rc;
+  if (m > 1 && (rc = graph_for(ln, sv->fmt, m, sv->building.load() == 0,
+                               &gx)) != SNN_OK)
+    return rc;
   const int slot = ln->ev_cur;
   SCK(cudaEventRecord(ln->ev[slot][0], ln->stream));
-  if (m > 1) {
+  if (gx) {
     SCK(cudaGraphLaunch(gx, ln->stream));
   } else {
-    if ((rc = launch_intervals(ln, sv->fmt, 1)) != SNN_OK) return rc;
+    if ((rc = launch_intervals(ln, sv->fmt, m)) != SNN_OK) return rc;
   }
   SCK(cudaEventRecord(ln->ev[slot][1], ln->stream));
+  LaneTables& tb = ln->tab[ln->cur];
+  if (!tb.last_use) SCK(cudaEventCreateWithFlags(&tb.last_use, cudaEventDisableTiming));
+  SCK(cudaEventRecord(tb.last_use, ln->stream));
+  tb.used = true;
   ln->ev_pending[slot] = true;
   ln->ev_m[slot] = m;
   ln->ev_cur ^= 1;
@@ -475,25 +558,35 @@ int lane_step(snn_server* sv, Lane* ln, bool* launched) {
   ln->intervals += m;
   ln->launches += 2ull * m;
   *launched = true;
-  // bookkeeping; retire nets that finished
-  std::vector<Req*> finished, keep;
+  // bookkeeping; nets that finished leave the batch and retire once this
+  // step has completed
+  std::vector<Req*> keep;
   std::vector<int> keep_steps;
+  bool any_done = false;
   for (size_t k = 0; k < ln->active.size(); ++k) {
     Req& q = *ln->active[k];
     q.steps_left -= (int64_t)m * ln->active_steps[k];
     if (q.steps_left <= 0) {
-      finished.push_back(ln->active[k]);
+      cudaEvent_t e = nullptr;
+      if (!ln->spare_events.empty()) {
+        e = ln->spare_events.back();
+        ln->spare_events.pop_back();
+      } else {
+        SCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      }
+      SCK(cudaEventRecord(e, ln->stream));
+      ln->retiring.emplace_back(ln->active[k], e);
+      any_done = true;
     } else {
       keep.push_back(ln->active[k]);
       keep_steps.push_back(ln->active_steps[k]);
     }
   }
-  if (!finished.empty()) {
+  if (any_done) {
     ln->active.swap(keep);
     ln->active_steps.swap(keep_steps);
     ln->dirty = true;
-    ln->t_last = 0;  // retiring (a synchronisation) is not a steady step
-    if ((rc = retire(sv, ln, finished)) != SNN_OK) return rc;
+    ln->t_last = 0;  // a change of batch is not a steady step
   }
   return SNN_OK;
 }
@@ -517,14 +610,32 @@ int snn_server_create(uint64_t mem_budget, int32_t weight_format, void* stream,
     delete sv;
     return sfail(SNN_E_CUDA, "no CUDA device");
   }
+  pool_hold(sv->device, +1);
+  sv->holds_pool = true;
+  {
+    // map the pool's memory up front (an allocation of the budget, freed at
+    // once, stays in the pool): growing it later, while requests are built,
+    // maps memory under the driver's locks and stalls the stepping thread's
+    // launches for the duration
+    const uint64_t warm = std::min<uint64_t>(mem_budget, kPoolWarmBytes);
+    void* p = nullptr;
+    if (pool_alloc(&p, warm, nullptr) == cudaSuccess) {
+      pool_free(p, nullptr);
+      cudaStreamSynchronize(nullptr);
+    } else {
+      cudaGetLastError();
+    }
+  }
   // smaller nets get higher stream priority: when SMs free up, the CTA
   // scheduler serves the short intervals of small nets first and the large
   // nets take the remaining capacity
   int prio_least = 0, prio_greatest = 0;
   cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  // (the builders take the least priority; every lane is above it)
+  const int lane_least = prio_greatest < prio_least ? prio_least - 1 : prio_least;
   for (int k = 0; k < kLanes; ++k) {
     Lane& ln = sv->lanes[k];
-    const int prio = prio_greatest + (prio_least - prio_greatest) * k / (kLanes - 1);
+    const int prio = prio_greatest + (lane_least - prio_greatest) * k / (kLanes - 1);
     if (k == 0 && stream) {
       ln.stream = static_cast<cudaStream_t>(stream);
     } else if (cudaStreamCreateWithPriority(&ln.stream, cudaStreamDefault, prio) !=
@@ -618,7 +729,7 @@ int snn_server_step(snn_server* sv, int32_t* n_active) {
     int rc = lane_step(sv, &sv->lanes[k], &launched);
     if (rc != SNN_OK) return rc;
     any = any || launched;
-    act += (int32_t)sv->lanes[k].active.size();
+    act += (int32_t)(sv->lanes[k].active.size() + sv->lanes[k].retiring.size());
   }
   if (any) sv->steps += 1;
   if (n_active) *n_active = act;
@@ -679,7 +790,7 @@ int snn_server_get_stats(snn_server* sv, snn_server_stats* out) {
   int tuned = 1, busiest = 0;
   for (int k = 0; k < kLanes; ++k) {
     const Lane& ln = sv->lanes[k];
-    out->active += ln.active.size();
+    out->active += ln.active.size() + ln.retiring.size();
     out->intervals += ln.intervals;
     out->kernel_launches += ln.launches;
     out->gpu_ms += ln.gpu_ms;
@@ -710,19 +821,27 @@ int snn_server_destroy(snn_server* sv) {
   for (auto& kv : sv->reqs)
     if (kv.second.net) snn_destroy(kv.second.net);
   for (Lane& ln : sv->lanes) {
-    for (cudaGraphExec_t g : ln.graph)
-      if (g) cudaGraphExecDestroy(g);
+    for (LaneTables& t : ln.tab) {
+      for (cudaGraphExec_t g : t.graph)
+        if (g) cudaGraphExecDestroy(g);
+      if (t.last_use) cudaEventDestroy(t.last_use);
+      if (ln.stream) {
+        pool_free(t.d_nets, ln.stream);
+        pool_free(t.d_umap, ln.stream);
+        pool_free(t.d_dmap, ln.stream);
+      }
+    }
+    for (auto& fe : ln.retiring) cudaEventDestroy(fe.second);
+    for (cudaEvent_t e : ln.spare_events) cudaEventDestroy(e);
     for (auto& pair : ln.ev)
       for (cudaEvent_t e : pair)
         if (e) cudaEventDestroy(e);
     if (ln.stream) {
-      pool_free(ln.d_nets, ln.stream);
-      pool_free(ln.d_umap, ln.stream);
-      pool_free(ln.d_dmap, ln.stream);
       cudaStreamSynchronize(ln.stream);
       if (ln.own_stream) cudaStreamDestroy(ln.stream);
     }
   }
+  if (sv->holds_pool) pool_hold(sv->device, -1);
   delete sv;
   return SNN_OK;
 }

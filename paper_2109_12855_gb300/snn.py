@@ -65,7 +65,7 @@ class snn_params(C.Structure):
                 ("deliver_mode", C.c_int32), ("spike_log_capacity", C.c_uint64),
                 ("tile_width", C.c_int32), ("stream_priority", C.c_int32),
                 ("part_lo", C.c_uint32), ("part_hi", C.c_uint32),
-                ("acc_words", C.c_int32), ("reserved_", C.c_int32)]
+                ("acc_words", C.c_int32), ("build_yield", C.c_int32)]
 
 
 class snn_conn_params(C.Structure):

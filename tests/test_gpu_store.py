@@ -5,7 +5,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from gpu_common import edge_net, fixed_net, need_gpu
+from gpu_common import edge_net, fixed_net, need_gpu, stream
 
 pytestmark = pytest.mark.gpu
 
@@ -118,3 +118,33 @@ def test_empty_store():
         assert st.n_synapses == 0 and st.interval == 32
         assert net.deliver([1, 2, 3], [0, 0, 5]) == 0
         assert not net.read_rb().any()
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_yielding_build_gives_the_same_store(fmt):
+    """build_yield (short whole-SM build CTAs, as a server's builds use)
+    changes the launch shape, not the store: fixed in-degree and edge-list
+    stores (with a segment longer than shared memory) equal the normal
+    build bit for bit."""
+    from paper_2109_12855_gb300 import snn
+    stores = []
+    for y in (0, 1):
+        p = snn.params(n_exc=4000, n_inh=1000, weight_format=fmt, build_yield=y)
+        with snn.Net(p, stream()) as net:
+            net.connect_fixed_indegree(snn.conn_params(
+                k_exc=400, k_inh=100, w_exc=22.4, w_inh=-112.0, sd_exc=2.0,
+                sd_inh=10.0, d_lo=10, d_hi=20, seed=5, clip_exc=1))
+            net.finalize()
+            stores.append(net.read_store() + (net.stats().tile_width,))
+        src, tgt, d, w = W.random_edges(3000, 40000, 1, 20, seed=9, hub=7,
+                                        hub_edges=20000)
+        p = snn.params(n_exc=3000, n_inh=0, weight_format=fmt, build_yield=y)
+        with snn.Net(p, stream()) as net:
+            net.connect_edges(src, tgt, d, w)
+            net.finalize()
+            stores.append(net.read_store())
+    fixed, edges = stores[0::2], stores[1::2]
+    for other in fixed[1:]:
+        assert all(np.array_equal(x, y) for x, y in zip(fixed[0], other))
+    for other in edges[1:]:
+        assert all(np.array_equal(x, y) for x, y in zip(edges[0], other))
