@@ -57,7 +57,7 @@ __device__ __forceinline__ uint32_t fixed_source(const BuildFixed& b,
 // One block per local target (the draws use its global index); a grid
 // smaller than the targets walks them in strides (a build confined to some
 // SMs, see BuildShape).
-__global__ void k_count_fixed(BuildFixed b, uint32_t* deg) {
+__global__ void __launch_bounds__(1024) k_count_fixed(BuildFixed b, uint32_t* deg) {
   const uint32_t kk = b.k_e + b.k_i;
   for (uint32_t tgt = blockIdx.x; tgt < b.n_tgt; tgt += gridDim.x)
     for (uint32_t k = threadIdx.x; k < kk; k += blockDim.x) {
@@ -66,7 +66,7 @@ __global__ void k_count_fixed(BuildFixed b, uint32_t* deg) {
     }
 }
 
-__global__ void k_scatter_fixed(BuildFixed b, const uint64_t* row_ptr,
+__global__ void __launch_bounds__(1024) k_scatter_fixed(BuildFixed b, const uint64_t* row_ptr,
                                 uint32_t* cursor, uint64_t* keys, TileGeom g) {
   const uint32_t kk = b.k_e + b.k_i;
   const uint32_t span = (uint32_t)(b.d_hi - b.d_lo + 1);
@@ -212,22 +212,112 @@ __device__ __forceinline__ uint32_t pow2_ceil(uint32_t x) {
   return p;
 }
 
+// Segments (keys of one target tile) up to this long are rank-sorted by a
+// warp in registers; a row with a longer one is sorted whole (bitonic).
+constexpr uint32_t kWarpSegMax = 256;
+// Rows of stores with more tiles than this are sorted whole.
+constexpr uint32_t kBucketTilesMax = 4096;
+
+// Sort one row of keys in shared memory (len keys at a[0..len), room for the
+// next power of two; cnt: n_tiles + 1 words): bucket by target tile
+// (histogram, exclusive scan, scatter from registers), then every warp
+// rank-sorts the short segments of the tiles it takes.  Keys are distinct,
+// so a key's rank in its segment is its position, and the result equals a
+// full sort of the row.  Falls back to the bitonic network when a segment
+// is longer than kWarpSegMax or the store has too many tiles.
+__device__ void sort_row(uint64_t* a, uint32_t len, uint32_t* cnt,
+                         uint32_t n_tiles, int lb) {
+  const uint32_t P = pow2_ceil(len);
+  bool whole = n_tiles > kBucketTilesMax || len > 16u * blockDim.x;
+  if (!whole) {
+    for (uint32_t t = threadIdx.x; t <= n_tiles; t += blockDim.x) cnt[t] = 0;
+    __syncthreads();
+    // keys of this thread (at most 16) into registers, tiles counted
+    uint64_t r[16];
+#pragma unroll
+    for (uint32_t q = 0; q < 16; ++q) {
+      const uint32_t i = threadIdx.x + q * blockDim.x;
+      if (i < len) {
+        r[q] = a[i];
+        atomicAdd(&cnt[(uint32_t)(r[q] >> (40 + lb))], 1u);
+      }
+    }
+    __syncthreads();
+    // longest segment, then the exclusive scan of the counts (one thread
+    // per block of counts: n_tiles is small)
+    __shared__ uint32_t s_max;
+    if (threadIdx.x == 0) {
+      uint32_t run = 0, mx = 0;
+      for (uint32_t t = 0; t <= n_tiles; ++t) {
+        const uint32_t c = cnt[t];
+        cnt[t] = run;
+        run += c;
+        mx = max(mx, c);
+      }
+      s_max = mx;
+    }
+    __syncthreads();
+    whole = s_max > kWarpSegMax;
+    // scatter into the buckets (cnt becomes each bucket's end)
+#pragma unroll
+    for (uint32_t q = 0; q < 16; ++q) {
+      const uint32_t i = threadIdx.x + q * blockDim.x;
+      if (i < len) {
+        const uint32_t pos = atomicAdd(&cnt[(uint32_t)(r[q] >> (40 + lb))], 1u);
+        a[pos] = r[q];
+      }
+    }
+    __syncthreads();
+    if (!whole) {
+      const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+      const uint32_t n_warps = blockDim.x >> 5;
+      for (uint32_t t = warp; t < n_tiles; t += n_warps) {
+        const uint32_t end = cnt[t];
+        const uint32_t beg = t == 0 ? 0u : cnt[t - 1];
+        const uint32_t c = end - beg;
+        if (c < 2) continue;
+        uint64_t key[kWarpSegMax / 32];
+        uint32_t rank[kWarpSegMax / 32];
+#pragma unroll
+        for (uint32_t q = 0; q < kWarpSegMax / 32; ++q) {
+          rank[q] = 0;
+          key[q] = lane + 32u * q < c ? a[beg + lane + 32u * q] : ~0ull;
+        }
+        for (uint32_t i = 0; i < c; ++i) {
+          const uint64_t y = a[beg + i];  // the same word for every lane
+#pragma unroll
+          for (uint32_t q = 0; q < kWarpSegMax / 32; ++q) rank[q] += y < key[q];
+        }
+        __syncwarp();
+#pragma unroll
+        for (uint32_t q = 0; q < kWarpSegMax / 32; ++q)
+          if (lane + 32u * q < c) a[beg + rank[q]] = key[q];
+        __syncwarp();
+      }
+      __syncthreads();
+      return;
+    }
+  }
+  for (uint32_t i = len + threadIdx.x; i < P; i += blockDim.x) a[i] = ~0ull;
+  __syncthreads();
+  if (P > 1) bitonic(a, P);
+}
+
 template <int FMT, int WMODE>
-__global__ void k_sort_pack(uint32_t n, const uint64_t* row_ptr,
+__global__ void __launch_bounds__(1024) k_sort_pack(uint32_t n, const uint64_t* row_ptr,
                             uint64_t* keys, void* recs, BuildFixed b,
                             const double* edge_w, uint32_t cap, TileGeom g,
                             uint32_t n_tiles, uint32_t* tile_off,
                             uint32_t* stats) {
   extern __shared__ uint64_t sk[];
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(sk + cap);
   for (uint32_t row = blockIdx.x; row < n; row += gridDim.x) {
     const uint64_t beg = row_ptr[row];
     const uint32_t len = (uint32_t)(row_ptr[row + 1] - beg);
     if (len > cap) continue;                 // uniform per block
-    const uint32_t P = pow2_ceil(len);
-    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
-      sk[i] = i < len ? keys[beg + i] : ~0ull;
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) sk[i] = keys[beg + i];
     __syncthreads();
-    if (P > 1) bitonic(sk, P);
+    if (len > 1) sort_row(sk, len, cnt, n_tiles, g.lb);
     pack_row<FMT, WMODE>(sk, len, row, beg, recs, b, edge_w, g, n_tiles,
                          tile_off, stats);
     __syncthreads();
@@ -235,7 +325,7 @@ __global__ void k_sort_pack(uint32_t n, const uint64_t* row_ptr,
 }
 
 template <int FMT, int WMODE>
-__global__ void k_sort_long(const uint32_t* rows, uint32_t n_long,
+__global__ void __launch_bounds__(1024) k_sort_long(const uint32_t* rows, uint32_t n_long,
                             const uint64_t* row_ptr,
                             uint64_t* keys, void* recs, BuildFixed b,
                             const double* edge_w, uint64_t* scratch,
@@ -283,7 +373,7 @@ __global__ void k_unpack(const void* recs, uint64_t n, uint32_t* tgt,
 }
 
 template <int FMT>
-__global__ void k_delay_range(const void* recs, uint64_t n, unsigned* out) {
+__global__ void __launch_bounds__(1024) k_delay_range(const void* recs, uint64_t n, unsigned* out) {
   unsigned lo = 0xFFFFFFFFu, hi = 0u;
   for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
        s += (uint64_t)gridDim.x * blockDim.x) {
@@ -338,14 +428,18 @@ cudaError_t build_shape(Kernel kernel, unsigned blocks, unsigned threads,
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  // the kernel's dynamic shared-memory limit is always raised to the whole
-  // opt-in amount: one value for every caller, so that builds on several
-  // host threads never lower it under one another's launch
+  // the kernel's dynamic shared-memory limit is always raised to all that
+  // its static shared memory leaves of the opt-in amount: one value for
+  // every caller, so that builds on several host threads never lower it
+  // under one another's launch
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return e;
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           optin);
+                           dyn_max);
   if (e != cudaSuccess) return e;
   if (!t_build_yield) return cudaSuccess;
-  const size_t excl = std::min<size_t>((size_t)per_sm / 2 + 2048, (size_t)optin);
+  const size_t excl = std::min<size_t>((size_t)per_sm / 2 + 2048, (size_t)dyn_max);
   out->threads = threads > 1024 ? threads : 1024;
   out->smem = std::max(smem, excl);
   return cudaSuccess;
@@ -362,7 +456,9 @@ cudaError_t sort_pack_t(uint32_t n, const uint64_t* row_ptr, uint64_t* keys,
   uint32_t cap = max_row < kSortCap ? max_row : kSortCap;
   uint32_t P = 1;
   while (P < cap) P <<= 1;
-  size_t smem = (size_t)P * sizeof(uint64_t);
+  // keys (room for the next power of two) and the tile buckets
+  size_t smem = (size_t)P * sizeof(uint64_t) +
+                (size_t)(std::min(n_tiles, kBucketTilesMax) + 1) * sizeof(uint32_t);
   cudaError_t e;
   unsigned threads = P >= 1024 ? 1024 : (P >= 128 ? P : 128);
   unsigned blocks = n < (1u << 20) ? n : (1u << 20);
@@ -372,8 +468,7 @@ cudaError_t sort_pack_t(uint32_t n, const uint64_t* row_ptr, uint64_t* keys,
         cudaSuccess)
       return e;
     k_sort_pack<FMT, WMODE><<<sh.blocks, sh.threads, sh.smem, s>>>(
-        n, row_ptr, keys, recs, bb, edge_w, kSortCap, g, n_tiles, tile_off,
-        stats);
+        n, row_ptr, keys, recs, bb, edge_w, P, g, n_tiles, tile_off, stats);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (n_long) {
