@@ -854,11 +854,13 @@ def _lat_stats(lat):
             "max_ms": float(a[-1]), "mean_ms": float(a.mean())}
 
 
-def serve_batched(snn, reqs, arrivals, budget, stream, clocks=None):
+def serve_batched(snn, reqs, arrivals, budget, stream, clocks=None,
+                  persistent=0):
     """Continuous batching: submit each request at its arrival time, step the
     server until every request finished.  Latency = completion - arrival."""
     sv = snn.snn_server_create(budget, reqs[0].params.weight_format, stream)
     try:
+        snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_PERSISTENT, persistent)
         ids, lag = [], []
         if clocks:
             clocks.start()
@@ -976,8 +978,10 @@ def run_serve(args, rate_hz, nu_ext):
     barrier()
     batched = serve_batched(snn, bf16, arrivals, budget, stream,
                             Clocks(gpu_index))
+    persist = serve_batched(snn, bf16, arrivals, budget, stream, persistent=1)
     serial = serve_serial(snn, fp32, arrivals, stream)
     sat_batched = serve_batched(snn, bf16, zero, budget, stream)
+    sat_persist = serve_batched(snn, bf16, zero, budget, stream, persistent=1)
     sat_serial_bf16 = serve_serial(snn, [r for r in serve_requests(
         snn, stream_reqs, 1, nu_ext, False, off)], zero, stream)
     sat_serial = serve_serial(snn, fp32, zero, stream)
@@ -1028,6 +1032,8 @@ def run_serve(args, rate_hz, nu_ext):
         "latency": batched["latency"],
         "serving": {
             "batched_bf16": {"events_per_s": rate(batched), **batched},
+            "batched_bf16_persistent": {"events_per_s": rate(persist),
+                                        **persist},
             "serial_fp32": {"events_per_s": rate(serial), **serial},
             "saturated": {
                 "batched_bf16": {"events_per_s": rate(sat_batched),
@@ -1035,6 +1041,10 @@ def run_serve(args, rate_hz, nu_ext):
                                  "latency": sat_batched["latency"],
                                  "intervals_per_step":
                                      sat_batched["intervals_per_step"]},
+                "batched_bf16_persistent": {
+                    "events_per_s": rate(sat_persist),
+                    "wall_s": sat_persist["wall_s"],
+                    "latency": sat_persist["latency"]},
                 "serial_bf16": {"events_per_s": rate(sat_serial_bf16),
                                 "wall_s": sat_serial_bf16["wall_s"],
                                 "latency": sat_serial_bf16["latency"]},

@@ -542,6 +542,32 @@ typedef struct snn_server_stats {
  * void* for the batched launches (NULL: an internal blocking stream). */
 int snn_server_create(uint64_t mem_budget, int32_t weight_format,
                       void* stream, snn_server** out);
+/* Serving options (snn_server_set_option):
+ *  SNN_SERVE_OPT_PERSISTENT  1: each snn_server_step is ONE launch
+ *    of a persistent kernel that advances every running net by its own
+ *    number of intervals: CTAs claim ready items -- a net's update blocks of
+ *    an interval, then its delivery tiles -- from per-net device queues, an
+ *    update once the net's previous delivery is complete, a delivery once
+ *    its update is; nets are served smallest first, each net runs as many
+ *    intervals as fit the step's target GPU time at its measured time per
+ *    interval, and the target is autotuned (0.25 - 2 ms).  While a large
+ *    request is being built, 16 SMs are left to the build.  0 (default): the
+ *    lanes of batched update and delivery launches described above, which
+ *    measure faster.  Changes only while no net runs (SNN_E_STATE
+ *    otherwise).
+ *  SNN_SERVE_OPT_SPIN_LIMIT  polls (32 to 256 ns apart) a CTA of the
+ *    persistent kernel makes while no item is ready before it gives up:
+ *    the launch then ends, the nets it ran fail with SNN_E_TIMEOUT
+ *    (default 2^20, a fraction of a second).
+ *  SNN_SERVE_OPT_STEP_US     target GPU time of a persistent step in
+ *    microseconds (0: autotuned). */
+enum {
+  SNN_SERVE_OPT_PERSISTENT = 0,
+  SNN_SERVE_OPT_SPIN_LIMIT = 1,
+  SNN_SERVE_OPT_STEP_US = 2
+};
+int snn_server_set_option(snn_server* sv, int32_t option, double value);
+
 /* Queue a request; *id identifies it.  Thread-safe.  SNN_E_ARG for invalid
  * parameters or a footprint above the whole budget.  A request with
  * params.tile_width == 0 gets delivery tiles in proportion to its synapses

@@ -258,6 +258,29 @@ struct BatchNet {
   int pad_;
 };
 
+// Progress of one net in one launch of the persistent serving kernel
+// (written by the host before the launch, counters zero).  The launch runs
+// iv intervals of the net; interval r is ub update items (blocks of the
+// update's threads) then nt delivery items (tiles); items are claimed in
+// order through `next`, an update item of interval r once del_done >= r nt,
+// a delivery item once upd_done >= (r + 1) ub.
+struct alignas(128) ServeNet {  // one cache line per net (polled by CTAs)
+  unsigned int next;          // next item to claim
+  unsigned int upd_done;      // update items finished
+  unsigned int del_done;      // delivery items finished
+  unsigned int n_items;       // iv (ub + nt)
+  unsigned int ub, nt, iv;
+  unsigned int pad_;
+  unsigned long long t_first; // globaltimer ns at the first claim
+  unsigned long long t_last;  // and at the latest completion
+};
+
+// Launch-wide state of the persistent serving kernel.
+struct ServeCtl {
+  unsigned int error;         // SNN_ERRF_TIMEOUT when a wait gave up
+  unsigned int pad_[31];
+};
+
 __device__ inline unsigned lane_id() { return threadIdx.x & 31u; }
 
 }  // namespace snn
@@ -294,6 +317,17 @@ cudaError_t launch_deliver_tiled_batch(int fmt, const BatchNet* nets,
                                        const uint2* bmap, uint32_t n_ctas,
                                        size_t smem, cudaStream_t s);
 uint32_t update_threads();
+// Threads of a persistent serving CTA (= neurons of one update item).
+uint32_t serve_threads();
+// The persistent serving kernel: every net of the table advances by its
+// ServeNet intervals; CTAs claim ready items until none is left.  A CTA that
+// finds nothing ready polls again up to spin_limit times (about 100 ns
+// apart), then sets ServeCtl.error and leaves, as do all others.  n_ctas:
+// the grid; smem: the largest accumulator of the nets.
+cudaError_t launch_serve(int fmt, const BatchNet* nets, ServeNet* sn,
+                         ServeCtl* ctl, uint32_t n_nets, uint32_t n_ctas,
+                         size_t smem, unsigned long long spin_limit,
+                         cudaStream_t s);
 cudaError_t launch_deliver_noalloc(const NetView& v, const uint32_t* src,
                                    const int32_t* t, uint32_t n,
                                    cudaStream_t s);

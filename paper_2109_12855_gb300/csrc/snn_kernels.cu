@@ -1184,6 +1184,129 @@ k_deliver_tiled_batch(const BatchNet* __restrict__ nets,
 }
 
 // ---------------------------------------------------------------------------
+// Persistent serving kernel: one launch advances every admitted net by its
+// own number of intervals.  Each net is a chain of items -- per interval its
+// update blocks, then its delivery tiles -- with the dependencies of the
+// time-driven cycle (Section 2.1): an interval's delivery reads the spike
+// list its update wrote, and the next update reads the ring buffer that
+// delivery filled.  A CTA claims the first ready item of the first net
+// (nets are ordered by size, smallest first) and runs it; so small nets
+// keep advancing while large ones take the remaining CTAs, and no net waits
+// for the pace of another.  Deadlock-free: an item is claimed only when its
+// dependencies have completed, and no item waits inside.  The only wait is
+// a CTA polling for a ready item; it gives up after spin_limit polls
+// (ServeCtl.error = SNN_ERRF_TIMEOUT), and every CTA then leaves.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned x;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(x) : "l"(p) : "memory");
+  return x;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The two kinds of item, compiled out of line (each keeps its own register
+// allocation instead of sharing one with the other and the claim loop).
+__device__ __noinline__ void serve_update(const NetView& v, const UpdConst& c,
+                                          int n_steps, uint32_t block) {
+  update_body<false>(v, c, n_steps, 1, 0, block);
+}
+template <int FMT>
+__device__ __noinline__ void serve_deliver(const NetView& v, uint32_t tile,
+                                           int* acc_mem, uint32_t desc_off,
+                                           uint32_t desc_cap) {
+  deliver_tile_body<FMT, false, false>(v, &v.ctl->pair, &v.ctl->done, v.list, 0,
+                                       1, tile, acc_mem, desc_off, desc_cap);
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(kTileThreads, 1)
+k_serve(const BatchNet* __restrict__ nets, ServeNet* sn, ServeCtl* ctl,
+        uint32_t n_nets, uint32_t desc_off, uint32_t desc_cap,
+        unsigned long long spin_limit) {
+  extern __shared__ __align__(16) int acc_mem[];
+  __shared__ UpdConst s_c;
+  __shared__ int s_state;      // 0: run s_net/s_item, 1: all claimed, 2: error
+  __shared__ uint32_t s_net, s_item;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int st = 1;
+      unsigned long long polls = 0;
+      unsigned nap = 32;  // ns between polls, doubling up to 256 while idle
+      for (;;) {
+        if (*reinterpret_cast<volatile unsigned*>(&ctl->error)) {
+          st = 2;
+          break;
+        }
+        bool left = false, got = false;
+        for (uint32_t j = 0; j < n_nets && !got; ++j) {
+          volatile ServeNet& q = sn[j];
+          const unsigned per = q.ub + q.nt, n_items = q.n_items;
+          for (;;) {
+            const unsigned k = q.next;
+            if (k >= n_items) break;
+            left = true;
+            const unsigned r = k / per, w = k - r * per;
+            const bool ready = w < q.ub ? q.del_done >= r * q.nt
+                                        : q.upd_done >= (r + 1) * q.ub;
+            if (!ready) break;
+            if (atomicCAS(&sn[j].next, k, k + 1) == k) {
+              if (k == 0) sn[j].t_first = global_ns();
+              s_net = j;
+              s_item = k;
+              got = true;
+              break;
+            }
+          }
+        }
+        if (got) {
+          st = 0;
+          break;
+        }
+        if (!left) break;  // every item of every net is claimed
+        if (++polls > spin_limit) {
+          atomicOr(&ctl->error, (unsigned)SNN_ERRF_TIMEOUT);
+          st = 2;
+          break;
+        }
+        __nanosleep(nap);
+        nap = nap < 256 ? 2 * nap : 256;
+      }
+      s_state = st;
+    }
+    __syncthreads();
+    if (s_state != 0) break;
+    const uint32_t j = s_net, k = s_item;
+    ServeNet& q = sn[j];
+    const unsigned per = q.ub + q.nt, r = k / per, w = k - r * per;
+    const bool upd = w < q.ub;
+    // every thread acquires what the item depends on (its writers released
+    // it with a fence before counting their item done)
+    ld_acquire_u32(upd ? &q.del_done : &q.upd_done);
+    const NetView& v = nets[j].v;
+    if (upd) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&nets[j].c);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_c);
+      for (uint32_t x = threadIdx.x; x < sizeof(UpdConst) / 4; x += blockDim.x)
+        dst[x] = src[x];
+      __syncthreads();
+      serve_update(v, s_c, nets[j].n_steps, w);
+    } else {
+      serve_deliver<FMT>(v, w - q.ub, acc_mem, desc_off, desc_cap);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicAdd(upd ? &q.upd_done : &q.del_done, 1u);
+      atomicMax(&q.t_last, global_ns());
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Caller's spike list -> entries with chunk prefix sums (one CTA).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
@@ -1536,6 +1659,31 @@ cudaError_t launch_deliver_tiled_batch(int fmt, const BatchNet* nets,
 }
 
 uint32_t update_threads() { return kUpdThreads; }
+
+uint32_t serve_threads() { return kTileThreads; }
+
+cudaError_t launch_serve(int fmt, const BatchNet* nets, ServeNet* sn,
+                         ServeCtl* ctl, uint32_t n_nets, uint32_t n_ctas,
+                         size_t smem, unsigned long long spin_limit,
+                         cudaStream_t s) {
+  if (n_nets == 0 || n_ctas == 0) return cudaSuccess;
+  static std::atomic<uint32_t> lim[2][64];
+  const int k = fmt == SNN_W_FP32_12B ? 0 : 1;
+  size_t dm = 0;
+  cudaError_t e = k == 0 ? allow_tile_smem(k_serve<SNN_W_FP32_12B>, lim[0], &dm)
+                         : allow_tile_smem(k_serve<SNN_W_BF16_8B>, lim[1], &dm);
+  if (e != cudaSuccess) return e;
+  DescLayout dl;  // after the largest accumulator of the nets
+  e = desc_layout(smem, dm, false, &dl);
+  if (e != cudaSuccess) return e;
+  if (k == 0)
+    k_serve<SNN_W_FP32_12B><<<n_ctas, kTileThreads, dl.smem, s>>>(
+        nets, sn, ctl, n_nets, dl.off, dl.cap, spin_limit);
+  else
+    k_serve<SNN_W_BF16_8B><<<n_ctas, kTileThreads, dl.smem, s>>>(
+        nets, sn, ctl, n_nets, dl.off, dl.cap, spin_limit);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_prepare_external(const NetView& v, const uint32_t* src,
                                     const int32_t* t, uint32_t n,

@@ -74,6 +74,17 @@ constexpr int kMaxGraphLog = 4;
 // Device memory mapped into the pool when a server is created (at most its
 // budget).
 constexpr uint64_t kPoolWarmBytes = 64ull << 30;
+// Persistent mode: the target GPU time of one step (one launch of the
+// persistent kernel), candidates of its autotuner in microseconds, polls of
+// a CTA that finds no ready item before it reports a timeout (32 to 256 ns
+// apart: a fraction of a second), and the SMs left to large builds while
+// one is in flight.
+constexpr double kStepUsCandidates[] = {250.0, 500.0, 1000.0, 2000.0};
+constexpr int kStepTuneSteps = 3;
+constexpr unsigned long long kSpinLimit = 1ull << 20;
+constexpr int kBuildReserveSms = 16;
+// Nets one persistent step runs at most (sizes its pinned host records).
+constexpr size_t kServeMaxNets = 4096;
 // Lanes by synapse count: below 2^24, below 2^27, and the rest.
 constexpr int kLanes = 3;
 constexpr uint64_t kLaneBound[kLanes - 1] = {1ull << 24, 1ull << 27};
@@ -92,6 +103,8 @@ struct Req {
   uint64_t est = 0;
   std::vector<uint32_t> sp_src;
   std::vector<int32_t> sp_t;
+  double iv_us = 0;      // persistent mode: measured time per interval
+  int fail_code = 0;     // non-zero: retire as failed (e.g. SNN_E_TIMEOUT)
 };
 
 }  // namespace
@@ -115,6 +128,7 @@ struct LaneTables {
   cudaGraphExec_t graph[kMaxGraphLog + 1] = {};
   cudaEvent_t last_use = nullptr;  // after the last step that read them
   bool used = false;
+  std::vector<uint32_t> ub, nt;    // persistent mode: items per interval
 };
 
 // One lane: a batch of running nets advanced together on its own stream.
@@ -151,6 +165,21 @@ struct Lane {
   int tune_best_m = 1;
   double t_last = 0;      // wall time of the lane's previous step (0: idle)
   int m_last = 0;         // intervals of that step
+  // persistent mode, per event-pair slot: the per-net launch records (host
+  // copy sent before the launch, device copy read back after it), the
+  // launch's error word, and the nets (with their interval counts) it ran
+  ServeNet* h_sn[2] = {nullptr, nullptr};
+  ServeNet* h_sn_back[2] = {nullptr, nullptr};
+  ServeCtl* h_ctl[2] = {nullptr, nullptr};
+  std::vector<std::pair<Req*, uint32_t>> step_nets[2];
+  ServeNet* d_sn = nullptr;
+  size_t cap_sn = 0;
+  ServeCtl* d_ctl = nullptr;
+  // autotuner of the step's target GPU time
+  double step_us = kStepUsCandidates[0];
+  int st_idx = 0, st_count = 0, st_tuned = 0;
+  double st_gpu = 0, st_wall = 0, st_best = -1;
+  double st_util[sizeof(kStepUsCandidates) / sizeof(double)] = {};
 };
 
 struct snn_server {
@@ -180,6 +209,11 @@ struct snn_server {
   // CUDA graph (instantiation waits for the build's kernels; it launches
   // the intervals directly meanwhile, or replays a graph it already has)
   std::atomic<int> building{0};
+  std::atomic<int> building_large{0};  // of which large requests
+  bool persistent = false;              // one persistent launch per step
+  unsigned long long spin_limit = kSpinLimit;
+  double step_us_fixed = 0;             // > 0: no autotuning
+  int sms = 1;
 };
 
 namespace {
@@ -187,13 +221,17 @@ namespace {
 // Device bytes a request will hold (the store with its build keys, tile
 // index, ring buffer, state, interval list, spike log), plus slack for the
 // allocator's granularity.
-int32_t serve_tile_width(const snn_request& r) {
+int32_t serve_tile_width(const snn_request& r, bool persistent) {
   const uint64_t n = (uint64_t)r.params.n_exc + r.params.n_inh;
   const uint64_t n_syn = n * ((uint64_t)r.conn.k_exc + r.conn.k_inh);
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   uint64_t tiles = (n_syn + kSynPerTile - 1) / kSynPerTile;
+  // the persistent kernel claims tiles one by one: a small net gets at
+  // least a few (of 32 neurons or more), so that its delivery spreads over
+  // several CTAs when the GPU has room
+  if (persistent) tiles = std::max<uint64_t>(tiles, std::min<uint64_t>(8, (n + 31) / 32));
   tiles = std::min<uint64_t>(std::max<uint64_t>(tiles, 1),
                              std::min<uint64_t>(kServeMaxTiles, std::max(sms, 1)));
   return (int32_t)std::min<uint64_t>((n + tiles - 1) / tiles, 1u << 30);
@@ -246,10 +284,13 @@ void builder_main(snn_server* sv, int cls) {
     q.res.t_admit = now_s() - sv->t0;
     sv->used += q.est;
     snn_request r = q.r;
-    r.params.stream_priority = prio_least;
+    // small builds (a few ms) run at the highest priority, so that small
+    // requests start at once; large builds at the lowest, below the lanes
+    r.params.stream_priority = cls == 0 ? prio_greatest : prio_least;
     // builds hand SMs back to the running nets every few microseconds
     r.params.build_yield = 1;
     sv->building.fetch_add(1);
+    if (cls == 1) sv->building_large.fetch_add(1);
     lk.unlock();
     // build outside the lock, on the net's own stream
     snn_net* net = nullptr;
@@ -261,6 +302,7 @@ void builder_main(snn_server* sv, int cls) {
       rc = SNN_E_ARG;
     if (rc == SNN_OK) rc = snn_sync(net);
     sv->building.fetch_sub(1);
+    if (cls == 1) sv->building_large.fetch_sub(1);
     lk.lock();
     Req& q2 = sv->reqs[id];
     if (rc == SNN_OK) {
@@ -335,6 +377,13 @@ int rebuild_tables(Lane* ln, bool* busy) {
     for (uint32_t tl = 0; tl < net->n_tiles; ++tl)
       t.h_dmap.push_back(make_uint2((uint32_t)k, tl));
     smem = std::max(smem, tiled_smem_bytes(t.h_nets[k].v));
+  }
+  t.ub.resize(ln->active.size());
+  t.nt.resize(ln->active.size());
+  for (size_t k = 0; k < ln->active.size(); ++k) {
+    const snn_net* net = ln->active[k]->net;
+    t.ub[k] = (net->n + serve_threads() - 1) / serve_threads();
+    t.nt[k] = net->n_tiles;
   }
   if ((rc = ensure_dev(&t.d_nets, &t.cap_nets, t.h_nets.size(), ln->stream)) != SNN_OK)
     return rc;
@@ -454,7 +503,7 @@ int retire_done(snn_server* sv, Lane* ln) {
     snn_net* net = q->net;
     const bool rec = q->r.record_spikes != 0;
     snn_stats st;
-    rc = snn_get_stats(net, &st);
+    rc = q->fail_code ? q->fail_code : snn_get_stats(net, &st);
     std::vector<uint32_t> src;
     std::vector<int32_t> t;
     if (rc == SNN_OK && rec && net->log_cap) {
@@ -591,6 +640,213 @@ int lane_step(snn_server* sv, Lane* ln, bool* launched) {
   return SNN_OK;
 }
 
+// Persistent mode: observe the GPU time of a finished step for the step
+// length autotuner (steady steps only), and move to the next candidate or
+// settle on the shortest step whose GPU utilisation (GPU time over wall
+// time) is within 5 % of the best.
+void tune_step_length(Lane* ln, double gpu_ms) {
+  if (ln->st_tuned) return;
+  const double now = now_s();
+  if (ln->st_count == 0) {
+    ln->st_wall = now;  // window start
+    ln->st_gpu = 0;
+  } else {
+    ln->st_gpu += gpu_ms;
+  }
+  if (++ln->st_count <= kStepTuneSteps) return;
+  const double util = ln->st_gpu / (1e3 * std::max(now - ln->st_wall, 1e-9));
+  constexpr int nc = (int)(sizeof(kStepUsCandidates) / sizeof(double));
+  if (ln->st_best < 0 || util > ln->st_best) ln->st_best = util;
+  ln->st_util[ln->st_idx] = util;
+  ln->st_count = 0;
+  if (++ln->st_idx < nc) {
+    ln->step_us = kStepUsCandidates[ln->st_idx];
+    return;
+  }
+  for (int c = 0; c < nc; ++c)
+    if (ln->st_util[c] >= 0.95 * ln->st_best) {
+      ln->step_us = kStepUsCandidates[c];
+      break;
+    }
+  ln->st_tuned = 1;
+}
+
+// Persistent mode: fold a finished step (GPU time; each net's measured time
+// per interval; a timeout fails the nets it ran).  *done = false while the
+// step runs.
+int fold_persistent(snn_server* sv, Lane* ln, int slot, bool* done) {
+  *done = true;
+  if (!ln->ev_pending[slot]) return SNN_OK;
+  int rc;
+  if ((rc = event_done(ln->ev[slot][1], done)) != SNN_OK || !*done) return rc;
+  float ms = 0;
+  SCK(cudaEventElapsedTime(&ms, ln->ev[slot][0], ln->ev[slot][1]));
+  ln->gpu_ms += ms;
+  ln->ev_pending[slot] = false;
+  const bool timeout = ln->h_ctl[slot]->error != 0;
+  auto& sn = ln->step_nets[slot];
+  for (size_t k = 0; k < sn.size(); ++k) {
+    Req* q = sn[k].first;
+    const ServeNet& b = ln->h_sn_back[slot][k];
+    if (b.iv && b.t_last > b.t_first) {
+      const double us = 1e-3 * (double)(b.t_last - b.t_first) / b.iv;
+      q->iv_us = q->iv_us > 0 ? 0.5 * (q->iv_us + us) : us;
+    }
+    if (timeout) q->fail_code = SNN_E_TIMEOUT;
+  }
+  if (timeout) {
+    // the nets of that step leave the batch and retire as failed
+    std::vector<Req*> keep;
+    std::vector<int> keep_steps;
+    for (size_t k = 0; k < ln->active.size(); ++k) {
+      Req* q = ln->active[k];
+      if (q->fail_code) {
+        cudaEvent_t e = nullptr;
+        SCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        SCK(cudaEventRecord(e, ln->stream));
+        ln->retiring.emplace_back(q, e);
+      } else {
+        keep.push_back(q);
+        keep_steps.push_back(ln->active_steps[k]);
+      }
+    }
+    ln->active.swap(keep);
+    ln->active_steps.swap(keep_steps);
+    ln->dirty = true;
+  } else if (ln->t_last > 0) {
+    tune_step_length(ln, ms);
+  }
+  sn.clear();
+  return SNN_OK;
+}
+
+// Persistent mode: one step = one launch of the persistent kernel that runs
+// every net's next intervals: as many as fit the target step time at the
+// net's measured time per interval (so small nets take many intervals while
+// a large net takes a few), all of one length (a net's last, shorter
+// interval runs alone in its step).  Nothing here waits for the GPU.
+int lane_step_persistent(snn_server* sv, Lane* ln, bool* launched) {
+  *launched = false;
+  int rc;
+  if ((rc = retire_done(sv, ln)) != SNN_OK) return rc;
+  bool reuse_done = true;
+  for (int k = 0; k < 2; ++k) {
+    const int slot = ln->ev_cur ^ k;
+    bool done = true;
+    if ((rc = fold_persistent(sv, ln, slot, &done)) != SNN_OK) return rc;
+    if (k == 0) reuse_done = done;
+  }
+  if (!reuse_done) return SNN_OK;
+  if (ln->active.empty()) {
+    ln->t_last = 0;
+    return SNN_OK;
+  }
+  const size_t n = ln->active.size();
+  SREQ(n <= kServeMaxNets, SNN_E_STATE, "more than %d running nets",
+       (int)kServeMaxNets);
+  std::vector<uint32_t> iv(n);
+  for (size_t k = 0; k < n; ++k) {
+    const Req& q = *ln->active[k];
+    const int D = q.net->interval;
+    int next = D;
+    if (q.steps_left < D) {
+      iv[k] = 1;
+      next = (int)q.steps_left;
+    } else {
+      const double est = q.iv_us > 0 ? q.iv_us
+                                     : 20.0 + 40.0 * (double)q.net->n_syn / 1.27e9;
+      const double want = std::max(1.0, std::floor(ln->step_us / est + 0.5));
+      iv[k] = (uint32_t)std::min<double>(want, (double)(q.steps_left / D));
+    }
+    if (ln->active_steps[k] != next) {
+      ln->active_steps[k] = next;
+      ln->dirty = true;
+    }
+  }
+  if (ln->dirty) {
+    bool busy = false;
+    if ((rc = rebuild_tables(ln, &busy)) != SNN_OK) return rc;
+    if (busy) return SNN_OK;
+  }
+  LaneTables& tb = ln->tab[ln->cur];
+  if (n > ln->cap_sn) {
+    pool_free(ln->d_sn, ln->stream);
+    ln->d_sn = nullptr;
+    ln->cap_sn = 0;
+    SCK(pool_alloc(reinterpret_cast<void**>(&ln->d_sn), kServeMaxNets * sizeof(ServeNet),
+                   ln->stream));
+    ln->cap_sn = kServeMaxNets;
+  }
+  const int slot = ln->ev_cur;
+  ServeNet* h = ln->h_sn[slot];
+  auto& sn = ln->step_nets[slot];
+  sn.clear();
+  for (size_t k = 0; k < n; ++k) {
+    ServeNet e{};
+    e.ub = tb.ub[k];
+    e.nt = tb.nt[k];
+    e.iv = iv[k];
+    e.n_items = iv[k] * (e.ub + e.nt);
+    h[k] = e;
+    sn.emplace_back(ln->active[k], iv[k]);
+  }
+  SCK(cudaMemcpyAsync(ln->d_sn, h, n * sizeof(ServeNet), cudaMemcpyHostToDevice,
+                      ln->stream));
+  SCK(cudaMemsetAsync(ln->d_ctl, 0, sizeof(ServeCtl), ln->stream));
+  SCK(cudaEventRecord(ln->ev[slot][0], ln->stream));
+  // while a large build runs, some SMs stay free for its kernels (small
+  // builds run at a higher priority and need no reserve)
+  const int ctas =
+      std::max(1, sv->sms - (sv->building_large.load() ? kBuildReserveSms : 0));
+  SCK(launch_serve(sv->fmt, tb.d_nets, ln->d_sn, ln->d_ctl, (uint32_t)n,
+                   (uint32_t)ctas, tb.dsmem, sv->spin_limit, ln->stream));
+  SCK(cudaMemcpyAsync(ln->h_sn_back[slot], ln->d_sn, n * sizeof(ServeNet),
+                      cudaMemcpyDeviceToHost, ln->stream));
+  SCK(cudaMemcpyAsync(ln->h_ctl[slot], ln->d_ctl, sizeof(ServeCtl),
+                      cudaMemcpyDeviceToHost, ln->stream));
+  SCK(cudaEventRecord(ln->ev[slot][1], ln->stream));
+  if (!tb.last_use) SCK(cudaEventCreateWithFlags(&tb.last_use, cudaEventDisableTiming));
+  SCK(cudaEventRecord(tb.last_use, ln->stream));
+  tb.used = true;
+  ln->ev_pending[slot] = true;
+  ln->ev_m[slot] = 1;
+  ln->ev_cur ^= 1;
+  if (ln->t_last == 0) ln->t_last = now_s();
+  ln->steps += 1;
+  ln->launches += 1;
+  *launched = true;
+  // bookkeeping: intervals counted, finished nets retire after this step
+  std::vector<Req*> keep;
+  std::vector<int> keep_steps;
+  bool any_done = false;
+  for (size_t k = 0; k < n; ++k) {
+    Req& q = *ln->active[k];
+    ln->intervals += iv[k];
+    q.steps_left -= (int64_t)iv[k] * ln->active_steps[k];
+    if (q.steps_left <= 0) {
+      cudaEvent_t e = nullptr;
+      if (!ln->spare_events.empty()) {
+        e = ln->spare_events.back();
+        ln->spare_events.pop_back();
+      } else {
+        SCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      }
+      SCK(cudaEventRecord(e, ln->stream));
+      ln->retiring.emplace_back(ln->active[k], e);
+      any_done = true;
+    } else {
+      keep.push_back(ln->active[k]);
+      keep_steps.push_back(ln->active_steps[k]);
+    }
+  }
+  if (any_done) {
+    ln->active.swap(keep);
+    ln->active_steps.swap(keep_steps);
+    ln->dirty = true;
+  }
+  return SNN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -612,6 +868,8 @@ int snn_server_create(uint64_t mem_budget, int32_t weight_format, void* stream,
   }
   pool_hold(sv->device, +1);
   sv->holds_pool = true;
+  cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, sv->device);
+  if (sv->sms < 1) sv->sms = 1;
   {
     // map the pool's memory up front (an allocation of the budget, freed at
     // once, stays in the pool): growing it later, while requests are built,
@@ -652,11 +910,63 @@ int snn_server_create(uint64_t mem_budget, int32_t weight_format, void* stream,
           return sfail(SNN_E_CUDA, "event creation failed");
         }
     ln.ips = kTuneCandidates[0];
+    if (k == 0) {
+      // persistent-mode records (page-locked: copied asynchronously)
+      for (int sl = 0; sl < 2; ++sl)
+        if (cudaHostAlloc(&ln.h_sn[sl], kServeMaxNets * sizeof(ServeNet), 0) != cudaSuccess ||
+            cudaHostAlloc(&ln.h_sn_back[sl], kServeMaxNets * sizeof(ServeNet), 0) != cudaSuccess ||
+            cudaHostAlloc(&ln.h_ctl[sl], sizeof(ServeCtl), 0) != cudaSuccess) {
+          snn_server_destroy(sv);
+          return sfail(SNN_E_OOM, "page-locked host allocation failed");
+        }
+      if (pool_alloc(reinterpret_cast<void**>(&ln.d_ctl), sizeof(ServeCtl), ln.stream) !=
+          cudaSuccess) {
+        snn_server_destroy(sv);
+        return sfail(SNN_E_OOM, "device allocation failed");
+      }
+    }
   }
   sv->builder[0] = std::thread(builder_main, sv, 0);
   sv->builder[1] = std::thread(builder_main, sv, 1);
   *out = sv;
   return SNN_OK;
+}
+
+int snn_server_set_option(snn_server* sv, int32_t option, double value) {
+  SREQ(sv, SNN_E_ARG, "null server");
+  switch (option) {
+    case SNN_SERVE_OPT_PERSISTENT: {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      bool idle = sv->ready.empty();
+      for (const Lane& ln : sv->lanes)
+        idle = idle && ln.active.empty() && ln.retiring.empty();
+      SREQ(idle, SNN_E_STATE, "the serving mode changes only while no net runs");
+      SREQ(value == 0 || value == 1, SNN_E_ARG, "persistent must be 0 or 1");
+      sv->persistent = value != 0;
+      return SNN_OK;
+    }
+    case SNN_SERVE_OPT_SPIN_LIMIT:
+      SREQ(value >= 1 && value <= 1e15, SNN_E_ARG, "spin limit out of range");
+      sv->spin_limit = (unsigned long long)value;
+      return SNN_OK;
+    case SNN_SERVE_OPT_STEP_US:
+      SREQ(value >= 0 && value <= 1e6, SNN_E_ARG, "step length out of range");
+      sv->step_us_fixed = value;
+      for (Lane& ln : sv->lanes) {
+        if (value > 0) {
+          ln.step_us = value;
+          ln.st_tuned = 1;
+        } else {
+          ln.st_tuned = 0;
+          ln.st_idx = 0;
+          ln.st_count = 0;
+          ln.step_us = kStepUsCandidates[0];
+        }
+      }
+      return SNN_OK;
+    default:
+      return sfail(SNN_E_ARG, "unknown server option %d", option);
+  }
 }
 
 int snn_server_submit(snn_server* sv, const snn_request* req, uint64_t* id) {
@@ -681,7 +991,8 @@ int snn_server_submit(snn_server* sv, const snn_request* req, uint64_t* id) {
   } else {
     q.r.params.spike_log_capacity = 0;
   }
-  if (q.r.params.tile_width == 0) q.r.params.tile_width = serve_tile_width(q.r);
+  if (q.r.params.tile_width == 0)
+    q.r.params.tile_width = serve_tile_width(q.r, sv->persistent);
   q.est = estimate_bytes(q.r, sv->fmt);
   SREQ(q.est <= sv->budget, SNN_E_ARG,
        "request needs about %llu bytes, above the server budget",
@@ -715,9 +1026,13 @@ int snn_server_step(snn_server* sv, int32_t* n_active) {
     for (Req* q : sv->ready) {
       q->res.state = SNN_REQ_RUNNING;
       q->res.t_start = now_s() - sv->t0;
-      Lane& ln = sv->lanes[lane_of(q->net)];
-      ln.active.push_back(q);
-      ln.active_steps.push_back(-1);
+      Lane& ln = sv->lanes[sv->persistent ? 0 : lane_of(q->net)];
+      // (smallest nets first: the persistent kernel serves them first)
+      size_t at = ln.active.size();
+      if (sv->persistent)
+        while (at > 0 && ln.active[at - 1]->net->n_syn > q->net->n_syn) --at;
+      ln.active.insert(ln.active.begin() + at, q);
+      ln.active_steps.insert(ln.active_steps.begin() + at, -1);
       ln.dirty = true;
     }
     sv->ready.clear();
@@ -726,7 +1041,9 @@ int snn_server_step(snn_server* sv, int32_t* n_active) {
   int32_t act = 0;
   for (int k = 0; k < kLanes; ++k) {
     bool launched = false;
-    int rc = lane_step(sv, &sv->lanes[k], &launched);
+    int rc = sv->persistent ? (k == 0 ? lane_step_persistent(sv, &sv->lanes[k], &launched)
+                                      : SNN_OK)
+                            : lane_step(sv, &sv->lanes[k], &launched);
     if (rc != SNN_OK) return rc;
     any = any || launched;
     act += (int32_t)(sv->lanes[k].active.size() + sv->lanes[k].retiring.size());
@@ -803,6 +1120,13 @@ int snn_server_get_stats(snn_server* sv, snn_server_stats* out) {
   out->mem_used = sv->used;
   out->intervals_per_step = sv->lanes[busiest].ips;
   out->tuned = tuned && sv->steps > 0;
+  if (sv->persistent) {
+    // one lane; its intervals per launch on average, and the step tuner
+    const Lane& ln = sv->lanes[0];
+    out->intervals_per_step =
+        ln.steps ? (int32_t)((ln.intervals + ln.steps / 2) / ln.steps) : 0;
+    out->tuned = ln.st_tuned;
+  }
   return SNN_OK;
 }
 
@@ -832,6 +1156,15 @@ int snn_server_destroy(snn_server* sv) {
       }
     }
     for (auto& fe : ln.retiring) cudaEventDestroy(fe.second);
+    for (int sl = 0; sl < 2; ++sl) {
+      if (ln.h_sn[sl]) cudaFreeHost(ln.h_sn[sl]);
+      if (ln.h_sn_back[sl]) cudaFreeHost(ln.h_sn_back[sl]);
+      if (ln.h_ctl[sl]) cudaFreeHost(ln.h_ctl[sl]);
+    }
+    if (ln.stream) {
+      pool_free(ln.d_sn, ln.stream);
+      pool_free(ln.d_ctl, ln.stream);
+    }
     for (cudaEvent_t e : ln.spare_events) cudaEventDestroy(e);
     for (auto& pair : ln.ev)
       for (cudaEvent_t e : pair)

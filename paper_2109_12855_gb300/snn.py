@@ -41,7 +41,7 @@ EXPORTS = [
     "snn_server_get_stats", "snn_server_destroy", "snn_set_stdp",
     "snn_read_weights", "snn_read_spike_stats", "snn_clear_spike_stats",
     "snn_read_pending", "snn_get_bounds", "snn_set_bounds",
-    "snn_deliver_gathered",
+    "snn_deliver_gathered", "snn_server_set_option",
 ]
 SNN_REQ_QUEUED, SNN_REQ_BUILDING, SNN_REQ_RUNNING, SNN_REQ_DONE = 0, 1, 2, 3
 SNN_REQ_FAILED = -1
@@ -205,6 +205,7 @@ def lib():
             "snn_server_release": ([_P, C.c_uint64], C.c_int),
             "snn_server_get_stats": ([_P, C.POINTER(snn_server_stats)], C.c_int),
             "snn_server_destroy": ([_P], C.c_int),
+            "snn_server_set_option": ([_P, C.c_int32, C.c_double], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -648,6 +649,13 @@ def snn_server_get_stats(sv) -> snn_server_stats:
     st = snn_server_stats()
     _check(lib().snn_server_get_stats(sv, C.byref(st)))
     return st
+
+
+SNN_SERVE_OPT_PERSISTENT, SNN_SERVE_OPT_SPIN_LIMIT, SNN_SERVE_OPT_STEP_US = 0, 1, 2
+
+
+def snn_server_set_option(sv, option: int, value: float):
+    _check(lib().snn_server_set_option(sv, option, float(value)))
 
 
 def snn_server_destroy(sv):

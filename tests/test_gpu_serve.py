@@ -1,11 +1,14 @@
 """Serving: independent simulation requests batched onto one GPU.
 
-A served net runs through the batched update and batched tiled-delivery
-kernels, one launch each per interval for all running nets.  Because tiled
-delivery sums in exact fixed point and every random draw is keyed by
-(neuron, step), a request's spike train must equal, bit for bit, the same
-net simulated alone through the single-net path, whatever else shares its
-batch, when it was admitted, and how many intervals a step runs."""
+By default a server step runs lanes of batched update and batched
+tiled-delivery launches, one each per interval; the persistent mode makes a
+step one launch of the persistent serving kernel, which advances every
+running net by its own number of intervals (CTAs claim the ready update
+blocks and delivery tiles of the nets).  Because tiled delivery sums in exact fixed point and every random
+draw is keyed by (neuron, step), a request's spike train must equal, bit for
+bit, the same net simulated alone through the single-net path, whatever
+else shares its batch, when it was admitted, and how many intervals a step
+runs."""
 import numpy as np
 import pytest
 
@@ -79,8 +82,9 @@ def _check_equal_to_solo(sv, rid, r):
     return res
 
 
+@pytest.mark.parametrize("persistent", [1, 0], ids=["persistent", "lanes"])
 @pytest.mark.parametrize("fmt", [0, 1], ids=["fp32", "bf16"])
-def test_batched_requests_equal_solo_runs(fmt):
+def test_batched_requests_equal_solo_runs(fmt, persistent):
     """Mixed sizes, seeds, delay ranges and lengths (one not a multiple of
     its interval); two requests join while the first two are running."""
     from paper_2109_12855_gb300 import snn
@@ -90,6 +94,7 @@ def test_batched_requests_equal_solo_runs(fmt):
             _req(11250, 4, 400, fmt, (12, 30), nu=15000.0, tag=14)]
     sv = snn.snn_server_create(8 * GB, fmt, stream())
     try:
+        snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_PERSISTENT, persistent)
         ids = [snn.snn_server_submit(sv, r) for r in reqs[:2]]
         for _ in range(5):
             snn.snn_server_step(sv)
@@ -104,7 +109,10 @@ def test_batched_requests_equal_solo_runs(fmt):
         st = snn.snn_server_get_stats(sv)
         assert st.done == 4 and st.failed == 0 and st.active == 0
         assert st.mem_used == 0
-        assert st.kernel_launches == 2 * st.intervals
+        if persistent:   # one launch per step, several intervals each
+            assert st.kernel_launches == st.steps < st.intervals
+        else:
+            assert st.kernel_launches == 2 * st.intervals
     finally:
         snn.snn_server_destroy(sv)
 
@@ -186,5 +194,57 @@ def test_requests_rejected_or_failed():
         snn.snn_server_release(sv, ids[1])
         with pytest.raises(snn.SnnError):
             snn.snn_server_poll(sv, ids[1])
+    finally:
+        snn.snn_server_destroy(sv)
+
+
+def test_persistent_steps_pace_nets_by_their_own_interval_time():
+    """A long small net and a long large net in one persistent kernel: the
+    step-length tuner settles, every net runs several intervals per launch,
+    and both equal their solo runs."""
+    from paper_2109_12855_gb300 import snn
+    small, large = _req(2000, 31, 20000, 1), _req(40000, 32, 3000, 1)
+    sv = snn.snn_server_create(16 * GB, 1, stream())
+    try:
+        snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_PERSISTENT, 1)
+        ids = [snn.snn_server_submit(sv, r) for r in (large, small)]
+        _drain(sv, ids)
+        st = snn.snn_server_get_stats(sv)
+        assert st.tuned == 1 and st.intervals_per_step > 1, \
+            (st.tuned, st.steps, st.intervals, st.intervals_per_step)
+        assert st.intervals == 2000 + 300 and 2 * st.steps < st.intervals
+        for rid, r in zip(ids, (large, small)):
+            _check_equal_to_solo(sv, rid, r)
+        # the small net (2,000 intervals) took less time than the large one
+        # (300 intervals) would have at its own pace
+        rs, rl = (snn.snn_server_poll(sv, i) for i in (ids[1], ids[0]))
+        assert rs.t_done - rs.t_start < (rl.t_done - rl.t_start) * 2000 / 300
+    finally:
+        snn.snn_server_destroy(sv)
+
+
+def test_persistent_kernel_wait_limit_fails_the_step_not_the_gpu():
+    """A spin limit of one poll makes the persistent kernel give up at once
+    (a CTA finds no ready item): its launch ends, the requests it ran fail
+    with SNN_E_TIMEOUT, and the server serves the next request normally."""
+    from paper_2109_12855_gb300 import snn
+    sv = snn.snn_server_create(4 * GB, 0, stream())
+    try:
+        snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_PERSISTENT, 1)
+        snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_SPIN_LIMIT, 1)
+        bad = [_req(3000, 41 + k, 500) for k in range(2)]
+        ids = [snn.snn_server_submit(sv, r) for r in bad]
+        _drain(sv, ids)
+        for i in ids:
+            res = snn.snn_server_poll(sv, i)
+            assert res.state == snn.SNN_REQ_FAILED
+            assert res.error == snn.SNN_E_TIMEOUT
+        snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_SPIN_LIMIT, 1 << 22)
+        good = _req(3000, 45, 500)
+        rid = snn.snn_server_submit(sv, good)
+        _drain(sv, [rid])
+        _check_equal_to_solo(sv, rid, good)
+        st = snn.snn_server_get_stats(sv)
+        assert (st.done, st.failed, st.mem_used) == (1, 2, 0)
     finally:
         snn.snn_server_destroy(sv)
