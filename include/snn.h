@@ -244,6 +244,13 @@ typedef struct snn_net snn_net;
 /* Library identity and diagnostics. */
 int snn_abi_version(void);
 const char* snn_last_error(void);
+/* Host-side fault injection for tests (not part of the paper's method):
+ * after `after` more device allocations of the library succeed (process-
+ * wide, any thread), the next `count` fail as if device memory were
+ * exhausted, so that error paths (SNN_E_OOM from snn_create, connect,
+ * finalize, a server's build) run without exhausting the GPU.  after < 0
+ * switches it off. */
+int snn_debug_fail_allocations(int64_t after, int64_t count);
 
 /* Fill *p with the benchmark defaults: 1,000 E + 250 I neurons, h = 0.1 ms,
  * tau_m = 10 ms, C = 250 pF, V_th = 20 mV, V_reset = 0, t_ref = 2 ms,
@@ -510,7 +517,8 @@ enum {
   SNN_REQ_BUILDING = 1,
   SNN_REQ_RUNNING = 2,
   SNN_REQ_DONE = 3,
-  SNN_REQ_FAILED = -1
+  SNN_REQ_FAILED = -1,
+  SNN_REQ_CANCELLED = 4
 };
 
 typedef struct snn_result {
@@ -587,6 +595,14 @@ int snn_server_spikes(snn_server* sv, uint64_t id, uint32_t* src, int32_t* t,
                       uint64_t cap, uint64_t* n);
 /* Forget a finished request's result. */
 int snn_server_release(snn_server* sv, uint64_t id);
+/* Cancel a request (thread-safe).  A queued request leaves the queue at
+ * once; one being built is destroyed when its build ends; a running one
+ * leaves its batch at the next snn_server_step and is freed once the GPU
+ * work already launched for it has completed.  Its state becomes
+ * SNN_REQ_CANCELLED (no spikes or counters are kept) and its memory returns
+ * to the budget.  SNN_E_STATE if it already finished, failed or was
+ * cancelled; SNN_E_ARG for an unknown id. */
+int snn_server_cancel(snn_server* sv, uint64_t id);
 int snn_server_get_stats(snn_server* sv, snn_server_stats* out);
 /* Stop the builder threads, free all nets; sv may be NULL. */
 int snn_server_destroy(snn_server* sv);

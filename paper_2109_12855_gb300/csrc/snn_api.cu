@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -215,8 +216,27 @@ void count_net(int dev, int delta, cudaStream_t s) {
 
 }  // namespace
 
+// Host-side fault injection (snn_debug_fail_allocations): after g_fail_after
+// more allocations succeed, the next g_fail_count fail.
+std::atomic<long long> g_fail_after{-1};
+std::atomic<long long> g_fail_count{0};
+
+bool injected_failure() {
+  long long a = g_fail_after.load(std::memory_order_relaxed);
+  while (a > 0) {
+    if (g_fail_after.compare_exchange_weak(a, a - 1)) return false;
+  }
+  if (a < 0) return false;
+  long long c = g_fail_count.load(std::memory_order_relaxed);
+  while (c > 0) {
+    if (g_fail_count.compare_exchange_weak(c, c - 1)) return true;
+  }
+  return false;
+}
+
 cudaError_t snn::pool_alloc(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
   if (bytes == 0) bytes = 16;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -609,6 +629,13 @@ void drop_graphs(snn_net* net) {
 extern "C" {
 
 int snn_abi_version(void) { return SNN_ABI_VERSION; }
+
+int snn_debug_fail_allocations(int64_t after, int64_t count) {
+  REQ(count >= 0, SNN_E_ARG, "negative count");
+  g_fail_count.store(count);
+  g_fail_after.store(after < 0 ? -1 : after);
+  return SNN_OK;
+}
 
 const char* snn_last_error(void) { return g_err.c_str(); }
 

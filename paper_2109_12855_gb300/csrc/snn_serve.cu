@@ -105,7 +105,11 @@ struct Req {
   std::vector<int32_t> sp_t;
   double iv_us = 0;      // persistent mode: measured time per interval
   int fail_code = 0;     // non-zero: retire as failed (e.g. SNN_E_TIMEOUT)
+  bool cancel = false;   // snn_server_cancel asked (guarded by the mutex)
 };
+
+// fail_code of a cancelled request
+constexpr int kCancelled = 1;
 
 }  // namespace
 
@@ -305,7 +309,12 @@ void builder_main(snn_server* sv, int cls) {
     if (cls == 1) sv->building_large.fetch_sub(1);
     lk.lock();
     Req& q2 = sv->reqs[id];
-    if (rc == SNN_OK) {
+    if (rc == SNN_OK && q2.cancel) {
+      snn_destroy(net);
+      sv->used -= q2.est;
+      q2.res.state = SNN_REQ_CANCELLED;
+      q2.res.t_done = now_s() - sv->t0;
+    } else if (rc == SNN_OK) {
       q2.net = net;
       q2.steps_left = r.n_steps;
       q2.res.n_synapses = net->n_syn;
@@ -504,6 +513,16 @@ int retire_done(snn_server* sv, Lane* ln) {
     const bool rec = q->r.record_spikes != 0;
     snn_stats st;
     rc = q->fail_code ? q->fail_code : snn_get_stats(net, &st);
+    if (q->fail_code == kCancelled) {
+      snn_destroy(net);
+      std::lock_guard<std::mutex> lk(sv->mu);
+      q->net = nullptr;
+      sv->used -= q->est;
+      q->res.t_done = now_s() - sv->t0;
+      q->res.state = SNN_REQ_CANCELLED;
+      sv->cv.notify_all();
+      continue;
+    }
     std::vector<uint32_t> src;
     std::vector<int32_t> t;
     if (rc == SNN_OK && rec && net->log_cap) {
@@ -541,12 +560,45 @@ int retire_done(snn_server* sv, Lane* ln) {
   return SNN_OK;
 }
 
+// Nets of the lane whose cancellation was asked leave the batch and retire
+// (as cancelled) once the work already launched for them has completed.
+int drop_cancelled(snn_server* sv, Lane* ln) {
+  std::vector<Req*> gone;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (Req* q : ln->active)
+      if (q->cancel) gone.push_back(q);
+  }
+  if (gone.empty()) return SNN_OK;
+  std::vector<Req*> keep;
+  std::vector<int> keep_steps;
+  for (size_t k = 0; k < ln->active.size(); ++k) {
+    Req* q = ln->active[k];
+    if (std::find(gone.begin(), gone.end(), q) != gone.end()) {
+      q->fail_code = kCancelled;
+      cudaEvent_t e = nullptr;
+      SCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      SCK(cudaEventRecord(e, ln->stream));
+      ln->retiring.emplace_back(q, e);
+    } else {
+      keep.push_back(q);
+      keep_steps.push_back(ln->active_steps[k]);
+    }
+  }
+  ln->active.swap(keep);
+  ln->active_steps.swap(keep_steps);
+  ln->dirty = true;
+  ln->t_last = 0;
+  return SNN_OK;
+}
+
 // One step of one lane: retire what finished, then launch its nets' next
 // intervals (several in one graph when the autotuner chose so) unless the
 // GPU still needs the lane's event pair or its other table set.
 int lane_step(snn_server* sv, Lane* ln, bool* launched) {
   *launched = false;
   int rc;
+  if ((rc = drop_cancelled(sv, ln)) != SNN_OK) return rc;
   if ((rc = retire_done(sv, ln)) != SNN_OK) return rc;
   // fold in the GPU time of finished steps, oldest first; the pair this
   // step reuses must be finished, else the lane sits this step out
@@ -728,6 +780,7 @@ int fold_persistent(snn_server* sv, Lane* ln, int slot, bool* done) {
 int lane_step_persistent(snn_server* sv, Lane* ln, bool* launched) {
   *launched = false;
   int rc;
+  if ((rc = drop_cancelled(sv, ln)) != SNN_OK) return rc;
   if ((rc = retire_done(sv, ln)) != SNN_OK) return rc;
   bool reuse_done = true;
   for (int k = 0; k < 2; ++k) {
@@ -1024,6 +1077,15 @@ int snn_server_step(snn_server* sv, int32_t* n_active) {
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     for (Req* q : sv->ready) {
+      if (q->cancel) {  // cancelled after its build: nothing launched yet
+        snn_destroy(q->net);
+        q->net = nullptr;
+        sv->used -= q->est;
+        q->res.state = SNN_REQ_CANCELLED;
+        q->res.t_done = now_s() - sv->t0;
+        sv->cv.notify_all();
+        continue;
+      }
       q->res.state = SNN_REQ_RUNNING;
       q->res.t_start = now_s() - sv->t0;
       Lane& ln = sv->lanes[sv->persistent ? 0 : lane_of(q->net)];
@@ -1089,9 +1151,35 @@ int snn_server_release(snn_server* sv, uint64_t id) {
   auto it = sv->reqs.find(id);
   SREQ(it != sv->reqs.end(), SNN_E_ARG, "unknown request");
   SREQ(it->second.res.state == SNN_REQ_DONE ||
-           it->second.res.state == SNN_REQ_FAILED,
+           it->second.res.state == SNN_REQ_FAILED ||
+           it->second.res.state == SNN_REQ_CANCELLED,
        SNN_E_STATE, "request not finished");
   sv->reqs.erase(it);
+  return SNN_OK;
+}
+
+int snn_server_cancel(snn_server* sv, uint64_t id) {
+  SREQ(sv, SNN_E_ARG, "null server");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(id);
+  SREQ(it != sv->reqs.end(), SNN_E_ARG, "unknown request %llu",
+       (unsigned long long)id);
+  Req& q = it->second;
+  const int st = q.res.state;
+  SREQ(st == SNN_REQ_QUEUED || st == SNN_REQ_BUILDING || st == SNN_REQ_RUNNING,
+       SNN_E_STATE, "request %llu already ended", (unsigned long long)id);
+  SREQ(!q.cancel, SNN_E_STATE, "request %llu already cancelled",
+       (unsigned long long)id);
+  q.cancel = true;
+  if (st == SNN_REQ_QUEUED) {
+    for (auto& qu : sv->queue) {
+      auto pos = std::find(qu.begin(), qu.end(), id);
+      if (pos != qu.end()) qu.erase(pos);
+    }
+    q.res.state = SNN_REQ_CANCELLED;
+    q.res.t_done = now_s() - sv->t0;
+    sv->cv.notify_all();
+  }
   return SNN_OK;
 }
 

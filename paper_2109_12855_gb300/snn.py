@@ -41,10 +41,12 @@ EXPORTS = [
     "snn_server_get_stats", "snn_server_destroy", "snn_set_stdp",
     "snn_read_weights", "snn_read_spike_stats", "snn_clear_spike_stats",
     "snn_read_pending", "snn_get_bounds", "snn_set_bounds",
-    "snn_deliver_gathered", "snn_server_set_option",
+    "snn_deliver_gathered", "snn_server_set_option", "snn_server_cancel",
+    "snn_debug_fail_allocations",
 ]
 SNN_REQ_QUEUED, SNN_REQ_BUILDING, SNN_REQ_RUNNING, SNN_REQ_DONE = 0, 1, 2, 3
 SNN_REQ_FAILED = -1
+SNN_REQ_CANCELLED = 4
 
 
 class SnnError(RuntimeError):
@@ -206,6 +208,8 @@ def lib():
             "snn_server_get_stats": ([_P, C.POINTER(snn_server_stats)], C.c_int),
             "snn_server_destroy": ([_P], C.c_int),
             "snn_server_set_option": ([_P, C.c_int32, C.c_double], C.c_int),
+            "snn_server_cancel": ([_P, C.c_uint64], C.c_int),
+            "snn_debug_fail_allocations": ([C.c_int64, C.c_int64], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -656,6 +660,14 @@ SNN_SERVE_OPT_PERSISTENT, SNN_SERVE_OPT_SPIN_LIMIT, SNN_SERVE_OPT_STEP_US = 0, 1
 
 def snn_server_set_option(sv, option: int, value: float):
     _check(lib().snn_server_set_option(sv, option, float(value)))
+
+
+def snn_server_cancel(sv, rid: int):
+    _check(lib().snn_server_cancel(sv, rid))
+
+
+def snn_debug_fail_allocations(after: int, count: int = 1):
+    _check(lib().snn_debug_fail_allocations(after, count))
 
 
 def snn_server_destroy(sv):

@@ -64,7 +64,8 @@ def _drain(sv, ids, max_steps=100000, watch=None):
         if watch:
             watch(snn.snn_server_get_stats(sv))
         states = [snn.snn_server_poll(sv, i).state for i in ids]
-        if all(s in (snn.SNN_REQ_DONE, snn.SNN_REQ_FAILED) for s in states):
+        if all(s in (snn.SNN_REQ_DONE, snn.SNN_REQ_FAILED,
+                     snn.SNN_REQ_CANCELLED) for s in states):
             return
     raise AssertionError("server did not finish")
 
@@ -248,3 +249,73 @@ def test_persistent_kernel_wait_limit_fails_the_step_not_the_gpu():
         assert (st.done, st.failed, st.mem_used) == (1, 2, 0)
     finally:
         snn.snn_server_destroy(sv)
+
+
+@pytest.mark.parametrize("persistent", [0, 1], ids=["lanes", "persistent"])
+def test_cancel_queued_and_running_requests(persistent):
+    """Cancelling a queued request removes it before it is built; cancelling
+    a running one drops it from its batch (freed once its launched work has
+    completed); the others still equal their solo runs; the budget is
+    returned; a finished request cannot be cancelled."""
+    from paper_2109_12855_gb300 import snn
+    keep = _req(3000, 51, 800)
+    run_long = _req(5000, 52, 200000)         # would run for a long time
+    queued = _req(2000, 53, 500)
+    sv = snn.snn_server_create(4 * GB, 0, stream())
+    try:
+        snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_PERSISTENT, persistent)
+        ids = [snn.snn_server_submit(sv, r) for r in (keep, run_long)]
+        for _ in range(2000):                 # until both run
+            snn.snn_server_step(sv)
+            if all(snn.snn_server_poll(sv, i).state == snn.SNN_REQ_RUNNING
+                   for i in ids):
+                break
+        qid = snn.snn_server_submit(sv, queued)
+        snn.snn_server_cancel(sv, qid)        # queued or building
+        snn.snn_server_cancel(sv, ids[1])     # running
+        with pytest.raises(snn.SnnError) as e:
+            snn.snn_server_cancel(sv, ids[1])  # already cancelled
+        assert e.value.code == snn.SNN_E_STATE
+        _drain(sv, ids + [qid])
+        for i in (qid, ids[1]):
+            assert snn.snn_server_poll(sv, i).state == snn.SNN_REQ_CANCELLED
+        _check_equal_to_solo(sv, ids[0], keep)
+        with pytest.raises(snn.SnnError) as e:
+            snn.snn_server_cancel(sv, ids[0])  # finished
+        assert e.value.code == snn.SNN_E_STATE
+        st = snn.snn_server_get_stats(sv)
+        assert st.done == 1 and st.active == 0 and st.mem_used == 0
+        snn.snn_server_release(sv, qid)
+    finally:
+        snn.snn_server_destroy(sv)
+
+
+def test_injected_allocation_failures():
+    """Host-side fault injection: a device allocation that fails makes
+    snn_create and a server's build fail with SNN_E_OOM and leaves the
+    library usable (the next net and the next request succeed)."""
+    from paper_2109_12855_gb300 import snn
+    try:
+        snn.snn_debug_fail_allocations(3, 1)  # the 4th allocation fails
+        with pytest.raises(snn.SnnError) as e:
+            snn.Net(snn.params(n_exc=100, n_inh=25), stream())
+        assert e.value.code == snn.SNN_E_OOM
+        with snn.Net(snn.params(n_exc=100, n_inh=25), stream()) as net:
+            net.finalize()                    # allocations succeed again
+        sv = snn.snn_server_create(4 * GB, 0, stream())
+        try:
+            snn.snn_debug_fail_allocations(0, 1)  # the build's first one
+            bad = snn.snn_server_submit(sv, _req(2000, 61, 300))
+            _drain(sv, [bad])
+            res = snn.snn_server_poll(sv, bad)
+            assert res.state == snn.SNN_REQ_FAILED
+            assert res.error == snn.SNN_E_OOM
+            good = _req(2000, 62, 300)
+            rid = snn.snn_server_submit(sv, good)
+            _drain(sv, [rid])
+            _check_equal_to_solo(sv, rid, good)
+            assert snn.snn_server_get_stats(sv).mem_used == 0
+        finally:
+            snn.snn_server_destroy(sv)
+    finally:
+        snn.snn_debug_fail_allocations(-1, 0)
