@@ -1083,9 +1083,15 @@ def ctypes_size(t):
 def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
     """Rank r simulates neurons split(N, world)[r] of ONE network with the
     synapses of all sources onto them; every interval the ranks all-gather
-    their spike lists (NCCL, device tensors) and deliver the union.  The
-    union of the partitions equals the whole net bit for bit.  Strong
-    scaling: the total work is fixed as the number of GPUs grows."""
+    their spike lists and deliver the union.  The union of the partitions
+    equals the whole net bit for bit.  Strong scaling: the total work is
+    fixed as the number of GPUs grows.
+
+    Default exchange: the update writes its spikes into a fixed-size device
+    buffer, one NCCL all_gather_into_tensor moves the buffers (none at
+    N=1), the delivery reads them directly -- no host synchronisation per
+    interval.  --host-exchange: read each pending list (counts through the
+    host) and all-gather variable-length lists."""
     import torch
     from paper_2109_12855_gb300 import partition as PT
     from paper_2109_12855_gb300 import snn
@@ -1124,8 +1130,19 @@ def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
     d_src = torch.empty(max(net.n * D, 1), dtype=torch.int32, device="cuda")
     d_t = torch.empty_like(d_src)
     steps_per = int(round(bio_ms / 0.1))
+    xch = None
+    if not args.host_exchange:
+        def cap_max(v):
+            import torch.distributed as dist
+            x = torch.tensor([int(v)], dtype=torch.int64, device="cuda")
+            dist.all_reduce(x, op=dist.ReduceOp.MAX)
+            return int(x.item())
+        xch = PT.DeviceExchange([net], reduce_max=cap_max if ws > 1 else None)
 
     def step(t0):
+        if xch is not None:
+            return PT.simulate_exchanged([net], xch, steps_per, t0=t0,
+                                         interval=D)
         t = t0
         while t < t0 + steps_per:
             m = min(D, t0 + steps_per - t)
@@ -1160,6 +1177,10 @@ def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
     spikes = b.spikes - a.spikes
     launches = b.kernel_launches - a.kernel_launches
     ms_max, ev_all, sp_all = reduce_over_ranks(ms, events, spikes)
+    if b.error_flags:
+        raise RuntimeError(f"device error flags {b.error_flags:#x}")
+    if xch is not None:
+        xch.close()
     net.close()
     if rank != 0:
         return
@@ -1177,11 +1198,27 @@ def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
                    "parallelism": f"target partition x{ws}: each GPU holds "
                                   "1/N of the neurons and the synapses onto "
                                   "them; spike lists all-gathered every "
-                                  "interval"},
+                                  "interval",
+                   "exchange": ("host lists (read + variable all-gather)"
+                                if args.host_exchange else
+                                "device buffers (fixed all_gather_into_tensor, "
+                                "no host sync)")},
         "roofline": None, "cpu_baseline": None, "e2e": None,
         "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)
+
+
+def use_partition(workload: str, kind: str, world: int, partition: bool,
+                  replicas: bool) -> bool:
+    """Several ranks split ONE network (target partition, strong scaling)
+    unless replicas are asked for; one rank runs the whole net unless the
+    partitioned path is asked for.  Plastic and replayed-list workloads do
+    not partition."""
+    partitionable = kind == "simulate" and "stdp" not in workload
+    if partition and not partitionable:
+        raise SystemExit(f"{workload} cannot be partitioned")
+    return partitionable and (partition or (world > 1 and not replicas))
 
 
 def main():
@@ -1192,6 +1229,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) +
                     sorted(SERVE_WORKLOADS), default=DEFAULT)
+    ap.add_argument("--host-exchange", action="store_true",
+                    help="with --partition: exchange through the host "
+                         "(pending lists read back every interval)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several ranks: independent copies of the "
+                         "network (one per GPU) instead of one partitioned "
+                         "network")
     ap.add_argument("--partition", action="store_true",
                     help="split one network over the ranks (target "
                          "partition, spike all-gather every interval) "
@@ -1233,6 +1277,8 @@ def main():
             run_serve(args, SERVE_WORKLOADS[args.workload], nu_ext)
         return
     wl, fmt, bio_ms, kind = WORKLOADS[args.workload]
+    args.partition = use_partition(args.workload, kind, dist_env()[0],
+                                   args.partition, args.replicas)
     if args.partition and args.impl != "reference":
         from paper_2109_12855_gb300 import build
         build()

@@ -85,9 +85,14 @@ enum {
   SNN_ERRF_CHUNKS = 1u << 3,     /* chunk counter of one interval overflowed */
   SNN_ERRF_TIMEOUT = 1u << 4,    /* a bounded device wait gave up (delivery of
                                     that launch is incomplete) */
-  SNN_ERRF_SCALES = 1u << 5      /* internal: an interval's exact-sum scales
+  SNN_ERRF_SCALES = 1u << 5,     /* internal: an interval's exact-sum scales
                                     were proven on the host but not found on
                                     the device (never expected) */
+  SNN_ERRF_CHECK = 1u << 6       /* bounds-checked builds only (snn_checked):
+                                    a synapse record with a target or delay
+                                    outside the store's ranges, a tile index
+                                    entry outside its row, or a spike list
+                                    with decreasing chunk offsets was skipped */
 };
 
 /* Neuron model and simulation parameters (iaf_psc_alpha, resting potential
@@ -405,6 +410,58 @@ int snn_deliver_gathered(snn_net* net, const uint32_t* src,
                          const int32_t* t_emit, uint32_t n_spikes, int mem,
                          uint64_t* n_events_out);
 
+/* Device-resident spike exchange between partitions (Section 2.1: the
+ * spikes of one min-delay interval are exchanged between processes once,
+ * before their delivery).  Without any host round trip per interval:
+ *
+ *   snn_update(part, t0, n)          writes the interval's own spikes into
+ *                                    the part's exchange buffer too
+ *   all-gather of the fixed-size     (NCCL on the caller's stream, or a
+ *   exchange buffers of all parts     plain device copy within one process)
+ *   snn_deliver_exchanged(part, ...) delivers the union read directly from
+ *                                    the gathered buffers
+ *
+ * Exchange buffer layout (little-endian 32-bit words, 16-byte aligned
+ * device memory of the net's device, 16 + 8 cap bytes):
+ *   word 0          spike count of the interval (zeroed in stream order
+ *                   before each update, which then adds its spikes)
+ *   words 1..3      unused (alignment)
+ *   words 4 + 2k    entry k: global source index
+ *   words 5 + 2k    entry k: emission step (int32)
+ * A count above cap (an undersized buffer) keeps the first cap entries and
+ * raises SNN_ERRF_SPIKE_LIST; snn_exchange_capacity gives the capacity that
+ * can never overflow. */
+
+/* Entries an exchange buffer of this partition needs so that it never
+ * overflows: local neurons x most spikes a neuron emits per interval (one
+ * per refractory period plus one step).  Finalized nets. */
+int snn_exchange_capacity(snn_net* net, uint64_t* cap_entries);
+
+/* Attach (buf != NULL) or detach (buf == NULL) the caller-owned exchange
+ * buffer of cap_entries entries (layout above; buf 16-byte aligned device
+ * memory of the net's device; not freed by the library).  While attached
+ * every snn_update / snn_simulate interval also writes its spikes there.
+ * SNN_E_ARG for a host, misaligned or foreign pointer or cap_entries of 0
+ * or above 2^32 - 1; SNN_E_STATE before snn_finalize or with an update
+ * pending. */
+int snn_set_exchange(snn_net* net, void* buf, uint64_t cap_entries);
+
+/* Deliver the pending interval with the list gathered from n_parts
+ * exchange buffers, part p at parts + p x stride_bytes (device memory; each
+ * holds its own count, so parts may be filled to different lengths; a count
+ * above (stride_bytes - 16) / 8 is read as that many entries).  The union is
+ * delivered as snn_deliver_gathered would deliver it (identical ring
+ * buffers).  The events delivered into this partition are
+ * counted on the device (snn_get_stats).  Asynchronous on the net's stream:
+ * the gathered buffers must be complete in stream order (e.g. an NCCL
+ * all-gather on the same stream) and stay unchanged until the delivery
+ * finishes.  Needs the tiled delivery and a static (non-plastic) net.
+ * SNN_E_STATE without a pending update, in atomic delivery mode or for
+ * plastic nets; SNN_E_ARG for n_parts outside [1, 64], a misaligned parts
+ * pointer or stride, or a stride below 16 bytes. */
+int snn_deliver_exchanged(snn_net* net, const void* parts, uint32_t n_parts,
+                          uint64_t stride_bytes);
+
 /* Accumulation bounds of the store (finalized nets).  The tiled delivery
  * sums each ring-buffer cell exactly in fixed point with scales derived
  * from these bounds; partitions of one network take the maximum of their
@@ -467,6 +524,27 @@ int snn_get_stats(snn_net* net, snn_stats* out);
 int snn_clear_errors(snn_net* net);
 /* Wait for all work of the net. */
 int snn_sync(snn_net* net);
+/* 1 for a bounds-checked build of the library (compiled with SNN_CHECK:
+ * every record's target and delay, every tile index entry and the order of
+ * every chunk offset is checked before use, failures raise SNN_ERRF_CHECK
+ * and skip the access), 0 for the production build. */
+int snn_checked(void);
+/* Bounds-checked builds: the number of nets whose SNN_ERRF_CHECK flag was
+ * seen set by snn_get_stats or snn_destroy since the library was loaded
+ * (always 0 in production builds). */
+uint64_t snn_debug_check_failures(void);
+/* Bounds-checked builds only: overwrite the target (field 0) or delay
+ * (field 1) of synapse record `index` of a finalized net with `value`, so
+ * that tests can show the checks skip and flag a corrupt store.
+ * SNN_E_STATE in production builds (whose kernels trust the store),
+ * SNN_E_ARG for an index outside the store or an unknown field. */
+int snn_debug_poke_record(snn_net* net, uint64_t index, int field,
+                          uint32_t value);
+/* The stream the net's work is enqueued on (*stream: a cudaStream_t; the
+ * one given to snn_create, or the one the library created when none was
+ * given).  Partitions that read each other's exchange buffers must share
+ * one stream, or order theirs with events. */
+int snn_get_stream(snn_net* net, void** stream);
 /* Free everything; net may be NULL. */
 int snn_destroy(snn_net* net);
 

@@ -626,6 +626,15 @@ void drop_graphs(snn_net* net) {
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+// Bounds-checked builds: nets seen with SNN_ERRF_CHECK (counted once each).
+static std::atomic<uint64_t> g_check_failures{0};
+static void note_check_failure(snn_net* net, unsigned flags) {
+  if (kChecked && (flags & SNN_ERRF_CHECK) && !net->check_noted) {
+    net->check_noted = true;
+    g_check_failures.fetch_add(1, std::memory_order_relaxed);
+  }
+}
+
 extern "C" {
 
 int snn_abi_version(void) { return SNN_ABI_VERSION; }
@@ -1203,6 +1212,84 @@ int snn_deliver_gathered(snn_net* net, const uint32_t* src,
   return SNN_OK;
 }
 
+// Device (or managed) memory of the net's device, 16-byte aligned: the
+// exchange buffers are read and written by the kernels directly.
+static int check_exchange_ptr(snn_net* net, const void* p, const char* what) {
+  REQ(((uintptr_t)p & 15u) == 0, SNN_E_ARG, "%s is not 16-byte aligned", what);
+  cudaPointerAttributes pa;
+  const cudaError_t pe = cudaPointerGetAttributes(&pa, p);
+  if (pe != cudaSuccess) cudaGetLastError();
+  REQ(pe == cudaSuccess, SNN_E_ARG, "%s: not a CUDA pointer (%s)", what,
+      cudaGetErrorString(pe));
+  REQ((pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) &&
+          pa.device == net->device,
+      SNN_E_ARG, "%s must be device memory of the net's device", what);
+  return SNN_OK;
+}
+
+int snn_exchange_capacity(snn_net* net, uint64_t* cap_entries) {
+  REQ(net && cap_entries, SNN_E_ARG, "null argument");
+  REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  *cap_entries = (uint64_t)net->n * std::max<uint32_t>(net->spikes_per_iv, 1u);
+  return SNN_OK;
+}
+
+int snn_set_exchange(snn_net* net, void* buf, uint64_t cap_entries) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  REQ(!net->pending, SNN_E_STATE, "spikes of an update are pending");
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  if (buf) {
+    REQ(cap_entries >= 1 && cap_entries <= 0xFFFFFFFFull, SNN_E_ARG,
+        "exchange capacity %llu outside [1, 2^32 - 1]",
+        (unsigned long long)cap_entries);
+    if ((rc = check_exchange_ptr(net, buf, "exchange buffer")) != SNN_OK)
+      return rc;
+  }
+  // the captured intervals hold the old view; the stream's queued work may
+  // still write the old buffer, so the caller's reuse waits for it
+  CK(cudaStreamSynchronize(net->stream));
+  drop_graphs(net);
+  net->xbuf = static_cast<uint32_t*>(buf);
+  net->xcap = buf ? (uint32_t)cap_entries : 0u;
+  return SNN_OK;
+}
+
+int snn_deliver_exchanged(snn_net* net, const void* parts, uint32_t n_parts,
+                          uint64_t stride_bytes) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  REQ(net->pending, SNN_E_STATE, "no pending interval (call snn_update first)");
+  REQ(!net->stdp_on, SNN_E_STATE, "plastic nets deliver their own spikes");
+  REQ(use_tiled(net), SNN_E_STATE,
+      "exchanged lists need the tiled delivery (deliver_mode TILED with a "
+      "window that fits a tile)");
+  REQ(n_parts >= 1 && n_parts <= kMaxGatherParts, SNN_E_ARG,
+      "n_parts %u outside [1, %u]", n_parts, kMaxGatherParts);
+  REQ(stride_bytes >= 16 && stride_bytes % 16 == 0, SNN_E_ARG,
+      "stride %llu is not a multiple of 16 bytes of at least 16",
+      (unsigned long long)stride_bytes);
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  if ((rc = check_exchange_ptr(net, parts, "parts")) != SNN_OK) return rc;
+  cudaStream_t s = net->stream;
+  // the union's events are counted by the delivery itself (the update's
+  // count covers only the local sources' synapses)
+  CK(cudaMemsetAsync(&net->ctl->pending_events, 0, sizeof(unsigned long long), s));
+  NetView v = net->view();
+  v.gx = static_cast<const uint32_t*>(parts);
+  v.gx_parts = n_parts;
+  v.gx_stride = stride_bytes / 4;
+  v.gx_cap = (uint32_t)std::min<uint64_t>((stride_bytes - 16) / 8, 0xFFFFFFFFull);
+  CK(launch_deliver_tiled(v, &net->ctl->pair, &net->ctl->done, net->list, 0, 1,
+                          s));
+  net->launches += 1;
+  net->del_launches += 1;
+  net->pending = false;
+  return SNN_OK;
+}
+
 int snn_deliver_noalloc(snn_net* net, const uint32_t* src,
                         const int32_t* t_emit, uint32_t n_spikes,
                         uint64_t* n_events_out) {
@@ -1621,6 +1708,7 @@ int snn_get_stats(snn_net* net, snn_stats* out) {
   out->first_neuron = net->g0;
   out->n_sources = net->n_src;
   out->acc_words = net->acc_words;
+  note_check_failure(net, c.error_flags);
   return SNN_OK;
 }
 
@@ -1771,10 +1859,55 @@ int snn_sync(snn_net* net) {
   return SNN_OK;
 }
 
+int snn_get_stream(snn_net* net, void** stream) {
+  REQ(net && stream, SNN_E_ARG, "null argument");
+  *stream = static_cast<void*>(net->stream);
+  return SNN_OK;
+}
+
+int snn_checked(void) { return kChecked ? 1 : 0; }
+
+uint64_t snn_debug_check_failures(void) {
+  return g_check_failures.load(std::memory_order_relaxed);
+}
+
+int snn_debug_poke_record(snn_net* net, uint64_t index, int field,
+                          uint32_t value) {
+  REQ(net, SNN_E_ARG, "null net");
+  REQ(kChecked, SNN_E_STATE,
+      "store corruption is only accepted by bounds-checked builds");
+  REQ(net->finalized, SNN_E_STATE, "net not finalized");
+  REQ(index < net->n_syn, SNN_E_ARG, "record %llu outside the store",
+      (unsigned long long)index);
+  REQ(field == 0 || (field == 1 && value <= 0xFFu), SNN_E_ARG,
+      "field %d / value %u", field, value);
+  int rc;
+  if ((rc = set_device(net)) != SNN_OK) return rc;
+  // target: word 0 of both formats; delay: low byte of word 2 (FP32
+  // records) or of word 1 (BF16 records)
+  const size_t rb = net->fmt == SNN_W_FP32_12B ? 12 : 8;
+  const size_t off = field == 0 ? 0 : (net->fmt == SNN_W_FP32_12B ? 8 : 4);
+  char* p = static_cast<char*>(net->recs) + index * rb + off;
+  uint32_t word = 0;
+  CK(cudaMemcpyAsync(&word, p, 4, cudaMemcpyDeviceToHost, net->stream));
+  CK(cudaStreamSynchronize(net->stream));
+  word = field == 0 ? value : ((word & ~0xFFu) | value);
+  CK(cudaMemcpyAsync(p, &word, 4, cudaMemcpyHostToDevice, net->stream));
+  CK(cudaStreamSynchronize(net->stream));
+  return SNN_OK;
+}
+
 int snn_destroy(snn_net* net) {
   if (!net) return SNN_OK;
   cudaSetDevice(net->device);
   if (net->stream) cudaStreamSynchronize(net->stream);
+  if (kChecked && net->ctl) {
+    unsigned flags = 0;
+    if (cudaMemcpy(&flags, &net->ctl->error_flags, sizeof flags,
+                   cudaMemcpyDeviceToHost) == cudaSuccess)
+      note_check_failure(net, flags);
+    cudaGetLastError();
+  }
   drop_graphs(net);
   for (cudaEvent_t e : net->ev) cudaEventDestroy(e);
   void* bufs[] = {net->V,        net->I,        net->J,       net->refr,

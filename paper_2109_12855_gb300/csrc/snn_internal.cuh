@@ -94,6 +94,15 @@ struct Ctl {
 // "No spike yet" for the spike-time fields of the plasticity state.
 constexpr int32_t kNoSpike = INT32_MIN;
 constexpr int kMaxStdpHistory = 32;
+constexpr uint32_t kMaxGatherParts = 64;  // exchange buffers of one delivery
+// SNN_CHECK builds (-DSNN_CHECK=1) compile bounds checks into the kernels:
+// a record whose target or delay lies outside the store's ranges, a tile
+// index entry outside its row, or a spike list whose chunk offsets are not
+// non-decreasing is skipped and raises SNN_ERRF_CHECK instead of being used.
+#ifndef SNN_CHECK
+#define SNN_CHECK 0
+#endif
+constexpr bool kChecked = SNN_CHECK != 0;
 
 // Plasticity state of a net with STDP on its E->E synapses (see
 // snn_kernels.cu); all pointers null for a static net.
@@ -236,6 +245,16 @@ struct NetView {
   float mean_run;           // synapses per (source, tile): the mean run length
   SpikeEntry* list;         // interval list, capacity list_cap
   uint64_t list_cap;
+  // partition exchange: the update also writes its spikes as {src, t} pairs
+  // into xbuf (word 0: count; entries from word 4; capacity xcap).  A
+  // delivery with gx set takes its list from gx_parts such buffers (gx_stride
+  // words apart, capacity gx_cap entries each) instead of `list`.
+  uint32_t* xbuf;
+  uint32_t xcap;
+  uint32_t gx_parts;
+  const uint32_t* gx;
+  uint64_t gx_stride;
+  uint32_t gx_cap;
   uint32_t* log_src;        // spike log, capacity log_cap
   int32_t* log_t;
   uint64_t log_cap;

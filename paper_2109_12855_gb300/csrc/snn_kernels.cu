@@ -213,6 +213,7 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
   __shared__ uint32_t s_thr[kMaxPoisson];
   __shared__ uint8_t s_guide[256];
   __shared__ unsigned long long s_base[2];
+  __shared__ uint32_t s_xbase;
   for (int k = threadIdx.x; k < c.n_thr; k += blockDim.x) s_thr[k] = c.thr[k];
   for (int k = threadIdx.x; k < 256; k += blockDim.x) s_guide[k] = c.guide[k];
   const long long t0 = from_ctl ? v.ctl->t_now : t0_arg;
@@ -334,6 +335,7 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
         const unsigned long long logb =
             v.log_cap ? atomicAdd(&v.ctl->log_count, (unsigned long long)tot_cnt)
                       : 0ull;
+        s_xbase = v.xbuf ? atomicAdd(v.xbuf, tot_cnt) : 0u;
         atomicAdd(&v.ctl->pending_events, tot_deg);
         atomicAdd(&v.ctl->spikes, (unsigned long long)tot_cnt);
         if ((uint32_t)old + (unsigned long long)tot_ch > 0xFFFFFFFFull)
@@ -361,6 +363,15 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
           if (v.tile_off && k == 0) prefetch_row_l2(v, v.g0 + i);
         } else {
           atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_SPIKE_LIST);
+        }
+        if (v.xbuf) {  // the partition exchange's copy of the list
+          const uint32_t xi = s_xbase + ex_cnt + k;
+          if (xi < v.xcap) {
+            reinterpret_cast<uint2*>(v.xbuf + 4)[xi] =
+                make_uint2(v.g0 + i, (uint32_t)(int32_t)t);
+          } else {
+            atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_SPIKE_LIST);
+          }
         }
         if (v.log_cap) {
           const unsigned long long li = logb + ex_cnt + k;
@@ -484,6 +495,19 @@ __device__ __forceinline__ void unpack<SNN_W_BF16_8B>(
   w = __uint_as_float(m0 & 0xFFFF0000u);
 }
 
+// Bounds-checked builds: a record whose target lies outside [lo, lo + width)
+// (or the net) or whose delay lies outside the store's range is skipped
+// and flagged.  Production builds compile this to `true`.
+__device__ __forceinline__ bool rec_in_bounds(const NetView& v, uint32_t tgt,
+                                              uint32_t d, uint32_t lo,
+                                              uint32_t width) {
+  if (!kChecked) return true;
+  const bool ok = tgt - lo < width && tgt < v.n && d >= (uint32_t)v.d_min &&
+                  d <= (uint32_t)v.d_max;
+  if (!ok) atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_CHECK);
+  return ok;
+}
+
 template <int FMT, bool COUNT>
 __global__ void __launch_bounds__(kDelThreads)
 k_deliver(NetView v, unsigned long long* pair_p, unsigned int* done_p,
@@ -523,9 +547,17 @@ k_deliver(NetView v, unsigned long long* pair_p, unsigned int* done_p,
     }
     uint32_t j = lo;
     uint64_t c = c_begin;
+    uint32_t prev_choff = 0u;
     while (c < c_end && j < n_sp) {
       const SpikeEntry e = list[j];
       ++j;
+      if (kChecked) {  // the merge-path split needs non-decreasing offsets
+        if (e.choff < prev_choff) {
+          atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_CHECK);
+          break;
+        }
+        prev_choff = e.choff;
+      }
       if (e.src >= v.n_src) continue;
       const uint64_t beg = v.row_ptr[e.src], end = v.row_ptr[e.src + 1];
       const uint64_t last = (uint64_t)e.choff + row_chunks(beg, end, CH);
@@ -553,6 +585,7 @@ k_deliver(NetView v, unsigned long long* pair_p, unsigned int* done_p,
                 uint32_t tgt, d;
                 float w;
                 unpack<FMT>(x[g], q, tgt, d, w);
+                if (!rec_in_bounds(v, tgt, d, 0u, v.n)) continue;
                 const size_t cell =
                     (size_t)(((uint32_t)t + d) & v.slot_mask) * v.pitch + tgt;
                 red_add_f32(v.rb + cell, w);
@@ -810,7 +843,7 @@ __device__ __noinline__ StdpOut stdp_weight(float w, int32_t t, uint32_t d,
 // a few dozen records (BF16, static): more runs per warp pass, fewer slots
 // per run.
 template <int FMT, bool COUNT, bool PL, bool FAST = false, bool ONE = false,
-          bool SHORT = false>
+          bool SHORT = false, bool GX = false>
 __device__ __forceinline__ void deliver_tile_body(
     const NetView& v, unsigned long long* pair_p, unsigned int* done_p,
     const SpikeEntry* __restrict__ list, int from_list_range, int advance_time,
@@ -844,7 +877,9 @@ __device__ __forceinline__ void deliver_tile_body(
   // the length are never used.
   constexpr int kDU = PL ? 1 : 4;
   SpikeEntry pre[kDU];
-  const bool spec = !from_list_range;
+  // GX: the list is gathered from the partitions' exchange buffers (v.gx)
+  constexpr bool gathered = GX;
+  const bool spec = !from_list_range && !gathered;
   if (spec) {
 #pragma unroll
     for (int u = 0; u < kDU; ++u) {
@@ -856,9 +891,27 @@ __device__ __forceinline__ void deliver_tile_body(
   // thread 0 derives the fixed-point scales meanwhile
   const unsigned long long pr =
       *reinterpret_cast<volatile unsigned long long*>(pair_p);
-  const uint32_t n_sp = (uint32_t)(pr >> 32);
+  uint32_t n_sp = (uint32_t)(pr >> 32);
+  // a list gathered from the partitions: the parts' counts (each at most
+  // its capacity) and their starts in the union, in part order
+  __shared__ uint32_t s_gstart[kMaxGatherParts + 1];
+  if (gathered) {
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (uint32_t p = 0; p < v.gx_parts; ++p) {
+        s_gstart[p] = run;
+        run += min(v.gx[(uint64_t)p * v.gx_stride], v.gx_cap);
+      }
+      s_gstart[v.gx_parts] = run;
+    }
+    __syncthreads();
+    n_sp = s_gstart[v.gx_parts];
+  }
   long long base;
   bool inwin;
+  // gathered lists: steps of this interval lie in [t_now, t_now + iv_span)
+  const long long t_now = gathered ? v.ctl->t_now : 0ll;
+  const uint32_t iv_span = (uint32_t)(W - (uint32_t)(v.d_max - v.d_min));
   if (from_list_range) {
     const long long tmin = v.ctl->ext_tmin, tmax = v.ctl->ext_tmax;
     base = tmin + v.d_min;
@@ -922,6 +975,8 @@ __device__ __forceinline__ void deliver_tile_body(
   }
   const uint32_t row_stride = v.n_tiles + 1;
   FixScale fx{};  // thread 0's s_fx, read after the first barrier
+  __shared__ unsigned long long s_events;  // gathered lists: this CTA's events
+  if (gathered && threadIdx.x == 0) s_events = 0ull;
 
   // one event: cell = d TW + tgt + off, off = (t - base) TW - tgt_lo per run
   auto add = [&](uint32_t tgt, int32_t t, int32_t off, uint32_t d, float w) {
@@ -1003,6 +1058,7 @@ __device__ __forceinline__ void deliver_tile_body(
           uint32_t tgt, d;
           float w;
           rec_fields(r[u][q], tgt, d, w);
+          if (!rec_in_bounds(v, tgt, d, tgt_lo, TW)) continue;
           if (pl && tgt < v.sp.n_exc)
             w = plastic(tgt, k0 + u, sd.t, d, wv[u][q], sd.beg + idx);
           add(tgt, sd.t, off, d, w);
@@ -1012,6 +1068,7 @@ __device__ __forceinline__ void deliver_tile_body(
         uint32_t tgt, d;
         float w;
         rec_fields(load_rec<FMT>(v.recs, sd.beg + idx), tgt, d, w);
+        if (!rec_in_bounds(v, tgt, d, tgt_lo, TW)) continue;
         if (pl && tgt < v.sp.n_exc)
           w = plastic(tgt, k0 + u, sd.t, d, __ldcs(v.sp.wp + sd.beg + idx),
                       sd.beg + idx);
@@ -1024,13 +1081,34 @@ __device__ __forceinline__ void deliver_tile_body(
   // thread in flight (the first ones already read), then their tile-index
   // words and row starts
   auto describe = [&](uint32_t j0, uint32_t nb) {
+    unsigned long long my_events = 0;
     for (uint32_t k0 = threadIdx.x; k0 < nb; k0 += kDU * blockDim.x) {
       SpikeEntry e[kDU];
       const bool have = spec && j0 == 0 && k0 == threadIdx.x;
 #pragma unroll
       for (int u = 0; u < kDU; ++u) {
         const uint32_t k = k0 + u * blockDim.x;
-        if (k < nb) e[u] = have ? pre[u] : list[j0 + k];
+        if (k < nb) {
+          if (gathered) {
+            const uint32_t g = j0 + k;
+            uint32_t p = 0;
+            while (s_gstart[p + 1] <= g) ++p;
+            const uint2 x = reinterpret_cast<const uint2*>(
+                v.gx + (uint64_t)p * v.gx_stride + 4)[g - s_gstart[p]];
+            // entries come from the caller's buffers: a source outside the
+            // store or a step outside this interval is skipped and flagged
+            // (its cells would lie outside the tile's window)
+            const bool ok = x.x < v.n_src &&
+                            (uint32_t)((int32_t)x.y - (int32_t)t_now) < iv_span;
+            if (!ok) atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_BAD_SOURCE);
+            e[u].src = ok ? x.x : 0xFFFFFFFFu;
+            e[u].t = (int32_t)x.y;
+            e[u].choff = 0;
+            e[u].pad = 0;
+          } else {
+            e[u] = have ? pre[u] : list[j0 + k];
+          }
+        }
       }
 #pragma unroll
       for (int u = 0; u < kDU; ++u) {
@@ -1042,6 +1120,11 @@ __device__ __forceinline__ void deliver_tile_body(
             const uint32_t a = to[0], b = to[1];
             sd.beg = v.row_ptr[e[u].src] + a;
             sd.len = b - a;
+            if (kChecked && (b < a || sd.beg + sd.len > v.row_ptr[e[u].src + 1])) {
+              atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_CHECK);
+              sd.len = 0;
+            }
+            if (gathered) my_events += sd.len;
           }
           s_desc[k] = sd;
           if (PL) {
@@ -1051,6 +1134,11 @@ __device__ __forceinline__ void deliver_tile_body(
           }
         }
       }
+    }
+    if (gathered) {  // (all threads of the CTA reach this)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) my_events += __shfl_xor_sync(kFull, my_events, o);
+      if (lane == 0 && my_events) atomicAdd(&s_events, my_events);
     }
   };
   // next U runs for this warp (shared counter: warps that met short runs or
@@ -1141,9 +1229,12 @@ __device__ __forceinline__ void deliver_tile_body(
       atomicAdd(&v.ctl->stdp_truncated, s_pl[1]);
     }
   }
-  // The last CTA to finish clears the list counters and advances the clock.
+  // The last CTA to finish clears the list counters and advances the clock
+  // (a gathered list's events -- its spikes' runs onto this partition's
+  // targets -- are counted by the CTAs themselves).
   __syncthreads();
   if (threadIdx.x == 0) {
+    if (gathered && s_events) atomicAdd(&v.ctl->pending_events, s_events);
     __threadfence();
     unsigned prev = atomicAdd(done_p, 1u);
     if (prev == v.n_tiles - 1) {
@@ -1151,20 +1242,20 @@ __device__ __forceinline__ void deliver_tile_body(
       *done_p = 0u;
       if (advance_time) {  // the interval's own list: commit its events
         v.ctl->t_now += v.ctl->iv_steps;
-        v.ctl->events += v.ctl->pending_events;
-        v.ctl->pending_events = 0ull;
+        v.ctl->events += atomicExch(&v.ctl->pending_events, 0ull);
       }
     }
   }
 }
 
-template <int FMT, bool COUNT, bool PL, bool FAST, bool ONE, bool SHORT>
+template <int FMT, bool COUNT, bool PL, bool FAST, bool ONE, bool SHORT,
+          bool GX>
 __global__ void __launch_bounds__(kTileThreads, 1)
 k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
                 const SpikeEntry* __restrict__ list, int from_list_range,
                 int advance_time, uint32_t desc_off, uint32_t desc_cap) {
   extern __shared__ __align__(16) int acc_mem[];
-  deliver_tile_body<FMT, COUNT, PL, FAST, ONE, SHORT>(
+  deliver_tile_body<FMT, COUNT, PL, FAST, ONE, SHORT, GX>(
       v, pair_p, done_p, list, from_list_range, advance_time, blockIdx.x,
       acc_mem, desc_off, desc_cap);
 }
@@ -1454,6 +1545,12 @@ cudaError_t launch_update(const NetView& v, const UpdConst& c, int n_steps,
         cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
       sms.store(m, std::memory_order_relaxed);
   }
+  // the exchange buffer's count restarts with every interval (after every
+  // delivery that read the previous one, in stream order)
+  if (v.xbuf) {
+    const cudaError_t e = cudaMemsetAsync(v.xbuf, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+  }
   if (blocks > 3u * (unsigned)std::max(sms.load(std::memory_order_relaxed), 1))
     k_update<4><<<blocks, kUpdThreads, 0, s>>>(v, c, n_steps, from_ctl_time, t0);
   else
@@ -1542,31 +1639,34 @@ cudaError_t desc_layout(size_t used, size_t dyn_max, bool plastic,
 }
 
 template <int FMT, bool COUNT, bool PL, bool FAST = false, bool ONE = false,
-          bool SHORT = false>
+          bool SHORT = false, bool GX = false>
 cudaError_t launch_tiled_t(const NetView& v, unsigned long long* pair,
                            unsigned int* done, const SpikeEntry* list,
                            int from_list_range, int advance_time,
                            cudaStream_t s) {
   static std::atomic<uint32_t> lim[64];
   size_t dm = 0;
-  cudaError_t e = allow_tile_smem(k_deliver_tiled<FMT, COUNT, PL, FAST, ONE, SHORT>,
-                                  lim, &dm);
+  cudaError_t e = allow_tile_smem(
+      k_deliver_tiled<FMT, COUNT, PL, FAST, ONE, SHORT, GX>, lim, &dm);
   if (e != cudaSuccess) return e;
   DescLayout dl;
   e = desc_layout(tiled_smem_bytes(v), dm, PL, &dl);
   if (e != cudaSuccess) return e;
-  k_deliver_tiled<FMT, COUNT, PL, FAST, ONE, SHORT>
+  k_deliver_tiled<FMT, COUNT, PL, FAST, ONE, SHORT, GX>
       <<<v.n_tiles, kTileThreads, dl.smem, s>>>(
       v, pair, done, list, from_list_range, advance_time, dl.off, dl.cap);
   return cudaGetLastError();
 }
 
-cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
-                                 unsigned int* done, const SpikeEntry* list,
-                                 int from_list_range, int advance_time,
-                                 cudaStream_t s) {
-#define SNN_TILED(F, C, P) \
-  launch_tiled_t<F, C, P>(v, pair, done, list, from_list_range, advance_time, s)
+template <bool GX>
+cudaError_t launch_deliver_tiled_gx(const NetView& v, unsigned long long* pair,
+                                    unsigned int* done, const SpikeEntry* list,
+                                    int from_list_range, int advance_time,
+                                    cudaStream_t s) {
+#define SNN_TILED(F, C, P)                                                   \
+  launch_tiled_t<F, C, P, false, false, false, GX>(v, pair, done, list,     \
+                                                   from_list_range,         \
+                                                   advance_time, s)
   // an interval's own list: the scales exist for every spike count when
   // they exist for the largest (E = max in-degree x spikes per neuron)
   bool interval_exact = false;
@@ -1575,7 +1675,9 @@ cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
         (uint64_t)v.k_in_max * (v.spikes_per_iv ? v.spikes_per_iv : 1u), v.max_abs_w);
     interval_exact = qs >= 0 && (v.acc_words == 2 || qs >= v.acc_qs_min);
   }
-  if (v.plastic) {
+  if constexpr (GX) {  // gathered lists: static nets only
+    if (v.plastic) return cudaErrorNotSupported;
+  } else if (v.plastic) {
     if (interval_exact)
       return v.fmt == SNN_W_FP32_12B
                  ? launch_tiled_t<SNN_W_FP32_12B, false, true, true>(
@@ -1591,17 +1693,19 @@ cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
   {
     if (interval_exact) {
       if (v.fmt == SNN_W_FP32_12B)
-        return launch_tiled_t<SNN_W_FP32_12B, false, false, true>(
-            v, pair, done, list, 0, advance_time, s);
+        return launch_tiled_t<SNN_W_FP32_12B, false, false, true, false,
+                              false, GX>(v, pair, done, list, 0, advance_time, s);
       if (v.acc_words == 1)
         // runs of a few dozen records: two slots for six runs per pass
         return v.mean_run < 48.f
-                   ? launch_tiled_t<SNN_W_BF16_8B, false, false, true, true, true>(
-                         v, pair, done, list, 0, advance_time, s)
-                   : launch_tiled_t<SNN_W_BF16_8B, false, false, true, true>(
-                         v, pair, done, list, 0, advance_time, s);
-      return launch_tiled_t<SNN_W_BF16_8B, false, false, true, false>(
-          v, pair, done, list, 0, advance_time, s);
+                   ? launch_tiled_t<SNN_W_BF16_8B, false, false, true, true,
+                                    true, GX>(v, pair, done, list, 0,
+                                              advance_time, s)
+                   : launch_tiled_t<SNN_W_BF16_8B, false, false, true, true,
+                                    false, GX>(v, pair, done, list, 0,
+                                               advance_time, s);
+      return launch_tiled_t<SNN_W_BF16_8B, false, false, true, false, false,
+                            GX>(v, pair, done, list, 0, advance_time, s);
     }
   }
   if (v.fmt == SNN_W_FP32_12B)
@@ -1610,6 +1714,18 @@ cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
   return v.counts ? SNN_TILED(SNN_W_BF16_8B, true, false)
                   : SNN_TILED(SNN_W_BF16_8B, false, false);
 #undef SNN_TILED
+}
+
+cudaError_t launch_deliver_tiled(const NetView& v, unsigned long long* pair,
+                                 unsigned int* done, const SpikeEntry* list,
+                                 int from_list_range, int advance_time,
+                                 cudaStream_t s) {
+  if (v.gx) {
+    if (from_list_range) return cudaErrorInvalidValue;
+    return launch_deliver_tiled_gx<true>(v, pair, done, list, 0, advance_time, s);
+  }
+  return launch_deliver_tiled_gx<false>(v, pair, done, list, from_list_range,
+                                        advance_time, s);
 }
 
 cudaError_t launch_fill_i32(int32_t* p, int32_t value, uint64_t n,

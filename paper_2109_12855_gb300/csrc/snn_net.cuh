@@ -49,6 +49,9 @@ struct snn_net {
   void* recs = nullptr;
   uint64_t n_syn = 0, recs_bytes = 0;
   uint32_t* tile_off = nullptr;  // [n][n_tiles + 1]
+  bool check_noted = false;      // SNN_ERRF_CHECK counted (checked builds)
+  uint32_t* xbuf = nullptr;      // caller's exchange buffer (snn_set_exchange)
+  uint32_t xcap = 0;
   uint32_t tile_w = 0, n_tiles = 0;
   int lo_bits = 0;
   int window = 0;
@@ -117,6 +120,12 @@ struct snn_net {
                                   : 0.f;
     v.list = list;
     v.list_cap = list_cap;
+    v.xbuf = xbuf;
+    v.xcap = xcap;
+    v.gx = nullptr;
+    v.gx_parts = 0;
+    v.gx_stride = 0;
+    v.gx_cap = 0;
     v.log_src = log_src;
     v.log_t = log_t;
     v.log_cap = log_cap;

@@ -1,8 +1,10 @@
-"""Build ``libsnn.so`` (the sm_103a CUDA library behind ``include/snn.h``).
+"""Build ``libsnn.so`` (the sm_103a CUDA library behind ``include/snn.h``)
+and its bounds-checked variant ``libsnn_check.so`` (the same sources with
+``-DSNN_CHECK=1``; the binding loads it when ``SNN_CHECKED=1`` is set).
 
-The translation units are compiled in parallel with nvcc for
-``arch=compute_103a,code=sm_103a`` and linked into a shared library inside
-the package directory (kept in-tree, next to the binding that loads it).
+The translation units of both are compiled in parallel with nvcc for
+``arch=compute_103a,code=sm_103a`` and linked into shared libraries inside
+the package directory (kept in-tree, next to the binding that loads them).
 """
 from __future__ import annotations
 
@@ -17,6 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsnn.so")
+LIB_CHECKED = os.path.join(PKG, "libsnn_check.so")
 SOURCES = ["snn_kernels.cu", "snn_build.cu", "snn_api.cu", "snn_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -38,18 +41,33 @@ def _inputs_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
+def lib_path() -> str:
+    """The library the binding loads: the bounds-checked variant when the
+    environment sets SNN_CHECKED=1, else the production one."""
+    return LIB_CHECKED if os.environ.get("SNN_CHECKED") == "1" else LIB
+
+
+def _fresh(lib: str) -> bool:
+    return os.path.exists(lib) and os.path.getmtime(lib) >= _inputs_mtime()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= _inputs_mtime()):
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+    """Build both variants (the stale ones); returns the loaded variant's
+    path."""
+    todo = [(lib, chk) for lib, chk in ((LIB, False), (LIB_CHECKED, True))
+            if force or not _fresh(lib)]
+    if not todo:
+        return lib_path()
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if verbose else []
 
-    def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src),
-               "-o", obj]
+    def compile_one(job):
+        src, chk = job
+        out = OUT_DIR + ("_check" if chk else "")
+        os.makedirs(out, exist_ok=True)
+        obj = os.path.join(out, src.replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *FLAGS, *(["-DSNN_CHECK=1"] if chk else []), *extra,
+               "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -57,15 +75,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    jobs = [(src, chk) for _, chk in todo for src in SOURCES]
+    with ThreadPoolExecutor(len(jobs)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for k, (lib, _) in enumerate(todo):
+        tmp = lib + ".tmp%d" % os.getpid()
+        mine = objs[k * len(SOURCES):(k + 1) * len(SOURCES)]
+        r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *mine],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
+    return lib_path()
 
 
 if __name__ == "__main__":

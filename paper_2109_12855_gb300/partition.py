@@ -18,6 +18,17 @@ the union of the partitions is bit-identical to the whole net.  The exchange
 is the only collective: ``allgather_spikes`` does it with torch.distributed
 (gloo with host tensors, NCCL with device tensors); this module only moves
 data, the simulation runs in the library.
+
+``DeviceExchange`` runs the same cycle without any host round trip: each
+update also writes its spikes into a fixed-capacity device buffer
+(``snn_set_exchange``), the buffers of all partitions are gathered on the
+device (one ``all_gather_into_tensor`` on the current stream across ranks;
+nothing at all when this process holds every partition), and each delivery
+reads the gathered buffers directly (``snn_deliver_exchanged``)::
+
+    update every partition          (snn_update: also fills its buffer)
+    all-gather the fixed buffers    (NCCL, device to device; none in-process)
+    deliver from the gathered rows  (snn_deliver_exchanged)
 """
 from __future__ import annotations
 
@@ -143,3 +154,153 @@ def simulate(nets, n_steps: int, t0: int | None = None, gather=None):
         events += run_interval(nets, t, m, gather)
         t += m
     return events
+
+
+# ---------------------------------------------------------------------------
+# device-resident exchange (no host synchronisation per interval)
+
+EXCHANGE_HEADER_WORDS = 4  # count word + 3 alignment words before the entries
+
+
+def exchange_words(cap: int) -> int:
+    """32-bit words of one exchange buffer of at least ``cap`` entries
+    (rows of whole 16-byte units)."""
+    w = EXCHANGE_HEADER_WORDS + 2 * cap
+    return (w + 3) // 4 * 4
+
+
+def row_capacity(words: int) -> int:
+    """Entries a row of ``words`` words holds: the clamp the delivery applies
+    to a row's count (a producer writing the row takes the same capacity)."""
+    return (words - EXCHANGE_HEADER_WORDS) // 2
+
+
+class DeviceExchange:
+    """Exchange buffers of the local partitions ``nets`` (all on this
+    process's current CUDA device and on the stream the caller runs them on:
+    the collective and the library calls must be ordered on one stream).
+
+    ``local`` holds one row per local partition, ``gathered`` the rows of
+    every partition of every rank in rank order (the same tensor when there
+    is one rank).  ``cap`` entries per row: by default the largest
+    ``snn_exchange_capacity`` of all partitions (``reduce_max`` maps it to
+    the maximum over ranks), which can never overflow."""
+
+    def __init__(self, nets, cap: int | None = None, group=None,
+                 reduce_max: Callable | None = None):
+        import torch
+        import torch.distributed as dist
+        self.nets = list(nets)
+        self.world = (dist.get_world_size(group)
+                      if dist.is_available() and dist.is_initialized() else 1)
+        # one stream orders every update before every delivery that reads
+        # its buffer (and, across ranks, the collective between them)
+        streams = {snn.snn_get_stream(net.h) for net in self.nets}
+        if len(streams) > 1:
+            raise ValueError("partitions sharing exchange buffers must run on "
+                             "one stream (pass it to create())")
+        if self.world > 1 and streams != {torch.cuda.current_stream().cuda_stream}:
+            raise ValueError("the partitions must run on the current CUDA "
+                             "stream, where the all-gather is ordered")
+        if cap is None:
+            cap = max(snn.snn_exchange_capacity(net.h) for net in self.nets)
+            if reduce_max is not None:
+                cap = int(reduce_max(cap))
+        words = exchange_words(int(cap))
+        self.cap = row_capacity(words)  # the readers' clamp, whole row
+        self.group = group
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.local = torch.zeros((len(self.nets), words), dtype=torch.int32,
+                                 device=dev)
+        self.gathered = self.local if self.world == 1 else torch.zeros(
+            (self.world * len(self.nets), words), dtype=torch.int32, device=dev)
+        torch.cuda.current_stream().synchronize()  # zeroed before first use
+        for k, net in enumerate(self.nets):
+            snn.snn_set_exchange(net.h, self.local[k], self.cap)
+
+    def gather(self):
+        """All-gather the local rows into ``gathered`` (asynchronous on the
+        current stream; nothing to do for one rank)."""
+        if self.world > 1:
+            allgather_rows(self.local, self.gathered, self.group)
+
+    def close(self):
+        for net in self.nets:
+            if net.h:
+                snn.snn_set_exchange(net.h, None)
+        self.nets = []
+
+
+def allgather_rows(local, gathered=None, group=None):
+    """All-gather of fixed-size exchange rows over torch.distributed: every
+    rank's ``local`` (rows x words) into ``gathered`` (ranks x rows x words,
+    rank-major), one collective with no size exchange before it (NCCL for
+    CUDA tensors, gloo for CPU tensors).  Returns ``gathered``."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size(group)
+    if gathered is None:
+        gathered = torch.empty((ws * local.shape[0],) + tuple(local.shape[1:]),
+                               dtype=local.dtype, device=local.device)
+    dist.all_gather_into_tensor(gathered, local, group=group)
+    return gathered
+
+
+def run_interval_exchanged(nets, xch: DeviceExchange, t0: int, steps: int):
+    """One interval of the partitioned network with the device exchange:
+    asynchronous, no host synchronisation."""
+    for net in nets:
+        snn.snn_update(net.h, t0, steps)
+    xch.gather()
+    for net in nets:
+        snn.snn_deliver_exchanged(net.h, xch.gathered)
+
+
+def simulate_exchanged(nets, xch: DeviceExchange, n_steps: int,
+                       t0: int | None = None, interval: int | None = None):
+    """Advance the partitions by n_steps with the device exchange (intervals
+    of the nets' interval length, a shorter last one).  Asynchronous: read
+    the events afterwards from the nets' statistics."""
+    if interval is None or t0 is None:
+        st = nets[0].stats()
+        interval = st.interval if interval is None else interval
+        t0 = st.t_now if t0 is None else t0
+    t, end = t0, t0 + n_steps
+    while t < end:
+        m = min(interval, end - t)
+        run_interval_exchanged(nets, xch, t, m)
+        t += m
+    return t
+
+
+def encode_exchange(src, t, cap: int) -> np.ndarray:
+    """One exchange row (int32 words, ``exchange_words(cap)`` of them) holding
+    the list (src, t); a list longer than the row keeps its count and the
+    entries that fit, as an overflowing update does."""
+    src = np.asarray(src, np.uint32)
+    t = np.asarray(t, np.int32)
+    row = np.zeros(exchange_words(cap), np.uint32)
+    row[0] = len(src)
+    k = min(len(src), row_capacity(len(row)))
+    e = row[EXCHANGE_HEADER_WORDS:EXCHANGE_HEADER_WORDS + 2 * k]
+    e[0::2] = src[:k]
+    e[1::2] = t[:k].view(np.uint32)
+    return row.view(np.int32)
+
+
+def decode_exchange(rows):
+    """(src, t) lists of exchange rows (a CPU int32 array or tensor whose
+    rows are buffers), concatenated in row order; counts above a row's
+    capacity are clamped as the delivery clamps them."""
+    a = np.asarray(rows.cpu() if hasattr(rows, "cpu") else rows)
+    a = a.reshape(-1, a.shape[-1]).view(np.uint32)
+    cap = row_capacity(a.shape[1])
+    srcs, ts = [], []
+    for r in a:
+        n = min(int(r[0]), cap)
+        e = r[EXCHANGE_HEADER_WORDS:EXCHANGE_HEADER_WORDS + 2 * n]
+        srcs.append(e[0::2])
+        ts.append(e[1::2].view(np.int32))
+    return (np.concatenate(srcs).astype(np.uint32) if srcs else
+            np.zeros(0, np.uint32),
+            np.concatenate(ts).astype(np.int32) if ts else np.zeros(0, np.int32))

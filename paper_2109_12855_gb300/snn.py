@@ -12,7 +12,9 @@ import os
 
 import numpy as np
 
-from .native import LIB
+from .native import lib_path
+
+LIB = lib_path()
 
 SNN_OK = 0
 SNN_E_OOM, SNN_E_ARG, SNN_E_STATE, SNN_E_TIMEOUT, SNN_E_OVERFLOW, SNN_E_CUDA = \
@@ -24,6 +26,7 @@ SNN_ERRF_SPIKE_LIST, SNN_ERRF_SPIKE_LOG, SNN_ERRF_BAD_SOURCE, SNN_ERRF_CHUNKS = 
     1, 2, 4, 8
 SNN_ERRF_TIMEOUT = 16
 SNN_ERRF_SCALES = 32
+SNN_ERRF_CHECK = 64
 
 EXPORTS = [
     "snn_abi_version", "snn_last_error", "snn_default_params",
@@ -42,7 +45,9 @@ EXPORTS = [
     "snn_read_weights", "snn_read_spike_stats", "snn_clear_spike_stats",
     "snn_read_pending", "snn_get_bounds", "snn_set_bounds",
     "snn_deliver_gathered", "snn_server_set_option", "snn_server_cancel",
-    "snn_debug_fail_allocations",
+    "snn_debug_fail_allocations", "snn_exchange_capacity",
+    "snn_set_exchange", "snn_deliver_exchanged", "snn_get_stream",
+    "snn_checked", "snn_debug_check_failures", "snn_debug_poke_record",
 ]
 SNN_REQ_QUEUED, SNN_REQ_BUILDING, SNN_REQ_RUNNING, SNN_REQ_DONE = 0, 1, 2, 3
 SNN_REQ_FAILED = -1
@@ -209,6 +214,15 @@ def lib():
             "snn_server_destroy": ([_P], C.c_int),
             "snn_server_set_option": ([_P, C.c_int32, C.c_double], C.c_int),
             "snn_server_cancel": ([_P, C.c_uint64], C.c_int),
+            "snn_exchange_capacity": ([_P, C.POINTER(C.c_uint64)], C.c_int),
+            "snn_get_stream": ([_P, C.POINTER(C.c_void_p)], C.c_int),
+            "snn_checked": ([], C.c_int),
+            "snn_debug_check_failures": ([], C.c_uint64),
+            "snn_debug_poke_record": ([_P, C.c_uint64, C.c_int, C.c_uint32],
+                                      C.c_int),
+            "snn_set_exchange": ([_P, _P, C.c_uint64], C.c_int),
+            "snn_deliver_exchanged": ([_P, _P, C.c_uint32, C.c_uint64],
+                                      C.c_int),
             "snn_debug_fail_allocations": ([C.c_int64, C.c_int64], C.c_int),
         }
         for name, (args, res) in sig.items():
@@ -429,6 +443,71 @@ def snn_deliver_gathered(net, src, t, want_events: bool = True) -> int:
                                       _buf(t)[0] if n else None, n, mem,
                                       C.byref(ev) if want_events else None))
     return ev.value
+
+
+def snn_checked() -> bool:
+    """True for the bounds-checked build of the library."""
+    return bool(lib().snn_checked())
+
+
+def snn_debug_check_failures() -> int:
+    return int(lib().snn_debug_check_failures())
+
+
+def snn_debug_poke_record(net, index: int, field: int, value: int):
+    """Bounds-checked builds: corrupt one record's target (field 0) or delay
+    (field 1)."""
+    _check(lib().snn_debug_poke_record(net, index, field, value))
+
+
+def snn_get_stream(net) -> int:
+    """The cudaStream_t (as an int; 0 for the legacy default stream) the
+    net's work is enqueued on."""
+    p = C.c_void_p()
+    _check(lib().snn_get_stream(net, C.byref(p)))
+    return p.value or 0
+
+
+def snn_exchange_capacity(net) -> int:
+    """Entries an exchange buffer of this partition needs (never overflows)."""
+    n = C.c_uint64()
+    _check(lib().snn_exchange_capacity(net, C.byref(n)))
+    return n.value
+
+
+def snn_set_exchange(net, buf, cap_entries: int | None = None):
+    """Attach a device exchange buffer (a CUDA tensor of at least 16 + 8 cap
+    bytes) or detach it (buf None)."""
+    if buf is None:
+        _check(lib().snn_set_exchange(net, None, 0))
+        return
+    ptr, mem = _buf(buf)
+    if mem != SNN_MEM_DEVICE:
+        raise ValueError("the exchange buffer must be a CUDA tensor")
+    nbytes = buf.numel() * buf.element_size()
+    if cap_entries is None:
+        cap_entries = (nbytes - 16) // 8
+    if nbytes < 16 + 8 * cap_entries:
+        raise ValueError(f"{nbytes} bytes hold fewer than {cap_entries} entries")
+    _check(lib().snn_set_exchange(net, ptr, cap_entries))
+
+
+def snn_deliver_exchanged(net, parts, n_parts: int | None = None,
+                          stride_bytes: int | None = None):
+    """Deliver the pending interval from gathered exchange buffers: a CUDA
+    tensor whose first dimension is the parts (each row one buffer), or a
+    raw device pointer with n_parts and stride_bytes."""
+    if isinstance(parts, int):
+        ptr = parts
+    else:
+        ptr, mem = _buf(parts)
+        if mem != SNN_MEM_DEVICE:
+            raise ValueError("gathered exchange buffers must be a CUDA tensor")
+        if n_parts is None:
+            n_parts = parts.shape[0]
+        if stride_bytes is None:
+            stride_bytes = parts.stride(0) * parts.element_size()
+    _check(lib().snn_deliver_exchanged(net, ptr, n_parts, stride_bytes))
 
 
 def snn_get_bounds(net) -> snn_bounds:

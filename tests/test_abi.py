@@ -32,6 +32,25 @@ def test_library_exports_every_declared_symbol(libpath):
     assert declared <= exported, sorted(declared - exported)
 
 
+def test_checked_variant_exports_the_same_symbols(libpath):
+    """libsnn_check.so (SNN_CHECK bounds checks) is built beside libsnn.so
+    with the same ABI; each reports which variant it is."""
+    import ctypes
+    from paper_2109_12855_gb300 import native
+    assert os.path.exists(native.LIB_CHECKED)
+    out = subprocess.run(["nm", "-D", "--defined-only", native.LIB_CHECKED],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (snn_[a-z_0-9]+)\b", out))
+    assert set(_declared()) <= exported
+    prod = ctypes.CDLL(native.LIB)
+    chk = ctypes.CDLL(native.LIB_CHECKED)
+    assert prod.snn_checked() == 0 and chk.snn_checked() == 1
+    f = prod.snn_debug_poke_record
+    f.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                  ctypes.c_uint32]
+    assert f(None, 0, 0, 0) != 0  # refused: null net
+
+
 def test_binding_covers_the_header(libpath):
     from paper_2109_12855_gb300 import snn
     assert sorted(snn.EXPORTS) == _declared()
@@ -85,8 +104,9 @@ def test_binding_constants_match_header(libpath):
     """The binding's copies of the header's constants (the allocation-free
     scratch capacity, the status codes) equal the compiled values."""
     from paper_2109_12855_gb300 import snn
-    src = ('#include "snn.h"\n#include <stdio.h>\nint main(){printf("%u %d %d %d",'
-           '(unsigned)SNN_NOALLOC_MAX_SPIKES,SNN_E_ARG,SNN_E_STATE,SNN_E_TIMEOUT);}')
+    src = ('#include "snn.h"\n#include <stdio.h>\nint main(){printf("%u %d %d %d %u",'
+           '(unsigned)SNN_NOALLOC_MAX_SPIKES,SNN_E_ARG,SNN_E_STATE,SNN_E_TIMEOUT,'
+           '(unsigned)SNN_ERRF_CHECK);}')
     exe = os.path.join(ROOT, "paper_2109_12855_gb300", "_build", "consts")
     os.makedirs(os.path.dirname(exe), exist_ok=True)
     r = subprocess.run(["gcc", "-x", "c", "-I", os.path.join(ROOT, "include"),
@@ -96,4 +116,4 @@ def test_binding_constants_match_header(libpath):
     vals = [int(x) for x in subprocess.run([exe], capture_output=True,
                                            text=True).stdout.split()]
     assert vals == [snn.SNN_NOALLOC_MAX_SPIKES, snn.SNN_E_ARG, snn.SNN_E_STATE,
-                    snn.SNN_E_TIMEOUT]
+                    snn.SNN_E_TIMEOUT, snn.SNN_ERRF_CHECK]

@@ -1,6 +1,7 @@
-"""Multi-process path of bench.py on the CPU: with N ranks every rank runs an
-independent replica and the reported value is all ranks' events over the
-slowest rank's time.  Two gloo ranks check the reduction and the barrier."""
+"""Multi-process path of bench.py on the CPU: with N ranks the ranks split
+one network (or run replicas on request) and the reported value is all
+ranks' events over the slowest rank's time.  Two gloo ranks check the
+reduction and the barrier."""
 import os
 import socket
 
@@ -50,3 +51,16 @@ def test_single_process_reduction_is_identity():
     import bench
     assert not dist.is_initialized()
     assert bench.reduce_over_ranks(12.5, 77, 3.0) == (12.5, 77, 3.0)
+
+
+def test_several_ranks_partition_one_network_by_default():
+    import bench
+    up = bench.use_partition
+    assert up("balanced-112500-fp32", "simulate", 4, False, False)
+    assert not up("balanced-112500-fp32", "simulate", 4, False, True)
+    assert not up("balanced-112500-fp32", "simulate", 1, False, False)
+    assert up("balanced-112500-fp32", "simulate", 1, True, False)
+    assert not up("balanced-112500-stdp-bf16", "simulate", 4, False, False)
+    assert not up("deliver-112500-fp32", "deliver", 8, False, False)
+    with pytest.raises(SystemExit):
+        up("deliver-112500-fp32", "deliver", 1, True, False)
