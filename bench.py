@@ -855,12 +855,13 @@ def _lat_stats(lat):
 
 
 def serve_batched(snn, reqs, arrivals, budget, stream, clocks=None,
-                  persistent=0):
+                  persistent=0, exclusive=0):
     """Continuous batching: submit each request at its arrival time, step the
     server until every request finished.  Latency = completion - arrival."""
     sv = snn.snn_server_create(budget, reqs[0].params.weight_format, stream)
     try:
         snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_PERSISTENT, persistent)
+        snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_EXCLUSIVE, exclusive)
         ids, lag = [], []
         if clocks:
             clocks.start()
@@ -979,9 +980,11 @@ def run_serve(args, rate_hz, nu_ext):
     batched = serve_batched(snn, bf16, arrivals, budget, stream,
                             Clocks(gpu_index))
     persist = serve_batched(snn, bf16, arrivals, budget, stream, persistent=1)
+    excl = serve_batched(snn, bf16, arrivals, budget, stream, exclusive=1)
     serial = serve_serial(snn, fp32, arrivals, stream)
     sat_batched = serve_batched(snn, bf16, zero, budget, stream)
     sat_persist = serve_batched(snn, bf16, zero, budget, stream, persistent=1)
+    sat_excl = serve_batched(snn, bf16, zero, budget, stream, exclusive=1)
     sat_serial_bf16 = serve_serial(snn, [r for r in serve_requests(
         snn, stream_reqs, 1, nu_ext, False, off)], zero, stream)
     sat_serial = serve_serial(snn, fp32, zero, stream)
@@ -1034,6 +1037,7 @@ def run_serve(args, rate_hz, nu_ext):
             "batched_bf16": {"events_per_s": rate(batched), **batched},
             "batched_bf16_persistent": {"events_per_s": rate(persist),
                                         **persist},
+            "exclusive_bf16": {"events_per_s": rate(excl), **excl},
             "serial_fp32": {"events_per_s": rate(serial), **serial},
             "saturated": {
                 "batched_bf16": {"events_per_s": rate(sat_batched),
@@ -1045,6 +1049,9 @@ def run_serve(args, rate_hz, nu_ext):
                     "events_per_s": rate(sat_persist),
                     "wall_s": sat_persist["wall_s"],
                     "latency": sat_persist["latency"]},
+                "exclusive_bf16": {"events_per_s": rate(sat_excl),
+                                   "wall_s": sat_excl["wall_s"],
+                                   "latency": sat_excl["latency"]},
                 "serial_bf16": {"events_per_s": rate(sat_serial_bf16),
                                 "wall_s": sat_serial_bf16["wall_s"],
                                 "latency": sat_serial_bf16["latency"]},
@@ -1139,10 +1146,13 @@ def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
             return int(x.item())
         xch = PT.DeviceExchange([net], reduce_max=cap_max if ws > 1 else None)
 
+    iv_per_step = -(-steps_per // D)
+
     def step(t0):
-        if xch is not None:
-            return PT.simulate_exchanged([net], xch, steps_per, t0=t0,
-                                         interval=D)
+        if xch is not None:  # replays of 8-interval graphs, as snn_simulate
+            PT.simulate_exchanged([net], xch, steps_per, interval=D,
+                                  graph_intervals=8)
+            return t0 + steps_per
         t = t0
         while t < t0 + steps_per:
             m = min(D, t0 + steps_per - t)
@@ -1175,7 +1185,10 @@ def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
     b = net.stats()
     events = b.events_delivered - a.events_delivered
     spikes = b.spikes - a.spikes
-    launches = b.kernel_launches - a.kernel_launches
+    # update + delivery per interval (graph replays are not counted by the
+    # library's host counters)
+    launches = (2 * iv_per_step * args.steps if xch is not None
+                else b.kernel_launches - a.kernel_launches)
     ms_max, ev_all, sp_all = reduce_over_ranks(ms, events, spikes)
     if b.error_flags:
         raise RuntimeError(f"device error flags {b.error_flags:#x}")
@@ -1202,7 +1215,7 @@ def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
                    "exchange": ("host lists (read + variable all-gather)"
                                 if args.host_exchange else
                                 "device buffers (fixed all_gather_into_tensor, "
-                                "no host sync)")},
+                                "no host sync), 8-interval CUDA graphs")},
         "roofline": None, "cpu_baseline": None, "e2e": None,
         "gpu_launches": launches,
     }

@@ -300,8 +300,13 @@ int snn_finalize(snn_net* net);
 /* Update all neurons for n_steps (1 <= n_steps <= interval) grid steps
  * starting at absolute step t0 (Section 2.1), reading and clearing ring
  * buffer slots t0 .. t0+n_steps-1.  Spikes go to the pending interval list
- * (and to the log).  Errors: SNN_E_STATE if spikes of an earlier update are
- * still pending (deliver or discard them first), SNN_E_ARG. */
+ * (and to the log).  t0 = SNN_T_DEVICE starts at the net's device clock
+ * (where the last delivery left it) instead: the call then reads no host
+ * time, so an update + exchange + delivery sequence can be captured into a
+ * CUDA graph and replayed (the library's host copy of the clock is not
+ * advanced by replays).  Errors: SNN_E_STATE if spikes of an earlier update
+ * are still pending (deliver or discard them first), SNN_E_ARG. */
+#define SNN_T_DEVICE (-1)
 int snn_update(snn_net* net, int64_t t0, int32_t n_steps);
 
 /* Deliver the pending interval list produced by snn_update (Algorithm REF
@@ -423,14 +428,20 @@ int snn_deliver_gathered(snn_net* net, const uint32_t* src,
  *
  * Exchange buffer layout (little-endian 32-bit words, 16-byte aligned
  * device memory of the net's device, 16 + 8 cap bytes):
- *   word 0          spike count of the interval (zeroed in stream order
- *                   before each update, which then adds its spikes)
+ *   word 0          spike count of the interval: the update adds its
+ *                   spikes, the interval's delivery (snn_deliver_pending,
+ *                   snn_simulate, snn_deliver_gathered or
+ *                   snn_deliver_exchanged) clears it when it completes;
+ *                   snn_set_exchange and snn_discard_pending zero it
  *   words 1..3      unused (alignment)
  *   words 4 + 2k    entry k: global source index
  *   words 5 + 2k    entry k: emission step (int32)
  * A count above cap (an undersized buffer) keeps the first cap entries and
  * raises SNN_ERRF_SPIKE_LIST; snn_exchange_capacity gives the capacity that
- * can never overflow. */
+ * can never overflow.  Since a net's delivery clears its own buffer, other
+ * nets read it only through a copy taken before that delivery (the
+ * all-gather's output; in one process, a device copy), while a net may read
+ * its own attached buffer in place. */
 
 /* Entries an exchange buffer of this partition needs so that it never
  * overflows: local neurons x most spikes a neuron emits per interval (one
@@ -646,11 +657,21 @@ int snn_server_create(uint64_t mem_budget, int32_t weight_format,
  *    the launch then ends, the nets it ran fail with SNN_E_TIMEOUT
  *    (default 2^20, a fraction of a second).
  *  SNN_SERVE_OPT_STEP_US     target GPU time of a persistent step in
- *    microseconds (0: autotuned). */
+ *    microseconds (0: autotuned).
+ *  SNN_SERVE_OPT_EXCLUSIVE   1: each step runs ONE net alone, with the
+ *    single-net kernels and tiles (about one per SM) on the net's own
+ *    stream, for about 1 ms of GPU time: the running net with the least
+ *    remaining work (steps left x synapses; shortest remaining processing
+ *    time first), chosen again at every step, so a newly admitted smaller
+ *    request preempts a larger one within a step or two; two steps are kept
+ *    queued so that the GPU does not idle between them.  Builds still run
+ *    concurrently.  0 (default): lanes.  Changes only while no net runs
+ *    (SNN_E_STATE otherwise). */
 enum {
   SNN_SERVE_OPT_PERSISTENT = 0,
   SNN_SERVE_OPT_SPIN_LIMIT = 1,
-  SNN_SERVE_OPT_STEP_US = 2
+  SNN_SERVE_OPT_STEP_US = 2,
+  SNN_SERVE_OPT_EXCLUSIVE = 3
 };
 int snn_server_set_option(snn_server* sv, int32_t option, double value);
 

@@ -1056,14 +1056,17 @@ int snn_update(snn_net* net, int64_t t0, int32_t n_steps) {
   REQ(!net->pending, SNN_E_STATE, "spikes of the previous update are pending");
   REQ(n_steps >= 1 && n_steps <= net->interval, SNN_E_ARG,
       "n_steps %d outside [1, interval %d]", n_steps, net->interval);
-  REQ(t0 >= 0 && t0 + n_steps < (1ll << 31), SNN_E_ARG, "t0 out of range");
+  const bool dev_clock = t0 == SNN_T_DEVICE;
+  REQ(dev_clock || (t0 >= 0 && t0 + n_steps < (1ll << 31)), SNN_E_ARG,
+      "t0 out of range");
   int rc;
   if ((rc = set_device(net)) != SNN_OK) return rc;
-  CK(launch_update(net->view(), net->uc, n_steps, 0, t0, net->stream));
+  CK(launch_update(net->view(), net->uc, n_steps, dev_clock ? 1 : 0,
+                   dev_clock ? 0 : t0, net->stream));
   net->launches += 1;
   net->upd_launches += 1;
   net->pending = true;
-  net->t_host = t0 + n_steps;
+  net->t_host = dev_clock ? net->t_host + n_steps : t0 + n_steps;
   return SNN_OK;
 }
 
@@ -1090,6 +1093,8 @@ int snn_discard_pending(snn_net* net) {
                      net->stream));
   CK(cudaMemsetAsync(&net->ctl->pending_events, 0, sizeof(unsigned long long),
                      net->stream));
+  if (net->xbuf)  // no delivery will clear the discarded spikes
+    CK(cudaMemsetAsync(net->xbuf, 0, sizeof(uint32_t), net->stream));
   CK(cudaMemcpyAsync(&net->ctl->t_now, &net->t_host, sizeof(long long),
                      cudaMemcpyHostToDevice, net->stream));
   CK(cudaStreamSynchronize(net->stream));
@@ -1251,8 +1256,13 @@ int snn_set_exchange(snn_net* net, void* buf, uint64_t cap_entries) {
   // still write the old buffer, so the caller's reuse waits for it
   CK(cudaStreamSynchronize(net->stream));
   drop_graphs(net);
+  if (buf) {  // an empty list until the first update
+    CK(cudaMemsetAsync(buf, 0, 16, net->stream));
+    CK(cudaStreamSynchronize(net->stream));
+  }
   net->xbuf = static_cast<uint32_t*>(buf);
   net->xcap = buf ? (uint32_t)cap_entries : 0u;
+  net->x_parts_ok = nullptr;
   return SNN_OK;
 }
 
@@ -1272,11 +1282,15 @@ int snn_deliver_exchanged(snn_net* net, const void* parts, uint32_t n_parts,
       (unsigned long long)stride_bytes);
   int rc;
   if ((rc = set_device(net)) != SNN_OK) return rc;
-  if ((rc = check_exchange_ptr(net, parts, "parts")) != SNN_OK) return rc;
+  // validated once per pointer (no runtime query inside a stream capture
+  // that replays the same buffers)
+  if (parts != net->x_parts_ok) {
+    if ((rc = check_exchange_ptr(net, parts, "parts")) != SNN_OK) return rc;
+    net->x_parts_ok = parts;
+  }
   cudaStream_t s = net->stream;
   // the union's events are counted by the delivery itself (the update's
-  // count covers only the local sources' synapses)
-  CK(cudaMemsetAsync(&net->ctl->pending_events, 0, sizeof(unsigned long long), s));
+  // count covers only the local sources' synapses and is dropped)
   NetView v = net->view();
   v.gx = static_cast<const uint32_t*>(parts);
   v.gx_parts = n_parts;
@@ -1339,6 +1353,37 @@ int snn_deliver_noalloc(snn_net* net, const uint32_t* src,
   return SNN_OK;
 }
 
+}  // extern "C"
+
+// The production path of snn_simulate: whole intervals as replays of the
+// net's captured graph (captured now if may_capture, else launched one by
+// one while none exists: instantiation waits for other streams' work), the
+// rest launched directly; asynchronous.
+int snn::simulate_async(snn_net* net, int64_t n_steps, bool may_capture) {
+  const int D = net->interval;
+  int64_t full = n_steps / D;
+  const int rem = (int)(n_steps % D);
+  cudaStream_t s = net->stream;
+  int rc;
+  if (full >= kGraphIntervals && (net->graph || may_capture)) {
+    if ((rc = capture_graph(net, false)) != SNN_OK) return rc;
+    for (; full >= kGraphIntervals; full -= kGraphIntervals) {
+      CK(cudaGraphLaunch(net->graph, s));
+      net->launches += 2 * kGraphIntervals;
+      net->upd_launches += kGraphIntervals;
+      net->del_launches += kGraphIntervals;
+    }
+  }
+  for (; full > 0; --full)
+    if ((rc = launch_interval(net, D)) != SNN_OK) return rc;
+  if (rem)
+    if ((rc = launch_interval(net, rem)) != SNN_OK) return rc;
+  net->t_host += n_steps;
+  return SNN_OK;
+}
+
+extern "C" {
+
 int snn_simulate(snn_net* net, int64_t n_steps) {
   REQ(net, SNN_E_ARG, "null net");
   REQ(net->finalized, SNN_E_STATE, "net not finalized");
@@ -1397,19 +1442,8 @@ int snn_simulate(snn_net* net, int64_t n_steps) {
     CK(cudaStreamSynchronize(s));
     if ((rc = add_times(n_iv)) != SNN_OK) return rc;
   } else {
-    if (full >= kGraphIntervals) {
-      if ((rc = capture_graph(net, false)) != SNN_OK) return rc;
-      for (; full >= kGraphIntervals; full -= kGraphIntervals) {
-        CK(cudaGraphLaunch(net->graph, s));
-        net->launches += 2 * kGraphIntervals;
-        net->upd_launches += kGraphIntervals;
-        net->del_launches += kGraphIntervals;
-      }
-    }
-    for (; full > 0; --full)
-      if ((rc = launch_interval(net, D)) != SNN_OK) return rc;
-    if (rem)
-      if ((rc = launch_interval(net, rem)) != SNN_OK) return rc;
+    if ((rc = simulate_async(net, n_steps, true)) != SNN_OK) return rc;
+    return SNN_OK;
   }
   net->t_host += n_steps;
   return SNN_OK;
@@ -1708,6 +1742,8 @@ int snn_get_stats(snn_net* net, snn_stats* out) {
   out->first_neuron = net->g0;
   out->n_sources = net->n_src;
   out->acc_words = net->acc_words;
+  // replayed captures advance the device clock only: resynchronise
+  if (!net->pending) net->t_host = c.t_now;
   note_check_failure(net, c.error_flags);
   return SNN_OK;
 }

@@ -89,6 +89,8 @@ struct Ctl {
   unsigned long long plastic_events;  // plastic synapse updates (accumulated)
   unsigned long long stdp_truncated;  // updates whose post-spike window
                                       // reached past the kept history
+  unsigned long long gx_events;  // events of a gathered list, counted by the
+                                 // delivery's CTAs (replace pending_events)
 };
 
 // "No spike yet" for the spike-time fields of the plasticity state.

@@ -609,6 +609,7 @@ k_deliver(NetView v, unsigned long long* pair_p, unsigned int* done_p,
       *pair_p = 0ull;
       *done_p = 0u;
       if (advance_time) {  // the interval's own list: commit its events
+        if (v.xbuf) *v.xbuf = 0u;  // the next update refills the exchange list
         v.ctl->t_now += v.ctl->iv_steps;
         v.ctl->events += v.ctl->pending_events;
         v.ctl->pending_events = 0ull;
@@ -876,36 +877,44 @@ __device__ __forceinline__ void deliver_tile_body(
   // memory round trip fewer before the runs can be described); entries past
   // the length are never used.
   constexpr int kDU = PL ? 1 : 4;
-  SpikeEntry pre[kDU];
   // GX: the list is gathered from the partitions' exchange buffers (v.gx)
   constexpr bool gathered = GX;
-  const bool spec = !from_list_range && !gathered;
+  SpikeEntry pre[GX ? 1 : kDU];
+  uint2 pre_g[GX ? kDU : 1];
+  const bool spec = !from_list_range;
   if (spec) {
 #pragma unroll
     for (int u = 0; u < kDU; ++u) {
       const uint32_t k = threadIdx.x + u * blockDim.x;
-      if (k < desc_cap && k < v.list_cap) pre[u] = list[k];
+      if constexpr (GX) {  // part 0's first entries (its count comes next)
+        if (k < desc_cap && k < v.gx_cap)
+          pre_g[u] = reinterpret_cast<const uint2*>(v.gx + 4)[k];
+      } else {
+        if (k < desc_cap && k < v.list_cap) pre[u] = list[k];
+      }
     }
   }
   // every thread reads the launch's list size and window (same addresses);
   // thread 0 derives the fixed-point scales meanwhile
-  const unsigned long long pr =
-      *reinterpret_cast<volatile unsigned long long*>(pair_p);
-  uint32_t n_sp = (uint32_t)(pr >> 32);
+  uint32_t n_sp;
   // a list gathered from the partitions: the parts' counts (each at most
-  // its capacity) and their starts in the union, in part order
+  // its capacity) and their starts in the union, in part order; every
+  // thread computes them (same values, no barrier) from the same words
   __shared__ uint32_t s_gstart[kMaxGatherParts + 1];
-  if (gathered) {
-    if (threadIdx.x == 0) {
-      uint32_t run = 0;
-      for (uint32_t p = 0; p < v.gx_parts; ++p) {
-        s_gstart[p] = run;
-        run += min(v.gx[(uint64_t)p * v.gx_stride], v.gx_cap);
-      }
-      s_gstart[v.gx_parts] = run;
+  if constexpr (GX) {
+    uint32_t run = 0;
+    for (uint32_t p = 0; p < v.gx_parts; ++p) {
+      s_gstart[p] = run;
+      run += min(*reinterpret_cast<const volatile uint32_t*>(
+                     v.gx + (uint64_t)p * v.gx_stride),
+                 v.gx_cap);
     }
-    __syncthreads();
-    n_sp = s_gstart[v.gx_parts];
+    s_gstart[v.gx_parts] = run;
+    n_sp = run;
+  } else {
+    const unsigned long long pr =
+        *reinterpret_cast<volatile unsigned long long*>(pair_p);
+    n_sp = (uint32_t)(pr >> 32);
   }
   long long base;
   bool inwin;
@@ -1089,12 +1098,14 @@ __device__ __forceinline__ void deliver_tile_body(
       for (int u = 0; u < kDU; ++u) {
         const uint32_t k = k0 + u * blockDim.x;
         if (k < nb) {
-          if (gathered) {
+          if constexpr (GX) {
             const uint32_t g = j0 + k;
             uint32_t p = 0;
             while (s_gstart[p + 1] <= g) ++p;
-            const uint2 x = reinterpret_cast<const uint2*>(
-                v.gx + (uint64_t)p * v.gx_stride + 4)[g - s_gstart[p]];
+            const uint2 x = (have && p == 0)
+                ? pre_g[u]
+                : reinterpret_cast<const uint2*>(
+                      v.gx + (uint64_t)p * v.gx_stride + 4)[g - s_gstart[p]];
             // entries come from the caller's buffers: a source outside the
             // store or a step outside this interval is skipped and flagged
             // (its cells would lie outside the tile's window)
@@ -1135,11 +1146,12 @@ __device__ __forceinline__ void deliver_tile_body(
         }
       }
     }
-    if (gathered) {  // (all threads of the CTA reach this)
+    // gathered lists: the warp's events (all threads of the CTA reach this)
+    if (gathered) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) my_events += __shfl_xor_sync(kFull, my_events, o);
-      if (lane == 0 && my_events) atomicAdd(&s_events, my_events);
     }
+    return my_events;
   };
   // next U runs for this warp (shared counter: warps that met short runs or
   // fast loads take more)
@@ -1152,9 +1164,11 @@ __device__ __forceinline__ void deliver_tile_body(
   uint32_t j0 = 0;
   do {
     const uint32_t nb = min(desc_cap, n_sp - j0);
-    describe(j0, nb);
+    const unsigned long long warp_events = describe(j0, nb);
     if (threadIdx.x == 0) s_next = 0u;
     __syncthreads();
+    // (after the barrier: s_events was cleared before it)
+    if (gathered && lane == 0 && warp_events) atomicAdd(&s_events, warp_events);
     fx = s_fx;
     if (FAST && !fx.fixed && n_sp > 0 && j0 == 0 && threadIdx.x == 0)
       atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_SCALES);
@@ -1234,15 +1248,20 @@ __device__ __forceinline__ void deliver_tile_body(
   // targets -- are counted by the CTAs themselves).
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (gathered && s_events) atomicAdd(&v.ctl->pending_events, s_events);
+    if (gathered && s_events) atomicAdd(&v.ctl->gx_events, s_events);
     __threadfence();
     unsigned prev = atomicAdd(done_p, 1u);
     if (prev == v.n_tiles - 1) {
       *pair_p = 0ull;
       *done_p = 0u;
       if (advance_time) {  // the interval's own list: commit its events
+        // this net's exchange list has been read (by the collective before
+        // this delivery, or by this delivery itself): the next update
+        // refills it
+        if (v.xbuf) *v.xbuf = 0u;
         v.ctl->t_now += v.ctl->iv_steps;
-        v.ctl->events += atomicExch(&v.ctl->pending_events, 0ull);
+        const unsigned long long own = atomicExch(&v.ctl->pending_events, 0ull);
+        v.ctl->events += gathered ? atomicExch(&v.ctl->gx_events, 0ull) : own;
       }
     }
   }
@@ -1544,12 +1563,6 @@ cudaError_t launch_update(const NetView& v, const UpdConst& c, int n_steps,
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
       sms.store(m, std::memory_order_relaxed);
-  }
-  // the exchange buffer's count restarts with every interval (after every
-  // delivery that read the previous one, in stream order)
-  if (v.xbuf) {
-    const cudaError_t e = cudaMemsetAsync(v.xbuf, 0, sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
   }
   if (blocks > 3u * (unsigned)std::max(sms.load(std::memory_order_relaxed), 1))
     k_update<4><<<blocks, kUpdThreads, 0, s>>>(v, c, n_steps, from_ctl_time, t0);

@@ -27,6 +27,9 @@ void pool_free(void* p, cudaStream_t s);
 // its lifetime, so that admitting a request never waits for memory to be
 // mapped again).
 void pool_hold(int dev, int delta);
+// snn_simulate's asynchronous production path (serving uses it directly:
+// may_capture false keeps it from instantiating a graph while builds run).
+int simulate_async(snn_net* net, int64_t n_steps, bool may_capture);
 }  // namespace snn
 
 // The net: parameters, device buffers and host bookkeeping.
@@ -52,6 +55,7 @@ struct snn_net {
   bool check_noted = false;      // SNN_ERRF_CHECK counted (checked builds)
   uint32_t* xbuf = nullptr;      // caller's exchange buffer (snn_set_exchange)
   uint32_t xcap = 0;
+  const void* x_parts_ok = nullptr;  // last gathered-parts pointer validated
   uint32_t tile_w = 0, n_tiles = 0;
   int lo_bits = 0;
   int window = 0;

@@ -85,6 +85,13 @@ constexpr unsigned long long kSpinLimit = 1ull << 20;
 constexpr int kBuildReserveSms = 16;
 // Nets one persistent step runs at most (sizes its pinned host records).
 constexpr size_t kServeMaxNets = 4096;
+// Exclusive mode: the target GPU time of one step of the chosen net, the
+// intervals of a net's first step (before its time per interval is known),
+// and the steps in flight on the GPU at most (the next one is queued while
+// the current one runs, so the GPU never idles between steps).
+constexpr double kExclusiveStepUs = 1000.0;
+constexpr int kExclusiveFirstIntervals = 16;
+constexpr int kExclusiveInFlight = 2;
 // Lanes by synapse count: below 2^24, below 2^27, and the rest.
 constexpr int kLanes = 3;
 constexpr uint64_t kLaneBound[kLanes - 1] = {1ull << 24, 1ull << 27};
@@ -103,7 +110,8 @@ struct Req {
   uint64_t est = 0;
   std::vector<uint32_t> sp_src;
   std::vector<int32_t> sp_t;
-  double iv_us = 0;      // persistent mode: measured time per interval
+  double iv_us = 0;      // persistent / exclusive mode: measured time per
+                         // interval
   int fail_code = 0;     // non-zero: retire as failed (e.g. SNN_E_TIMEOUT)
   bool cancel = false;   // snn_server_cancel asked (guarded by the mutex)
 };
@@ -179,6 +187,14 @@ struct Lane {
   ServeNet* d_sn = nullptr;
   size_t cap_sn = 0;
   ServeCtl* d_ctl = nullptr;
+  // exclusive mode: steps in flight (net, intervals, start and end events)
+  struct XStep {
+    Req* q;
+    int intervals;
+    cudaEvent_t e0, e1;
+  };
+  std::deque<XStep> x_inflight;
+  std::vector<cudaEvent_t> x_spare;  // timing events for reuse
   // autotuner of the step's target GPU time
   double step_us = kStepUsCandidates[0];
   int st_idx = 0, st_count = 0, st_tuned = 0;
@@ -215,6 +231,7 @@ struct snn_server {
   std::atomic<int> building{0};
   std::atomic<int> building_large{0};  // of which large requests
   bool persistent = false;              // one persistent launch per step
+  bool exclusive = false;               // one net per step, least work first
   unsigned long long spin_limit = kSpinLimit;
   double step_us_fixed = 0;             // > 0: no autotuning
   int sms = 1;
@@ -578,7 +595,8 @@ int drop_cancelled(snn_server* sv, Lane* ln) {
       q->fail_code = kCancelled;
       cudaEvent_t e = nullptr;
       SCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-      SCK(cudaEventRecord(e, ln->stream));
+      // (exclusive mode runs each net on its own stream)
+      SCK(cudaEventRecord(e, sv->exclusive ? q->net->stream : ln->stream));
       ln->retiring.emplace_back(q, e);
     } else {
       keep.push_back(q);
@@ -688,6 +706,89 @@ int lane_step(snn_server* sv, Lane* ln, bool* launched) {
     ln->active_steps.swap(keep_steps);
     ln->dirty = true;
     ln->t_last = 0;  // a change of batch is not a steady step
+  }
+  return SNN_OK;
+}
+
+// Exclusive mode: one step runs one net alone -- the running net with the
+// least remaining work (steps left x synapses: shortest remaining processing
+// time first, so that a small request is never slowed by a large one) --
+// for about kExclusiveStepUs of GPU time, with the single-net kernels on the
+// net's own stream (its captured interval graphs, or direct launches while a
+// build runs).  Up to kExclusiveInFlight steps are queued on the GPU; the
+// choice is made again at every step, so a newly admitted smaller request
+// preempts a larger one within a step or two.
+int lane_step_exclusive(snn_server* sv, Lane* ln, bool* launched) {
+  *launched = false;
+  int rc;
+  if ((rc = drop_cancelled(sv, ln)) != SNN_OK) return rc;
+  if ((rc = retire_done(sv, ln)) != SNN_OK) return rc;
+  // fold in the GPU time of completed steps, oldest first
+  while (!ln->x_inflight.empty()) {
+    Lane::XStep& x = ln->x_inflight.front();
+    bool done = true;
+    if ((rc = event_done(x.e1, &done)) != SNN_OK) return rc;
+    if (!done) break;
+    float ms = 0;
+    SCK(cudaEventElapsedTime(&ms, x.e0, x.e1));
+    ln->gpu_ms += ms;
+    const double us = 1e3 * ms / std::max(x.intervals, 1);
+    x.q->iv_us = x.q->iv_us > 0 ? 0.5 * (x.q->iv_us + us) : us;
+    ln->x_spare.push_back(x.e0);
+    ln->x_spare.push_back(x.e1);
+    ln->x_inflight.pop_front();
+  }
+  if (ln->active.empty() || ln->x_inflight.size() >= (size_t)kExclusiveInFlight)
+    return SNN_OK;
+  size_t pick = 0;
+  double best = 1e300;
+  for (size_t k = 0; k < ln->active.size(); ++k) {
+    const Req& q = *ln->active[k];
+    const double work = (double)q.steps_left * (double)q.net->n_syn;
+    if (work < best) {
+      best = work;
+      pick = k;
+    }
+  }
+  Req& q = *ln->active[pick];
+  const int iv = q.net->interval;
+  int m = kExclusiveFirstIntervals;
+  if (q.iv_us > 0)
+    m = (int)std::min(4096.0, std::max(8.0, kExclusiveStepUs / q.iv_us));
+  const int64_t steps = std::min<int64_t>((int64_t)m * iv, q.steps_left);
+  cudaEvent_t e[2];
+  for (int k = 0; k < 2; ++k) {
+    if (!ln->x_spare.empty()) {
+      e[k] = ln->x_spare.back();
+      ln->x_spare.pop_back();
+    } else {
+      SCK(cudaEventCreate(&e[k]));
+    }
+  }
+  cudaStream_t s = q.net->stream;
+  SCK(cudaEventRecord(e[0], s));
+  if ((rc = simulate_async(q.net, steps, sv->building.load() == 0)) != SNN_OK)
+    return rc;
+  SCK(cudaEventRecord(e[1], s));
+  const int n_iv = (int)((steps + iv - 1) / iv);
+  ln->x_inflight.push_back({&q, n_iv, e[0], e[1]});
+  ln->steps += 1;
+  ln->intervals += n_iv;
+  ln->launches += 2ull * n_iv;
+  *launched = true;
+  q.steps_left -= steps;
+  if (q.steps_left <= 0) {  // retire once this last step has completed
+    cudaEvent_t d = nullptr;
+    if (!ln->spare_events.empty()) {
+      d = ln->spare_events.back();
+      ln->spare_events.pop_back();
+    } else {
+      SCK(cudaEventCreateWithFlags(&d, cudaEventDisableTiming));
+    }
+    SCK(cudaEventRecord(d, s));
+    ln->retiring.emplace_back(&q, d);
+    ln->active.erase(ln->active.begin() + pick);
+    ln->active_steps.erase(ln->active_steps.begin() + pick);
   }
   return SNN_OK;
 }
@@ -996,6 +1097,19 @@ int snn_server_set_option(snn_server* sv, int32_t option, double value) {
       SREQ(idle, SNN_E_STATE, "the serving mode changes only while no net runs");
       SREQ(value == 0 || value == 1, SNN_E_ARG, "persistent must be 0 or 1");
       sv->persistent = value != 0;
+      if (sv->persistent) sv->exclusive = false;
+      return SNN_OK;
+    }
+    case SNN_SERVE_OPT_EXCLUSIVE: {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      bool idle = sv->ready.empty();
+      for (const Lane& ln : sv->lanes)
+        idle = idle && ln.active.empty() && ln.retiring.empty() &&
+               ln.x_inflight.empty();
+      SREQ(idle, SNN_E_STATE, "the serving mode changes only while no net runs");
+      SREQ(value == 0 || value == 1, SNN_E_ARG, "exclusive must be 0 or 1");
+      sv->exclusive = value != 0;
+      if (sv->exclusive) sv->persistent = false;
       return SNN_OK;
     }
     case SNN_SERVE_OPT_SPIN_LIMIT:
@@ -1044,7 +1158,9 @@ int snn_server_submit(snn_server* sv, const snn_request* req, uint64_t* id) {
   } else {
     q.r.params.spike_log_capacity = 0;
   }
-  if (q.r.params.tile_width == 0)
+  // (exclusive mode: the single-net tiles, about one per SM, for a net that
+  // runs alone)
+  if (q.r.params.tile_width == 0 && !sv->exclusive)
     q.r.params.tile_width = serve_tile_width(q.r, sv->persistent);
   q.est = estimate_bytes(q.r, sv->fmt);
   SREQ(q.est <= sv->budget, SNN_E_ARG,
@@ -1088,7 +1204,7 @@ int snn_server_step(snn_server* sv, int32_t* n_active) {
       }
       q->res.state = SNN_REQ_RUNNING;
       q->res.t_start = now_s() - sv->t0;
-      Lane& ln = sv->lanes[sv->persistent ? 0 : lane_of(q->net)];
+      Lane& ln = sv->lanes[sv->persistent || sv->exclusive ? 0 : lane_of(q->net)];
       // (smallest nets first: the persistent kernel serves them first)
       size_t at = ln.active.size();
       if (sv->persistent)
@@ -1105,7 +1221,9 @@ int snn_server_step(snn_server* sv, int32_t* n_active) {
     bool launched = false;
     int rc = sv->persistent ? (k == 0 ? lane_step_persistent(sv, &sv->lanes[k], &launched)
                                       : SNN_OK)
-                            : lane_step(sv, &sv->lanes[k], &launched);
+             : sv->exclusive ? (k == 0 ? lane_step_exclusive(sv, &sv->lanes[k], &launched)
+                                       : SNN_OK)
+                             : lane_step(sv, &sv->lanes[k], &launched);
     if (rc != SNN_OK) return rc;
     any = any || launched;
     act += (int32_t)(sv->lanes[k].active.size() + sv->lanes[k].retiring.size());
@@ -1208,12 +1326,12 @@ int snn_server_get_stats(snn_server* sv, snn_server_stats* out) {
   out->mem_used = sv->used;
   out->intervals_per_step = sv->lanes[busiest].ips;
   out->tuned = tuned && sv->steps > 0;
-  if (sv->persistent) {
+  if (sv->persistent || sv->exclusive) {
     // one lane; its intervals per launch on average, and the step tuner
     const Lane& ln = sv->lanes[0];
     out->intervals_per_step =
         ln.steps ? (int32_t)((ln.intervals + ln.steps / 2) / ln.steps) : 0;
-    out->tuned = ln.st_tuned;
+    out->tuned = sv->exclusive ? 1 : ln.st_tuned;
   }
   return SNN_OK;
 }
@@ -1244,6 +1362,11 @@ int snn_server_destroy(snn_server* sv) {
       }
     }
     for (auto& fe : ln.retiring) cudaEventDestroy(fe.second);
+    for (auto& x : ln.x_inflight) {
+      cudaEventDestroy(x.e0);
+      cudaEventDestroy(x.e1);
+    }
+    for (cudaEvent_t e : ln.x_spare) cudaEventDestroy(e);
     for (int sl = 0; sl < 2; ++sl) {
       if (ln.h_sn[sl]) cudaFreeHost(ln.h_sn[sl]);
       if (ln.h_sn_back[sl]) cudaFreeHost(ln.h_sn_back[sl]);

@@ -29,6 +29,10 @@ reads the gathered buffers directly (``snn_deliver_exchanged``)::
     update every partition          (snn_update: also fills its buffer)
     all-gather the fixed buffers    (NCCL, device to device; none in-process)
     deliver from the gathered rows  (snn_deliver_exchanged)
+
+The updates start at the device clock (``SNN_T_DEVICE``), so a run of
+intervals can be captured into one CUDA graph and replayed
+(``DeviceExchange.graph``), as the single-net simulation replays its own.
 """
 from __future__ import annotations
 
@@ -181,8 +185,10 @@ class DeviceExchange:
     the collective and the library calls must be ordered on one stream).
 
     ``local`` holds one row per local partition, ``gathered`` the rows of
-    every partition of every rank in rank order (the same tensor when there
-    is one rank).  ``cap`` entries per row: by default the largest
+    every partition of every rank in rank order: the all-gather's output,
+    a device copy of ``local`` for several partitions in one process (a
+    delivery clears its own row when it completes), or ``local`` itself for
+    a single partition.  ``cap`` entries per row: by default the largest
     ``snn_exchange_capacity`` of all partitions (``reduce_max`` maps it to
     the maximum over ranks), which can never overflow."""
 
@@ -196,6 +202,10 @@ class DeviceExchange:
         # one stream orders every update before every delivery that reads
         # its buffer (and, across ranks, the collective between them)
         streams = {snn.snn_get_stream(net.h) for net in self.nets}
+        self.stream = next(iter(streams))
+        self._tstream = (torch.cuda.ExternalStream(self.stream) if self.stream
+                         else torch.cuda.default_stream())
+        self._graphs = {}
         if len(streams) > 1:
             raise ValueError("partitions sharing exchange buffers must run on "
                              "one stream (pass it to create())")
@@ -212,19 +222,61 @@ class DeviceExchange:
         dev = torch.device("cuda", torch.cuda.current_device())
         self.local = torch.zeros((len(self.nets), words), dtype=torch.int32,
                                  device=dev)
-        self.gathered = self.local if self.world == 1 else torch.zeros(
-            (self.world * len(self.nets), words), dtype=torch.int32, device=dev)
+        self.gathered = (self.local if self.world == 1 and len(self.nets) == 1
+                         else torch.zeros((self.world * len(self.nets), words),
+                                          dtype=torch.int32, device=dev))
         torch.cuda.current_stream().synchronize()  # zeroed before first use
         for k, net in enumerate(self.nets):
             snn.snn_set_exchange(net.h, self.local[k], self.cap)
 
     def gather(self):
-        """All-gather the local rows into ``gathered`` (asynchronous on the
-        current stream; nothing to do for one rank)."""
-        if self.world > 1:
-            allgather_rows(self.local, self.gathered, self.group)
+        """All-gather the local rows into ``gathered`` on the nets' stream
+        (asynchronous; a device copy in one process, nothing for a single
+        partition)."""
+        if self.gathered is self.local:
+            return
+        import torch
+        with torch.cuda.stream(self._tstream):
+            if self.world > 1:
+                allgather_rows(self.local, self.gathered, self.group)
+            else:
+                self.gathered.copy_(self.local)
+
+    def graph(self, intervals: int, steps: int):
+        """A CUDA graph of ``intervals`` exchanged intervals of ``steps``
+        steps each (updates from the device clock), captured on the nets'
+        stream once and cached; None if this process cannot capture it (the
+        caller then runs the intervals eagerly).  Capture happens after at
+        least one eager interval has run (pointer checks and kernel
+        attributes are then settled)."""
+        import torch
+        key = (intervals, steps)
+        if key not in self._graphs:
+            t_now = [net.stats().t_now for net in self.nets]
+            g = torch.cuda.CUDAGraph()
+            try:
+                with torch.cuda.graph(g, stream=self._tstream):
+                    for _ in range(intervals):
+                        run_interval_exchanged(self.nets, self, steps)
+            except RuntimeError:
+                # nothing of the capture ran: clear a pending flag the
+                # interrupted sequence left and put the clocks back
+                g = None
+                for net, t in zip(self.nets, t_now):
+                    snn.snn_discard_pending(net.h)
+                    snn.snn_set_time(net.h, t)
+            self._graphs[key] = g
+        return self._graphs[key]
+
+    def replay(self, g):
+        """Replay a captured graph on the nets' stream (torch launches a
+        graph on its current stream)."""
+        import torch
+        with torch.cuda.stream(self._tstream):
+            g.replay()
 
     def close(self):
+        self._graphs.clear()
         for net in self.nets:
             if net.h:
                 snn.snn_set_exchange(net.h, None)
@@ -246,31 +298,46 @@ def allgather_rows(local, gathered=None, group=None):
     return gathered
 
 
-def run_interval_exchanged(nets, xch: DeviceExchange, t0: int, steps: int):
+def run_interval_exchanged(nets, xch: DeviceExchange, steps: int,
+                           t0: int = snn.SNN_T_DEVICE):
     """One interval of the partitioned network with the device exchange:
-    asynchronous, no host synchronisation."""
+    asynchronous, no host synchronisation (t0: the interval's first step,
+    by default the device clock)."""
+    ptr = xch.gathered.data_ptr()
+    rows = xch.gathered.shape[0]
+    stride = xch.gathered.stride(0) * xch.gathered.element_size()
     for net in nets:
         snn.snn_update(net.h, t0, steps)
     xch.gather()
     for net in nets:
-        snn.snn_deliver_exchanged(net.h, xch.gathered)
+        snn.snn_deliver_exchanged(net.h, ptr, rows, stride)
 
 
 def simulate_exchanged(nets, xch: DeviceExchange, n_steps: int,
-                       t0: int | None = None, interval: int | None = None):
-    """Advance the partitions by n_steps with the device exchange (intervals
-    of the nets' interval length, a shorter last one).  Asynchronous: read
-    the events afterwards from the nets' statistics."""
-    if interval is None or t0 is None:
-        st = nets[0].stats()
-        interval = st.interval if interval is None else interval
-        t0 = st.t_now if t0 is None else t0
-    t, end = t0, t0 + n_steps
-    while t < end:
-        m = min(interval, end - t)
-        run_interval_exchanged(nets, xch, t, m)
-        t += m
-    return t
+                       interval: int | None = None, graph_intervals: int = 0):
+    """Advance the partitions by n_steps from their device clock with the
+    device exchange (intervals of the nets' interval length, a shorter last
+    one).  graph_intervals > 0 replays a captured CUDA graph of that many
+    intervals while whole groups remain (after one eager interval).
+    Asynchronous: read the events afterwards from the nets' statistics.
+    Returns the number of graph replays."""
+    if interval is None:
+        interval = nets[0].stats().interval
+    left, replays = n_steps, 0
+    while left > 0:
+        m = min(interval, left)
+        g = None
+        if (graph_intervals > 0 and left < n_steps
+                and left >= graph_intervals * interval):
+            g = xch.graph(graph_intervals, interval)
+        if g is not None:
+            xch.replay(g)
+            replays += 1
+            left -= graph_intervals * interval
+            continue
+        run_interval_exchanged(nets, xch, m)
+        left -= m
+    return replays
 
 
 def encode_exchange(src, t, cap: int) -> np.ndarray:

@@ -20,6 +20,7 @@ SNN_OK = 0
 SNN_E_OOM, SNN_E_ARG, SNN_E_STATE, SNN_E_TIMEOUT, SNN_E_OVERFLOW, SNN_E_CUDA = \
     -1, -2, -3, -4, -5, -6
 SNN_MEM_HOST, SNN_MEM_DEVICE = 0, 1
+SNN_T_DEVICE = -1  # snn_update: start at the device clock
 SNN_W_FP32_12B, SNN_W_BF16_8B = 0, 1
 SNN_DELIVER_TILED, SNN_DELIVER_ATOMIC = 0, 1
 SNN_ERRF_SPIKE_LIST, SNN_ERRF_SPIKE_LOG, SNN_ERRF_BAD_SOURCE, SNN_ERRF_CHUNKS = \
@@ -735,6 +736,7 @@ def snn_server_get_stats(sv) -> snn_server_stats:
 
 
 SNN_SERVE_OPT_PERSISTENT, SNN_SERVE_OPT_SPIN_LIMIT, SNN_SERVE_OPT_STEP_US = 0, 1, 2
+SNN_SERVE_OPT_EXCLUSIVE = 3
 
 
 def snn_server_set_option(sv, option: int, value: float):

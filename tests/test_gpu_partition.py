@@ -93,9 +93,10 @@ def test_partitions_equal_the_whole_net(fmt, cuts):
         assert np.array_equal(wrb[:, lo:hi].view(np.uint32), rbs[k].view(np.uint32))
 
 
-def _run_parts_exchanged(fmt, cuts, steps, params=None):
+def _run_parts_exchanged(fmt, cuts, steps, params=None, graph=0):
     """The partitions advanced with the device exchange (in one process the
-    gathered rows are the local rows: no copy, no host synchronisation)."""
+    gathered rows are the local rows: no copy, no host synchronisation),
+    eagerly or replaying captured groups of `graph` intervals."""
     import torch
     from paper_2109_12855_gb300 import partition as PT
     pp = params or _params(fmt)
@@ -107,7 +108,8 @@ def _run_parts_exchanged(fmt, cuts, steps, params=None):
         for net in nets:
             net.finalize()
         xch = PT.DeviceExchange(nets)
-        PT.simulate_exchanged(nets, xch, steps, t0=0)
+        replays = PT.simulate_exchanged(nets, xch, steps, graph_intervals=graph)
+        assert (replays > 0) == (graph > 0)
         s.synchronize()
         logs = [net.read_spikes(1 << 21) for net in nets]
         states = [net.read_state() for net in nets]
@@ -123,15 +125,20 @@ def _run_parts_exchanged(fmt, cuts, steps, params=None):
 
 
 @pytest.mark.parametrize("fmt", [0, 1], ids=["fp32", "bf16"])
-@pytest.mark.parametrize("cuts", [[0, N], [0, 2500, N], [0, 1700, 3333, N]],
-                         ids=["1-part", "2-parts", "3-parts"])
-def test_device_exchange_equals_the_whole_net(fmt, cuts):
+@pytest.mark.parametrize("cuts,graph", [([0, N], 0), ([0, 2500, N], 0),
+                                        ([0, 1700, 3333, N], 0), ([0, N], 8),
+                                        ([0, 1700, 3333, N], 8)],
+                         ids=["1-part", "2-parts", "3-parts", "1-part-graph",
+                              "3-parts-graph"])
+def test_device_exchange_equals_the_whole_net(fmt, cuts, graph):
     """Update -> device exchange buffers -> delivery read straight from the
-    gathered buffers: the union equals the whole net bit for bit (spikes,
+    gathered buffers, eagerly or as replayed CUDA graphs (updates from the
+    device clock): the union equals the whole net bit for bit (spikes,
     state, ring buffers, events counted on the device)."""
-    steps = 1500
+    steps = 1505  # 150 intervals of 10 steps and a short one
     w_ev, (ws, wt), wstate, wrb = _run_whole(fmt, steps)
-    (ps, pt), states, rbs, stats = _run_parts_exchanged(fmt, cuts, steps)
+    (ps, pt), states, rbs, stats = _run_parts_exchanged(fmt, cuts, steps,
+                                                        graph=graph)
     assert len(ws) > 2000
     assert np.array_equal(ws, ps) and np.array_equal(wt, pt)
     assert sum(st.events_delivered for st in stats) == w_ev

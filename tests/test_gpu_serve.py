@@ -4,7 +4,9 @@ By default a server step runs lanes of batched update and batched
 tiled-delivery launches, one each per interval; the persistent mode makes a
 step one launch of the persistent serving kernel, which advances every
 running net by its own number of intervals (CTAs claim the ready update
-blocks and delivery tiles of the nets).  Because tiled delivery sums in exact fixed point and every random
+blocks and delivery tiles of the nets); the exclusive mode runs one net per
+step alone (least remaining work first) with the single-net kernels.
+Because tiled delivery sums in exact fixed point and every random
 draw is keyed by (neuron, step), a request's spike train must equal, bit for
 bit, the same net simulated alone through the single-net path, whatever
 else shares its batch, when it was admitted, and how many intervals a step
@@ -83,9 +85,16 @@ def _check_equal_to_solo(sv, rid, r):
     return res
 
 
-@pytest.mark.parametrize("persistent", [1, 0], ids=["persistent", "lanes"])
+def _set_mode(snn, sv, mode):
+    snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_PERSISTENT,
+                              int(mode == "persistent"))
+    snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_EXCLUSIVE,
+                              int(mode == "exclusive"))
+
+
+@pytest.mark.parametrize("mode", ["persistent", "lanes", "exclusive"])
 @pytest.mark.parametrize("fmt", [0, 1], ids=["fp32", "bf16"])
-def test_batched_requests_equal_solo_runs(fmt, persistent):
+def test_batched_requests_equal_solo_runs(fmt, mode):
     """Mixed sizes, seeds, delay ranges and lengths (one not a multiple of
     its interval); two requests join while the first two are running."""
     from paper_2109_12855_gb300 import snn
@@ -95,7 +104,7 @@ def test_batched_requests_equal_solo_runs(fmt, persistent):
             _req(11250, 4, 400, fmt, (12, 30), nu=15000.0, tag=14)]
     sv = snn.snn_server_create(8 * GB, fmt, stream())
     try:
-        snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_PERSISTENT, persistent)
+        _set_mode(snn, sv, mode)
         ids = [snn.snn_server_submit(sv, r) for r in reqs[:2]]
         for _ in range(5):
             snn.snn_server_step(sv)
@@ -110,7 +119,7 @@ def test_batched_requests_equal_solo_runs(fmt, persistent):
         st = snn.snn_server_get_stats(sv)
         assert st.done == 4 and st.failed == 0 and st.active == 0
         assert st.mem_used == 0
-        if persistent:   # one launch per step, several intervals each
+        if mode == "persistent":  # one launch per step, several intervals each
             assert st.kernel_launches == st.steps < st.intervals
         else:
             assert st.kernel_launches == 2 * st.intervals
@@ -251,8 +260,8 @@ def test_persistent_kernel_wait_limit_fails_the_step_not_the_gpu():
         snn.snn_server_destroy(sv)
 
 
-@pytest.mark.parametrize("persistent", [0, 1], ids=["lanes", "persistent"])
-def test_cancel_queued_and_running_requests(persistent):
+@pytest.mark.parametrize("mode", ["lanes", "persistent", "exclusive"])
+def test_cancel_queued_and_running_requests(mode):
     """Cancelling a queued request removes it before it is built; cancelling
     a running one drops it from its batch (freed once its launched work has
     completed); the others still equal their solo runs; the budget is
@@ -263,7 +272,7 @@ def test_cancel_queued_and_running_requests(persistent):
     queued = _req(2000, 53, 500)
     sv = snn.snn_server_create(4 * GB, 0, stream())
     try:
-        snn.snn_server_set_option(sv, snn.SNN_SERVE_OPT_PERSISTENT, persistent)
+        _set_mode(snn, sv, mode)
         ids = [snn.snn_server_submit(sv, r) for r in (keep, run_long)]
         for _ in range(2000):                 # until both run
             snn.snn_server_step(sv)
