@@ -118,6 +118,53 @@ __device__ double weight_of(const BuildFixed& b, const double* edge_w,
   return x;
 }
 
+// BF16 bits of a fixed-rule weight.  The rounding to 8 significant bits is
+// decided from an FP32 evaluation of the same Box-Muller normal whenever the
+// FP32 value's error bound lies inside one rounding interval, and only
+// otherwise (about 0.2 % of the draws) from the FP64 evaluation: rounding is
+// monotonic, so if both ends of [x - e, x + e] round to the same BF16 value,
+// the FP64 value does too.  The result equals the FP64 path's, at a small
+// fraction of its cost (FP64 arithmetic is a small share of this GPU's
+// throughput).  Bound: with the CUDA math library's documented maximum
+// errors (1 ulp for logf, log1pf and cospif; sqrtf correctly rounded) and
+// the conversions of the draw words to float, |s| <= 6.67 and
+// |dz| <= 14 2^-21 < 2^-16; the conversions of mean and sd and the final
+// fused multiply-add add at most 2^-23 (|mean| + 7 |sd|).
+__device__ uint16_t bf16_weight_bits(const BuildFixed& b, bool exc,
+                                     uint32_t tgt, uint32_t tie) {
+  const double mean = exc ? b.w_e : b.w_i, sd = exc ? b.sd_e : b.sd_i;
+  const bool clip_lo = exc && b.clip_e, clip_hi = !exc && b.clip_i;
+  if (sd == 0.0) {
+    double x = mean;
+    if (clip_lo && x < 0.0) x = 0.0;
+    if (clip_hi && x > 0.0) x = 0.0;
+    return bf16_bits_rne(x);
+  }
+  const U4 r = draw(b.seed, b.tgt0 + tgt, tie, 0u);
+  // ln u1 for u1 = (z + 1) 2^-32: directly below 1/2; above it as
+  // log1p(u1 - 1) with u1 - 1 = -(2^32 - 1 - z) 2^-32 (no cancellation)
+  const float ln = r.z < 0x7FFFFFFFu ? logf(((float)r.z + 1.0f) * 0x1p-32f)
+                                     : log1pf(-(float)(~r.z) * 0x1p-32f);
+  const float sv = sqrtf(-2.0f * ln);
+  const float cv = cospif(2.0f * ((float)r.w * 0x1p-32f));
+  const float sdf = (float)sd, meanf = (float)mean;
+  const float xf = fmaf(sdf, sv * cv, meanf);
+  const float e = fabsf(sdf) * 0x1p-16f +
+                  (fabsf(meanf) + 7.0f * fabsf(sdf)) * 0x1p-20f;
+  float lo = __fsub_rd(xf, e), hi = __fadd_ru(xf, e);
+  if (clip_lo) {
+    lo = fmaxf(lo, 0.0f);
+    hi = fmaxf(hi, 0.0f);
+  }
+  if (clip_hi) {
+    lo = fminf(lo, 0.0f);
+    hi = fminf(hi, 0.0f);
+  }
+  const uint16_t a = bf16_bits_rne((double)lo);
+  if (a == bf16_bits_rne((double)hi)) return a;
+  return bf16_bits_rne(weight_of<0>(b, nullptr, exc, tgt, tie));
+}
+
 // Writes a record; returns |stored weight| (as stored, widened to float).
 template <int FMT>
 __device__ __forceinline__ float store_rec(void* recs, uint64_t idx,
@@ -152,8 +199,17 @@ __device__ void pack_row(const uint64_t* sorted, uint32_t len, uint32_t row,
     uint32_t d = key_delay(key, g);
     uint32_t tgt = key_target(key, g);
     uint32_t tie = (uint32_t)key;
-    wmax = fmaxf(wmax, store_rec<FMT>(recs, beg + p, tgt, d,
-                                      weight_of<WMODE>(b, edge_w, exc, tgt, tie)));
+    if (FMT == SNN_W_BF16_8B && WMODE == 0) {
+      const uint16_t bits = bf16_weight_bits(b, exc, tgt, tie);
+      uint2 rec;
+      rec.x = tgt;
+      rec.y = (d & 0xFFu) | ((uint32_t)bits << 16);
+      reinterpret_cast<uint2*>(recs)[beg + p] = rec;
+      wmax = fmaxf(wmax, fabsf(bf16_to_f32(bits)));
+    } else {
+      wmax = fmaxf(wmax, store_rec<FMT>(recs, beg + p, tgt, d,
+                                        weight_of<WMODE>(b, edge_w, exc, tgt, tie)));
+    }
     // multiplicity of (target, delay): length of the run of equal keys
     // (ignoring the tie field) that starts here
     if (p == 0 || (sorted[p - 1] >> 32) != (key >> 32)) {
@@ -374,6 +430,12 @@ __global__ void k_unpack(const void* recs, uint64_t n, uint32_t* tgt,
 
 template <int FMT>
 __global__ void __launch_bounds__(1024) k_delay_range(const void* recs, uint64_t n, unsigned* out) {
+  __shared__ unsigned s_lo, s_hi;
+  if (threadIdx.x == 0) {
+    s_lo = 0xFFFFFFFFu;
+    s_hi = 0u;
+  }
+  __syncthreads();
   unsigned lo = 0xFFFFFFFFu, hi = 0u;
   for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n;
        s += (uint64_t)gridDim.x * blockDim.x) {
@@ -387,9 +449,16 @@ __global__ void __launch_bounds__(1024) k_delay_range(const void* recs, uint64_t
     lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
     hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
   }
+  // one pair of global atomics per block (not per warp: every warp would
+  // hit the same two words)
   if ((threadIdx.x & 31u) == 0) {
-    atomicMin(&out[0], lo);
-    atomicMax(&out[1], hi);
+    atomicMin(&s_lo, lo);
+    atomicMax(&s_hi, hi);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicMin(&out[0], s_lo);
+    atomicMax(&out[1], s_hi);
   }
 }
 
@@ -565,13 +634,13 @@ cudaError_t delay_range(int fmt, const void* recs, uint64_t n_syn,
   BuildShape sh;
   cudaError_t e;
   if (fmt == SNN_W_FP32_12B) {
-    if ((e = build_shape(k_delay_range<SNN_W_FP32_12B>, grid_for(n_syn, 256), 256,
+    if ((e = build_shape(k_delay_range<SNN_W_FP32_12B>, std::min(grid_for(n_syn, 256), 4096u), 256,
                          0, &sh)) != cudaSuccess)
       return e;
     k_delay_range<SNN_W_FP32_12B><<<sh.blocks, sh.threads, sh.smem, s>>>(
         recs, n_syn, dmin_dmax);
   } else {
-    if ((e = build_shape(k_delay_range<SNN_W_BF16_8B>, grid_for(n_syn, 256), 256,
+    if ((e = build_shape(k_delay_range<SNN_W_BF16_8B>, std::min(grid_for(n_syn, 256), 4096u), 256,
                          0, &sh)) != cudaSuccess)
       return e;
     k_delay_range<SNN_W_BF16_8B><<<sh.blocks, sh.threads, sh.smem, s>>>(

@@ -28,6 +28,7 @@ def _compare(net, store, exact_w=True, fmt=0):
     rp, tg, dl, w = net.read_store()
     st = net.stats()
     assert np.array_equal(rp, store.row_ptr)
+    differ = 0
     tw = st.tile_width
     wo = store.w.astype(np.float32)
     dlo = store.delay.astype(np.uint8)
@@ -49,6 +50,13 @@ def _compare(net, store, exact_w=True, fmt=0):
             # format at most a one-ulp difference can remain, and rarely
             ulp = np.spacing(np.abs(ow)) * (65536.0 if fmt == 1 else 1.0)
             assert np.all(np.abs(gw - ow) <= ulp), i
+            differ += int(np.count_nonzero(gw != ow))
+    # BF16 stores decide most roundings from an FP32 evaluation with an error
+    # bound (the FP64 one only near a rounding boundary): the result is the
+    # FP64 path's, so a differing weight stays as rare as a last-bit FP64
+    # difference between the two math libraries
+    if not exact_w and fmt == 1:
+        assert differ <= 1e-4 * max(len(tg), 1), differ
 
 
 @pytest.mark.parametrize("fmt", [0, 1])
