@@ -112,14 +112,16 @@ def stdp_config(w_e):
     return dict(tau_plus=20.0, tau_minus=20.0, lam=0.1, alpha=STDP_ALPHA,
                 mu=STDP_MU, w0=w_e * STDP_ALPHA ** (1.0 / (1.0 - STDP_MU)),
                 w_max=100.0, history=16)
-# DRAM bytes (read + write) per synaptic event of k_deliver_tiled, summed by
-# ncu over all launches of one timed step of the workload and divided by
-# that step's events (profiles/dram_k_deliver_tiled_<workload>.md).
-# It stands for the kernel it was measured on: the entry is used only while
-# the kernel sources (comments aside) hash to the recorded prefixes.
+# DRAM bytes (read + write) per synaptic event of k_deliver_tiled, measured
+# by ncu on launches of a small simulated case with the full-size launch
+# shape (same in-degree, runs per tile and window; a few GB on the device)
+# and divided by those launches' events (profiles/dram_k_deliver_tiled_*.md);
+# bench.py scales it by the events of an average full-size launch.  It
+# stands for the kernel it was measured on: the entry is used only while the
+# kernel sources (comments aside) hash to the recorded prefixes.
 TRAFFIC_B_PER_EVENT = {
-    "balanced-112500-fp32": (12.549, "ee1a403f501c8ab1", "a95a503bdbca9feb"),
-    "balanced-562500-bf16": (9.178, "ee1a403f501c8ab1", "a95a503bdbca9feb"),
+    "balanced-112500-fp32": (12.357, "6d4de1a684b67570", "ddb55fd96b82d881"),
+    "balanced-562500-bf16": (9.295, "6d4de1a684b67570", "ddb55fd96b82d881"),
 }
 # serving: a Poisson stream of independent balanced nets (BF16 records,
 # N log-uniform in [1,250, 112,500], 100 ms - 1 s each), mean rate in req/s
