@@ -166,15 +166,20 @@ __device__ uint16_t bf16_weight_bits(const BuildFixed& b, bool exc,
 }
 
 // Writes a record; returns |stored weight| (as stored, widened to float).
+// FP32 records also carry, above the delay byte, the record's cell in its
+// tile's ring-buffer window (d TW + position in the tile; below 2^24 for
+// tiles narrower than 2^16 targets, else 0), so that interval-list
+// deliveries need neither the target word nor the index arithmetic.
 template <int FMT>
 __device__ __forceinline__ float store_rec(void* recs, uint64_t idx,
-                                           uint32_t tgt, uint32_t d, double w) {
+                                           uint32_t tgt, uint32_t d, double w,
+                                           uint32_t cell = 0u) {
   if (FMT == SNN_W_FP32_12B) {
     uint32_t* p = reinterpret_cast<uint32_t*>(recs) + idx * 3u;
     const float wf = __double2float_rn(w);
     p[0] = tgt;
     p[1] = __float_as_uint(wf);
-    p[2] = d & 0xFFu;
+    p[2] = (d & 0xFFu) | (cell < (1u << 24) ? cell << 8 : 0u);
     return fabsf(wf);
   } else {
     uint2 r;
@@ -207,8 +212,11 @@ __device__ void pack_row(const uint64_t* sorted, uint32_t len, uint32_t row,
       reinterpret_cast<uint2*>(recs)[beg + p] = rec;
       wmax = fmaxf(wmax, fabsf(bf16_to_f32(bits)));
     } else {
+      const uint32_t in_tile = (uint32_t)(key >> 32) & ((1u << g.lb) - 1u);
+      const uint32_t cell = g.tw < (1u << 16) ? d * g.tw + in_tile : (1u << 24);
       wmax = fmaxf(wmax, store_rec<FMT>(recs, beg + p, tgt, d,
-                                        weight_of<WMODE>(b, edge_w, exc, tgt, tie)));
+                                        weight_of<WMODE>(b, edge_w, exc, tgt, tie),
+                                        cell));
     }
     // multiplicity of (target, delay): length of the run of equal keys
     // (ignoring the tie field) that starts here

@@ -678,6 +678,18 @@ __device__ __forceinline__ Rec1<SNN_W_BF16_8B> load_rec<SNN_W_BF16_8B>(
   x.b = u.y;
   return x;
 }
+// FP32 records, interval-list launches: only the weight and the delay word,
+// whose upper 24 bits hold the record's cell in its tile's window,
+// d TW + (target - first target of the tile), written by the store build.
+__device__ __forceinline__ Rec1<SNN_W_FP32_12B> load_rec_wc(const void* recs,
+                                                           uint64_t r) {
+  const uint32_t* p = reinterpret_cast<const uint32_t*>(recs) + r * 3u;
+  Rec1<SNN_W_FP32_12B> x;
+  x.a = 0u;
+  x.b = __ldcs(p + 1);
+  x.c = __ldcs(p + 2);
+  return x;
+}
 __device__ __forceinline__ void rec_fields(const Rec1<SNN_W_FP32_12B>& x,
                                            uint32_t& tgt, uint32_t& d,
                                            float& w) {
@@ -854,6 +866,10 @@ __device__ __forceinline__ void deliver_tile_body(
   constexpr int U = PL ? (FMT == SNN_W_FP32_12B ? 1 : 2)
                        : (FMT == SNN_W_FP32_12B ? 2 : (SHORT ? 6 : 4));
   constexpr int PER = SHORT ? 2 : 3;
+  // FP32 interval lists: each record's cell comes precomputed in its delay
+  // word (no target load, no d TW + target arithmetic); bounds-checked
+  // builds keep the checked form
+  constexpr bool CELL = FAST && FMT == SNN_W_FP32_12B && !PL && !COUNT && !kChecked;
   // run descriptors of one batch (desc_cap spikes), after the accumulator
   SegDesc* const s_desc =
       reinterpret_cast<SegDesc*>(reinterpret_cast<char*>(acc_mem) + desc_off);
@@ -1010,6 +1026,13 @@ __device__ __forceinline__ void deliver_tile_body(
       atomicAdd(v.counts + (size_t)(((uint32_t)t + d) & v.slot_mask) * v.pitch + tgt,
                 1u);
   };
+  // one event of an interval list (in the window, fixed point) by its cell
+  auto add_cell = [&](uint32_t cell, float w) {
+    int hi, lo;
+    fixed_split(w, fx, hi, lo);
+    atomicAdd(&accH[cell], hi);
+    atomicAdd(&accL[cell], lo);
+  };
 
   // plastic E->E synapse: update its weight (record index r), store it
   StdpConst sc{};
@@ -1045,7 +1068,10 @@ __device__ __forceinline__ void deliver_tile_body(
       for (int q = 0; q < PER; ++q) {
         const uint32_t idx = lane + 32u * q;
         if (idx < len) {
-          r[u][q] = load_rec<FMT>(v.recs, beg + idx);
+          if constexpr (CELL)
+            r[u][q] = load_rec_wc(v.recs, beg + idx);
+          else
+            r[u][q] = load_rec<FMT>(v.recs, beg + idx);
           if (pl) wv[u][q] = __ldcs(v.sp.wp + beg + idx);
         }
       }
@@ -1057,9 +1083,22 @@ __device__ __forceinline__ void deliver_tile_body(
     for (int u = 0; u < U; ++u) {
       if (k0 + u >= nb) break;
       const SegDesc sd = s_desc[k0 + u];
-      const int32_t off =
-          (int32_t)(((long long)sd.t - base) * (long long)TW) - (int32_t)tgt_lo;
+      const int32_t roff = (int32_t)(((long long)sd.t - base) * (long long)TW);
+      const int32_t off = roff - (int32_t)tgt_lo;
       const bool pl = PL && tile_plastic && s_kprev[k0 + u] >= 0.f;
+      if constexpr (CELL) {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          const uint32_t idx = lane + 32u * q;
+          if (idx < sd.len)
+            add_cell((r[u][q].c >> 8) + (uint32_t)roff, __uint_as_float(r[u][q].b));
+        }
+        for (uint32_t idx = 32u * PER + lane; idx < sd.len; idx += 32u) {
+          const Rec1<FMT> x = load_rec_wc(v.recs, sd.beg + idx);
+          add_cell((x.c >> 8) + (uint32_t)roff, __uint_as_float(x.b));
+        }
+        continue;
+      }
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
         const uint32_t idx = lane + 32u * q;
@@ -1705,10 +1744,13 @@ cudaError_t launch_deliver_tiled_gx(const NetView& v, unsigned long long* pair,
   }
   {
     if (interval_exact) {
-      if (v.fmt == SNN_W_FP32_12B)
-        return launch_tiled_t<SNN_W_FP32_12B, false, false, true, false,
-                              false, GX>(v, pair, done, list, 0, advance_time, s);
-      if (v.acc_words == 1)
+      if (v.fmt == SNN_W_FP32_12B) {
+        // (the records' precomputed cells exist for tiles below 2^16
+        // targets; wider tiles take the general form below)
+        if (v.tile_w < (1u << 16))
+          return launch_tiled_t<SNN_W_FP32_12B, false, false, true, false,
+                                false, GX>(v, pair, done, list, 0, advance_time, s);
+      } else if (v.acc_words == 1) {
         // runs of a few dozen records: two slots for six runs per pass
         return v.mean_run < 48.f
                    ? launch_tiled_t<SNN_W_BF16_8B, false, false, true, true,
@@ -1717,8 +1759,10 @@ cudaError_t launch_deliver_tiled_gx(const NetView& v, unsigned long long* pair,
                    : launch_tiled_t<SNN_W_BF16_8B, false, false, true, true,
                                     false, GX>(v, pair, done, list, 0,
                                                advance_time, s);
-      return launch_tiled_t<SNN_W_BF16_8B, false, false, true, false, false,
-                            GX>(v, pair, done, list, 0, advance_time, s);
+      } else {
+        return launch_tiled_t<SNN_W_BF16_8B, false, false, true, false, false,
+                              GX>(v, pair, done, list, 0, advance_time, s);
+      }
     }
   }
   if (v.fmt == SNN_W_FP32_12B)
