@@ -79,6 +79,20 @@ def test_fixed_indegree_store_weight_spread(fmt):
         _compare(net, O.build_fixed_indegree(cp), exact_w=False, fmt=fmt)
 
 
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_fixed_indegree_store_wide_spread_clipped(fmt):
+    """Spreads as large as the means: excitatory weights clipped at zero
+    (about a sixth of them), inhibitory ones crossing zero -- the BF16
+    rounding decided from FP32 near zero and at the clip, against the
+    oracle's FP64 values."""
+    net, cp = fixed_net(3000, 750, 300, 75, 22.4, -112.0, 10, 20, seed=29,
+                        fmt=fmt, sd_e=22.4, sd_i=112.0)
+    with net:
+        _compare(net, O.build_fixed_indegree(cp), exact_w=False, fmt=fmt)
+        w = net.read_store()[3]
+        assert np.count_nonzero(w == 0.0) > 0.05 * len(w)
+
+
 def test_fixed_indegree_store_medium_fixed_delay():
     net, cp = fixed_net(4000, 1000, 400, 100, 22.4, -112.0, 15, 15, seed=5)
     with net:
