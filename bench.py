@@ -1113,8 +1113,12 @@ def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
     s = torch.cuda.Stream()
     torch.cuda.set_stream(s)
     lo, hi = PT.split(wl.n, ws)[rank]
+    # spike log: this rank's spikes of the warm-up, timed and end-to-end
+    # steps (read back by the end-to-end steps)
+    per_step = int((hi - lo) * 8.0 * bio_ms * 1e-3 * 4) + 100000
     p = snn.params(n_exc=wl.n_e, n_inh=wl.n_i, weight_format=fmt, seed=1,
-                   nu_ext=nu_ext)
+                   nu_ext=nu_ext,
+                   spike_log_capacity=per_step * (args.warmup + args.steps + 2))
     w_e = snn.snn_psc_weight_for_psp(p, wl.psp_mv)
     p.w_ext = w_e
     c = snn.conn_params(k_exc=wl.k_e, k_inh=wl.k_i, w_exc=w_e,
@@ -1172,8 +1176,11 @@ def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
         t = step(t)
     torch.cuda.synchronize()
     a = net.stats()
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    clocks = Clocks(int(cvd) if cvd.isdigit() else local)
     barrier()
     torch.cuda.synchronize()
+    clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(s)
@@ -1182,6 +1189,7 @@ def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
     e1.record(s)
     e1.synchronize()
     torch.cuda.synchronize()
+    clk = clocks.stop()
     barrier()
     ms = e0.elapsed_time(e1)
     b = net.stats()
@@ -1194,6 +1202,38 @@ def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
     ms_max, ev_all, sp_all = reduce_over_ranks(ms, events, spikes)
     if b.error_flags:
         raise RuntimeError(f"device error flags {b.error_flags:#x}")
+    # end to end through the public API with host buffers: this rank's
+    # neuron state in from pinned host memory, the step, its spikes and
+    # state back
+    e2e = None
+    if xch is not None:
+        n_loc = net.n
+        hV = torch.empty(n_loc, dtype=torch.float32).pin_memory()
+        hI = torch.empty_like(hV).pin_memory()
+        hJ = torch.empty_like(hV).pin_memory()
+        hR = torch.empty(n_loc, dtype=torch.int32).pin_memory()
+        cap = per_step * (args.warmup + args.steps + 2)
+        hsrc = torch.empty(cap, dtype=torch.int32).pin_memory()
+        ht = torch.empty(cap, dtype=torch.int32).pin_memory()
+        snn.snn_read_state(net.h, hV, hI, hJ, hR)
+        snn.snn_read_spikes(net.h, hsrc, ht)
+        sp_read = [0]
+
+        def e2e_step():
+            snn.snn_write_state(net.h, hV, hI, hJ, hR)
+            step(0)
+            sp_read[0] += snn.snn_read_spikes(net.h, hsrc, ht)
+            snn.snn_read_state(net.h, hV, hI, hJ, hR)
+
+        c0 = net.stats()
+        ms_e2e = timed(torch, s, e2e_step, args.steps)
+        c1 = net.stats()
+        ms_e2e_max, ev_e2e_all, sp_e2e_all = reduce_over_ranks(
+            ms_e2e, c1.events_delivered - c0.events_delivered, sp_read[0])
+        e2e = {"value": ev_e2e_all / (ms_e2e_max * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": 16 * wl.n,
+               "d2h_bytes_per_step": int(16 * wl.n + 8 * sp_e2e_all / args.steps),
+               "steps": args.steps}
     if xch is not None:
         xch.close()
     net.close()
@@ -1218,8 +1258,8 @@ def run_partitioned(args, wl, fmt, bio_ms, nu_ext):
                                 if args.host_exchange else
                                 "device buffers (fixed all_gather_into_tensor, "
                                 "no host sync), 8-interval CUDA graphs")},
-        "roofline": None, "cpu_baseline": None, "e2e": None,
-        "gpu_launches": launches,
+        "roofline": None, "cpu_baseline": None, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 

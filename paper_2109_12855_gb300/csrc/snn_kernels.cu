@@ -93,77 +93,12 @@ __global__ void k_fill_i32(int32_t* p, int32_t value, uint64_t n) {
 // ring-buffer values of a step are loaded in groups of eight independent
 // loads ahead of use (one memory round trip per eight steps instead of one
 // per step).  Spikes are kept as a per-thread bit mask of step indices and
-// compacted once per block for up to 32 steps: a block scan of the per-thread
-// counts, then one set of global atomics per block reserves the block's list
-// entries and chunk ranges.
+// compacted once per warp for up to 32 steps: a warp scan of the per-thread
+// counts, then one set of global atomics per warp with spikes reserves its
+// list entries and chunk ranges.
 // ---------------------------------------------------------------------------
 constexpr int kPrefetch = 8;
 
-// Exclusive block scan of two 32-bit counts and a block sum of a 64-bit one;
-// returns the block totals through *tot_* (all threads).
-__device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b,
-                                            unsigned long long c,
-                                            uint32_t* ex_a, uint32_t* ex_b,
-                                            uint32_t* tot_a, uint32_t* tot_b,
-                                            unsigned long long* tot_c) {
-  __shared__ uint32_t sa[32], sb[32];
-  __shared__ unsigned long long sc[32];
-  __shared__ uint32_t s_ta, s_tb;
-  __shared__ unsigned long long s_tc;
-  const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-  const unsigned nw = (blockDim.x + 31) >> 5;
-  uint32_t ia = a, ib = b;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t ya = __shfl_up_sync(kFull, ia, o);
-    uint32_t yb = __shfl_up_sync(kFull, ib, o);
-    if (lane >= (unsigned)o) {
-      ia += ya;
-      ib += yb;
-    }
-  }
-  unsigned long long rc = c;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) rc += __shfl_xor_sync(kFull, rc, o);
-  if (lane == 31) {
-    sa[wid] = ia;
-    sb[wid] = ib;
-  }
-  if (lane == 0) sc[wid] = rc;
-  __syncthreads();
-  if (wid == 0) {
-    const uint32_t xa = lane < nw ? sa[lane] : 0u;
-    const uint32_t xb = lane < nw ? sb[lane] : 0u;
-    unsigned long long xc = lane < nw ? sc[lane] : 0ull;
-    uint32_t pa = xa, pb = xb;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t ya = __shfl_up_sync(kFull, pa, o);
-      uint32_t yb = __shfl_up_sync(kFull, pb, o);
-      if (lane >= (unsigned)o) {
-        pa += ya;
-        pb += yb;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) xc += __shfl_xor_sync(kFull, xc, o);
-    __syncwarp();
-    sa[lane] = pa - xa;  // exclusive prefix over warps
-    sb[lane] = pb - xb;
-    if (lane == 31) {
-      s_ta = pa;
-      s_tb = pb;
-    }
-    if (lane == 0) s_tc = xc;
-  }
-  __syncthreads();
-  *ex_a = sa[wid] + ia - a;
-  *ex_b = sb[wid] + ib - b;
-  *tot_a = s_ta;
-  *tot_b = s_tb;
-  *tot_c = s_tc;
-  __syncthreads();  // the shared arrays are reused by the next call
-}
 
 // Plasticity state at a spike of excitatory neuron i at step t: the
 // presynaptic trace (kept with the values before this spike, which its own
@@ -212,8 +147,6 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
                                             long long t0_arg, uint32_t block) {
   __shared__ uint32_t s_thr[kMaxPoisson];
   __shared__ uint8_t s_guide[256];
-  __shared__ unsigned long long s_base[2];
-  __shared__ uint32_t s_xbase;
   for (int k = threadIdx.x; k < c.n_thr; k += blockDim.x) s_thr[k] = c.thr[k];
   for (int k = threadIdx.x; k < 256; k += blockDim.x) s_guide[k] = c.guide[k];
   const long long t0 = from_ctl ? v.ctl->t_now : t0_arg;
@@ -320,31 +253,44 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
         }
       }
     }
-    // block compaction of this chunk's spikes
+    // warp compaction of this chunk's spikes: a warp with spikes scans its
+    // lanes' counts and reserves its list entries, chunk ranges and log
+    // slots with one set of global atomics; warps without spikes (most of
+    // them at a few Hz) go on without waiting for anyone
     const uint32_t cnt = __popc(mask);
-    if (__syncthreads_or(cnt != 0)) {
-      uint32_t ex_cnt, ex_ch, tot_cnt, tot_ch;
-      unsigned long long tot_deg;
-      block_scan2(cnt, cnt * nch, (unsigned long long)cnt * deg, &ex_cnt,
-                  &ex_ch, &tot_cnt, &tot_ch, &tot_deg);
-      if (threadIdx.x == 0) {
-        // all four counters first (separate lines, both returning atomics
-        // in flight together), then the overflow check on the list's one
-        const unsigned long long old =
-            atomicAdd(&v.ctl->pair, ((unsigned long long)tot_cnt << 32) | tot_ch);
-        const unsigned long long logb =
-            v.log_cap ? atomicAdd(&v.ctl->log_count, (unsigned long long)tot_cnt)
-                      : 0ull;
-        s_xbase = v.xbuf ? atomicAdd(v.xbuf, tot_cnt) : 0u;
-        atomicAdd(&v.ctl->pending_events, tot_deg);
-        atomicAdd(&v.ctl->spikes, (unsigned long long)tot_cnt);
-        if ((uint32_t)old + (unsigned long long)tot_ch > 0xFFFFFFFFull)
-          atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_CHUNKS);
-        s_base[0] = old;
-        s_base[1] = logb;
+    if (__ballot_sync(kFull, cnt != 0)) {
+      const unsigned lane = threadIdx.x & 31u;
+      uint32_t inc_cnt = cnt, inc_ch = cnt * nch;
+      unsigned long long inc_deg = (unsigned long long)cnt * deg;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ya = __shfl_up_sync(kFull, inc_cnt, o);
+        const uint32_t yb = __shfl_up_sync(kFull, inc_ch, o);
+        const unsigned long long yc = __shfl_up_sync(kFull, inc_deg, o);
+        if (lane >= (unsigned)o) {
+          inc_cnt += ya;
+          inc_ch += yb;
+          inc_deg += yc;
+        }
       }
-      __syncthreads();
-      const unsigned long long old = s_base[0], logb = s_base[1];
+      const uint32_t ex_cnt = inc_cnt - cnt, ex_ch = inc_ch - cnt * nch;
+      unsigned long long old = 0ull, logb = 0ull;
+      uint32_t xbase = 0u;
+      if (lane == 31u) {  // the warp's totals
+        // all counters first (separate lines, the returning atomics in
+        // flight together), then the overflow check on the list's one
+        old = atomicAdd(&v.ctl->pair, ((unsigned long long)inc_cnt << 32) | inc_ch);
+        logb = v.log_cap ? atomicAdd(&v.ctl->log_count, (unsigned long long)inc_cnt)
+                         : 0ull;
+        xbase = v.xbuf ? atomicAdd(v.xbuf, inc_cnt) : 0u;
+        atomicAdd(&v.ctl->pending_events, inc_deg);
+        atomicAdd(&v.ctl->spikes, (unsigned long long)inc_cnt);
+        if ((uint32_t)old + (unsigned long long)inc_ch > 0xFFFFFFFFull)
+          atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_CHUNKS);
+      }
+      old = __shfl_sync(kFull, old, 31);
+      logb = __shfl_sync(kFull, logb, 31);
+      xbase = __shfl_sync(kFull, xbase, 31);
       uint32_t m = mask, k = 0;
       while (m) {
         const int b = __ffs(m) - 1;
@@ -365,7 +311,7 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
           atomicOr(&v.ctl->error_flags, (unsigned)SNN_ERRF_SPIKE_LIST);
         }
         if (v.xbuf) {  // the partition exchange's copy of the list
-          const uint32_t xi = s_xbase + ex_cnt + k;
+          const uint32_t xi = xbase + ex_cnt + k;
           if (xi < v.xcap) {
             reinterpret_cast<uint2*>(v.xbuf + 4)[xi] =
                 make_uint2(v.g0 + i, (uint32_t)(int32_t)t);
@@ -397,7 +343,6 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
         }
         ++k;
       }
-      __syncthreads();  // s_base is rewritten by the next chunk
     }
   }
   if (live) {
