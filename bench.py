@@ -113,10 +113,12 @@ def stdp_config(w_e):
                 mu=STDP_MU, w0=w_e * STDP_ALPHA ** (1.0 / (1.0 - STDP_MU)),
                 w_max=100.0, history=16)
 # DRAM bytes (read + write) per synaptic event of k_deliver_tiled, measured
-# by ncu on launches of a small simulated case with the full-size launch
-# shape (same in-degree, runs per tile and window; a few GB on the device)
-# and divided by those launches' events (profiles/dram_k_deliver_tiled_*.md);
-# bench.py scales it by the events of an average full-size launch.  It
+# by ncu on launches of a small simulated case (a few GB on the device; for
+# the 1.27e9-synapse network with its launch shape: in-degree, runs per
+# tile, window; for the 6.3e9 one a short-run BF16 case, whose runs are
+# shorter than the full network's) and divided by those launches' events
+# (profiles/dram_k_deliver_tiled_*.md); bench.py scales it by the events of
+# an average full-size launch.  It
 # stands for the kernel it was measured on: the entry is used only while the
 # kernel sources (comments aside) hash to the recorded prefixes.
 TRAFFIC_B_PER_EVENT = {
