@@ -810,7 +810,13 @@ __device__ __forceinline__ void deliver_tile_body(
   // (plastic nets also hold each record's plastic weight: fewer runs)
   constexpr int U = PL ? (FMT == SNN_W_FP32_12B ? 1 : 2)
                        : (FMT == SNN_W_FP32_12B ? 2 : (SHORT ? 6 : 4));
-  constexpr int PER = SHORT ? 2 : 3;
+  constexpr int PER = 3;
+  // lanes per run: short runs take half a warp each, two side by side (48
+  // record slots per run instead of a whole warp's)
+  constexpr int LG = SHORT ? 16 : 32;
+  constexpr int G = 32 / LG;   // runs side by side in a warp
+  constexpr int UR = U / G;    // run slots of a lane per pass
+  static_assert(U % G == 0, "runs per pass must fill the warp");
   // FP32 interval lists: each record's cell comes precomputed in its delay
   // word (no target load, no d TW + target arithmetic); bounds-checked
   // builds keep the checked form
@@ -1001,17 +1007,20 @@ __device__ __forceinline__ void deliver_tile_body(
     my_trunc += o.trunc | (km < 0.f ? 1u : 0u);
     return o.w;
   };
-  auto load_pass = [&](Rec1<FMT> (&r)[U][PER], float (&wv)[U][PER], uint32_t k0,
+  const uint32_t sub = lane & (uint32_t)(LG - 1);  // lane within its run
+  const uint32_t grp = lane / (uint32_t)LG;         // run side of the warp
+  auto load_pass = [&](Rec1<FMT> (&r)[UR][PER], float (&wv)[UR][PER], uint32_t k0,
                        uint32_t nb) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const bool ok = k0 + u < nb;
-      const uint64_t beg = ok ? s_desc[k0 + u].beg : 0ull;
-      const uint32_t len = ok ? s_desc[k0 + u].len : 0u;
-      const bool pl = PL && tile_plastic && ok && s_kprev[k0 + u] >= 0.f;
+    for (int u = 0; u < UR; ++u) {
+      const uint32_t j = k0 + (uint32_t)(G * u) + grp;
+      const bool ok = j < nb;
+      const uint64_t beg = ok ? s_desc[j].beg : 0ull;
+      const uint32_t len = ok ? s_desc[j].len : 0u;
+      const bool pl = PL && tile_plastic && ok && s_kprev[j] >= 0.f;
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
-        const uint32_t idx = lane + 32u * q;
+        const uint32_t idx = sub + (uint32_t)LG * q;
         if (idx < len) {
           if constexpr (CELL)
             r[u][q] = load_rec_wc(v.recs, beg + idx);
@@ -1022,23 +1031,27 @@ __device__ __forceinline__ void deliver_tile_body(
       }
     }
   };
-  auto add_pass = [&](const Rec1<FMT> (&r)[U][PER], const float (&wv)[U][PER],
+  auto add_pass = [&](const Rec1<FMT> (&r)[UR][PER], const float (&wv)[UR][PER],
                       uint32_t k0, uint32_t nb) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (k0 + u >= nb) break;
-      const SegDesc sd = s_desc[k0 + u];
+    for (int u = 0; u < UR; ++u) {
+      const uint32_t j = k0 + (uint32_t)(G * u) + grp;
+      if (j >= nb) {
+        if constexpr (G == 1) break;  // (uniform across the warp)
+        else continue;
+      }
+      const SegDesc sd = s_desc[j];
       const int32_t roff = (int32_t)(((long long)sd.t - base) * (long long)TW);
       const int32_t off = roff - (int32_t)tgt_lo;
-      const bool pl = PL && tile_plastic && s_kprev[k0 + u] >= 0.f;
+      const bool pl = PL && tile_plastic && s_kprev[j] >= 0.f;
       if constexpr (CELL) {
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
-          const uint32_t idx = lane + 32u * q;
+          const uint32_t idx = sub + (uint32_t)LG * q;
           if (idx < sd.len)
             add_cell((r[u][q].c >> 8) + (uint32_t)roff, __uint_as_float(r[u][q].b));
         }
-        for (uint32_t idx = 32u * PER + lane; idx < sd.len; idx += 32u) {
+        for (uint32_t idx = (uint32_t)LG * PER + sub; idx < sd.len; idx += (uint32_t)LG) {
           const Rec1<FMT> x = load_rec_wc(v.recs, sd.beg + idx);
           add_cell((x.c >> 8) + (uint32_t)roff, __uint_as_float(x.b));
         }
@@ -1046,24 +1059,24 @@ __device__ __forceinline__ void deliver_tile_body(
       }
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
-        const uint32_t idx = lane + 32u * q;
+        const uint32_t idx = sub + (uint32_t)LG * q;
         if (idx < sd.len) {
           uint32_t tgt, d;
           float w;
           rec_fields(r[u][q], tgt, d, w);
           if (!rec_in_bounds(v, tgt, d, tgt_lo, TW)) continue;
           if (pl && tgt < v.sp.n_exc)
-            w = plastic(tgt, k0 + u, sd.t, d, wv[u][q], sd.beg + idx);
+            w = plastic(tgt, j, sd.t, d, wv[u][q], sd.beg + idx);
           add(tgt, sd.t, off, d, w);
         }
       }
-      for (uint32_t idx = 32u * PER + lane; idx < sd.len; idx += 32u) {
+      for (uint32_t idx = (uint32_t)LG * PER + sub; idx < sd.len; idx += (uint32_t)LG) {
         uint32_t tgt, d;
         float w;
         rec_fields(load_rec<FMT>(v.recs, sd.beg + idx), tgt, d, w);
         if (!rec_in_bounds(v, tgt, d, tgt_lo, TW)) continue;
         if (pl && tgt < v.sp.n_exc)
-          w = plastic(tgt, k0 + u, sd.t, d, __ldcs(v.sp.wp + sd.beg + idx),
+          w = plastic(tgt, j, sd.t, d, __ldcs(v.sp.wp + sd.beg + idx),
                       sd.beg + idx);
         add(tgt, sd.t, off, d, w);
       }
@@ -1161,16 +1174,16 @@ __device__ __forceinline__ void deliver_tile_body(
     // the weight update)
     if constexpr (PL) {
       for (uint32_t k = warp * U; k < nb; k += kTileWarps * U) {
-        Rec1<FMT> r[U][PER];
-        float wv[U][PER];
+        Rec1<FMT> r[UR][PER];
+        float wv[UR][PER];
         load_pass(r, wv, k, nb);
         add_pass(r, wv, k, nb);
       }
     } else {
       uint32_t k = grab();
       while (k < nb) {
-        Rec1<FMT> r[U][PER];
-        float wv[U][PER];
+        Rec1<FMT> r[UR][PER];
+        float wv[UR][PER];
         load_pass(r, wv, k, nb);
         const uint32_t k_next = grab();
         add_pass(r, wv, k, nb);
