@@ -798,8 +798,8 @@ __device__ __noinline__ StdpOut stdp_weight(float w, int32_t t, uint32_t d,
 // the host has shown to exist for every spike count: no per-event test of
 // either.
 // ONE: one-word cells known at compile time (BF16 stores).  SHORT: runs of
-// a few dozen records (BF16, static): more runs per warp pass, fewer slots
-// per run.
+// a few dozen records (BF16, static): eight runs per warp pass, each on half
+// a warp (48 record slots per run instead of 96).
 template <int FMT, bool COUNT, bool PL, bool FAST = false, bool ONE = false,
           bool SHORT = false, bool GX = false>
 __device__ __forceinline__ void deliver_tile_body(
@@ -809,7 +809,7 @@ __device__ __forceinline__ void deliver_tile_body(
   // U runs per warp pass, PER records per lane of each loaded before use
   // (plastic nets also hold each record's plastic weight: fewer runs)
   constexpr int U = PL ? (FMT == SNN_W_FP32_12B ? 1 : 2)
-                       : (FMT == SNN_W_FP32_12B ? 2 : (SHORT ? 6 : 4));
+                       : (FMT == SNN_W_FP32_12B ? 2 : (SHORT ? 8 : 4));
   constexpr int PER = 3;
   // lanes per run: short runs take half a warp each, two side by side (48
   // record slots per run instead of a whole warp's)
@@ -1709,7 +1709,7 @@ cudaError_t launch_deliver_tiled_gx(const NetView& v, unsigned long long* pair,
           return launch_tiled_t<SNN_W_FP32_12B, false, false, true, false,
                                 false, GX>(v, pair, done, list, 0, advance_time, s);
       } else if (v.acc_words == 1) {
-        // runs of a few dozen records: two slots for six runs per pass
+        // runs of a few dozen records: half a warp per run, eight per pass
         return v.mean_run < 48.f
                    ? launch_tiled_t<SNN_W_BF16_8B, false, false, true, true,
                                     true, GX>(v, pair, done, list, 0,
