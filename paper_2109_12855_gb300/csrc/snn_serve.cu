@@ -723,6 +723,10 @@ int lane_step_exclusive(snn_server* sv, Lane* ln, bool* launched) {
   int rc;
   if ((rc = drop_cancelled(sv, ln)) != SNN_OK) return rc;
   if ((rc = retire_done(sv, ln)) != SNN_OK) return rc;
+  // steps of nets retired just now keep no pointer to their request (the
+  // caller may release it once it has seen the result)
+  for (Lane::XStep& x : ln->x_inflight)
+    if (x.q && !x.q->net) x.q = nullptr;
   // fold in the GPU time of completed steps, oldest first
   while (!ln->x_inflight.empty()) {
     Lane::XStep& x = ln->x_inflight.front();
@@ -733,7 +737,7 @@ int lane_step_exclusive(snn_server* sv, Lane* ln, bool* launched) {
     SCK(cudaEventElapsedTime(&ms, x.e0, x.e1));
     ln->gpu_ms += ms;
     const double us = 1e3 * ms / std::max(x.intervals, 1);
-    x.q->iv_us = x.q->iv_us > 0 ? 0.5 * (x.q->iv_us + us) : us;
+    if (x.q) x.q->iv_us = x.q->iv_us > 0 ? 0.5 * (x.q->iv_us + us) : us;
     ln->x_spare.push_back(x.e0);
     ln->x_spare.push_back(x.e1);
     ln->x_inflight.pop_front();
@@ -767,8 +771,11 @@ int lane_step_exclusive(snn_server* sv, Lane* ln, bool* launched) {
   }
   cudaStream_t s = q.net->stream;
   SCK(cudaEventRecord(e[0], s));
-  if ((rc = simulate_async(q.net, steps, sv->building.load() == 0)) != SNN_OK)
+  if ((rc = simulate_async(q.net, steps, sv->building.load() == 0)) != SNN_OK) {
+    ln->x_spare.push_back(e[0]);
+    ln->x_spare.push_back(e[1]);
     return rc;
+  }
   SCK(cudaEventRecord(e[1], s));
   const int n_iv = (int)((steps + iv - 1) / iv);
   ln->x_inflight.push_back({&q, n_iv, e[0], e[1]});
