@@ -149,12 +149,6 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
   __shared__ uint8_t s_guide[256];
   for (int k = threadIdx.x; k < c.n_thr; k += blockDim.x) s_thr[k] = c.thr[k];
   for (int k = threadIdx.x; k < 256; k += blockDim.x) s_guide[k] = c.guide[k];
-  const long long t0 = from_ctl ? v.ctl->t_now : t0_arg;
-  if (block == 0 && threadIdx.x == 0) {
-    v.ctl->iv_steps = n_steps;
-    if (!from_ctl) v.ctl->t_now = t0;
-  }
-  __syncthreads();
 
   const uint32_t i = block * blockDim.x + threadIdx.x;
   const bool live = i < v.n;
@@ -186,6 +180,17 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
     isi_s1 = v.isi_sum[i];
     isi_s2 = v.isi_sq[i];
   }
+  // the single-net update may start while the previous delivery's last
+  // CTAs run (programmatic dependent launch): everything above reads only
+  // what the previous update wrote; from here on the delivery's ring-buffer
+  // additions, clock and counters must be complete
+  if constexpr (PL) asm volatile("griddepcontrol.wait;" ::: "memory");
+  const long long t0 = from_ctl ? v.ctl->t_now : t0_arg;
+  if (block == 0 && threadIdx.x == 0) {
+    v.ctl->iv_steps = n_steps;
+    if (!from_ctl) v.ctl->t_now = t0;
+  }
+  __syncthreads();
   U4 rnd{0, 0, 0, 0};
   long long rnd_block = -1;
   float* const rb_i = v.rb + i;  // slot s of neuron i at rb_i[s * pitch]
@@ -1274,6 +1279,8 @@ k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
   deliver_tile_body<FMT, COUNT, PL, FAST, ONE, SHORT, GX>(
       v, pair_p, done_p, list, from_list_range, advance_time, blockIdx.x,
       acc_mem, desc_off, desc_cap);
+  // the next update may be scheduled once every CTA got here
+  asm volatile("griddepcontrol.launch_dependents;");
 }
 
 // All nets of a batch in one launch: CTA b delivers tile bmap[b].y of net
@@ -1561,11 +1568,19 @@ cudaError_t launch_update(const NetView& v, const UpdConst& c, int n_steps,
         cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
       sms.store(m, std::memory_order_relaxed);
   }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kUpdThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (blocks > 3u * (unsigned)std::max(sms.load(std::memory_order_relaxed), 1))
-    k_update<4><<<blocks, kUpdThreads, 0, s>>>(v, c, n_steps, from_ctl_time, t0);
-  else
-    k_update<3><<<blocks, kUpdThreads, 0, s>>>(v, c, n_steps, from_ctl_time, t0);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, k_update<4>, v, c, n_steps, from_ctl_time, t0);
+  return cudaLaunchKernelEx(&cfg, k_update<3>, v, c, n_steps, from_ctl_time, t0);
 }
 
 cudaError_t launch_deliver(const NetView& v, unsigned long long* pair,
