@@ -315,6 +315,42 @@ void choose_tiles(uint32_t n, int window, int32_t hint, size_t per_target,
   *n_tiles = (uint32_t)nt;
 }
 
+// Plastic nets: a tile of excitatory targets applies the weight rule to its
+// E->E events, several times the work of a static tile of the same width
+// (measured: 3 to 5 times), and every tile takes a whole SM.  The static
+// tiles after the plastic ones therefore go kStaticTilesPerCta to a CTA,
+// and the width becomes the smallest (at least the chosen one's floor of
+// 64) whose CTAs still fit one wave, so that the plastic tiles are as narrow
+// as the SM count allows.  Nets already needing more than one wave keep
+// their geometry, one tile per CTA.
+constexpr uint32_t kStaticTilesPerCta = 4;
+void balance_plastic_tiles(uint32_t n, uint32_t n_exc, uint32_t* tile_w,
+                           int* lo_bits, uint32_t* n_tiles, uint32_t* pl_tiles,
+                           uint32_t* tile_grp) {
+  const uint32_t tw0 = *tile_w;
+  *pl_tiles = std::min<uint32_t>(*n_tiles, (n_exc + tw0 - 1) / tw0);
+  *tile_grp = 1;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms < 1 || n_exc == 0 || n_exc >= n) return;
+  const uint32_t k = kStaticTilesPerCta;
+  for (uint64_t tw = std::min<uint64_t>(std::max<uint64_t>(64, (n_exc + sms - 1) / sms), tw0);
+       tw <= tw0; ++tw) {
+    const uint64_t nt = (n + tw - 1) / tw, pt = (n_exc + tw - 1) / tw;
+    if (pt + (nt - pt + k - 1) / k > (uint64_t)sms) continue;
+    int lb = 1;
+    while ((1ull << lb) < tw) ++lb;
+    if (nt > (1ull << (24 - lb))) return;  // (the sort key's tile field)
+    *tile_w = (uint32_t)tw;
+    *lo_bits = lb;
+    *n_tiles = (uint32_t)nt;
+    *pl_tiles = (uint32_t)pt;
+    *tile_grp = k;
+    return;
+  }
+}
+
 }  // namespace
 
 void snn::tile_geometry(uint32_t n, int window, int32_t hint, uint32_t* tile_w,
@@ -475,6 +511,11 @@ int build_store(snn_net* net, uint32_t* d_deg, Scatter scatter,
   choose_tiles(net->n, iv + (d_hi - d_lo), net->p.tile_width,
                stdp_bytes_per_target(net, iv + (d_hi - d_lo)), net->acc_words,
                &net->tile_w, &net->lo_bits, &net->n_tiles);
+  net->pl_tiles = net->n_tiles;
+  net->tile_grp = 1;
+  if (net->stdp_on && net->p.tile_width == 0)
+    balance_plastic_tiles(net->n, net->p.n_exc, &net->tile_w, &net->lo_bits,
+                          &net->n_tiles, &net->pl_tiles, &net->tile_grp);
   CK(dalloc(&net->tile_off, (uint64_t)n * (net->n_tiles + 1) * sizeof(uint32_t), net->stream));
   // keys; for 8-byte records the key array becomes the record array
   uint64_t* keys = nullptr;

@@ -232,6 +232,10 @@ struct NetView {
   const uint32_t* tile_off; // [n][n_tiles + 1] row-relative tile starts
   uint32_t tile_w;          // targets per tile (tile tau: [tau tile_w, ...))
   uint32_t n_tiles;
+  // plastic nets: tiles [0, pl_tiles) hold the excitatory (plastic) targets
+  // and take one CTA each; the static tiles after them go tile_grp to a CTA
+  uint32_t pl_tiles;
+  uint32_t tile_grp;
   int d_min, d_max;         // delay range of the store
   int window;               // ring steps one interval's spikes can reach
   // bounds for the exact fixed-point accumulation of k_deliver_tiled

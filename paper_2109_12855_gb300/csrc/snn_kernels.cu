@@ -1276,9 +1276,25 @@ k_deliver_tiled(NetView v, unsigned long long* pair_p, unsigned int* done_p,
                 const SpikeEntry* __restrict__ list, int from_list_range,
                 int advance_time, uint32_t desc_off, uint32_t desc_cap) {
   extern __shared__ __align__(16) int acc_mem[];
-  deliver_tile_body<FMT, COUNT, PL, FAST, ONE, SHORT, GX>(
-      v, pair_p, done_p, list, from_list_range, advance_time, blockIdx.x,
-      acc_mem, desc_off, desc_cap);
+  if constexpr (PL) {
+    // one tile of plastic targets, or up to tile_grp static tiles one
+    // after another in the same shared memory
+    uint32_t t0 = blockIdx.x, t1 = blockIdx.x + 1u;
+    if (blockIdx.x >= v.pl_tiles) {
+      t0 = v.pl_tiles + (blockIdx.x - v.pl_tiles) * v.tile_grp;
+      t1 = min(t0 + v.tile_grp, v.n_tiles);
+    }
+    for (uint32_t t = t0; t < t1; ++t) {
+      if (t > t0) __syncthreads();  // the previous tile's last reads
+      deliver_tile_body<FMT, COUNT, PL, FAST, ONE, SHORT, GX>(
+          v, pair_p, done_p, list, from_list_range, advance_time, t, acc_mem,
+          desc_off, desc_cap);
+    }
+  } else {
+    deliver_tile_body<FMT, COUNT, PL, FAST, ONE, SHORT, GX>(
+        v, pair_p, done_p, list, from_list_range, advance_time, blockIdx.x,
+        acc_mem, desc_off, desc_cap);
+  }
   // the next update may be scheduled once every CTA got here
   asm volatile("griddepcontrol.launch_dependents;");
 }
@@ -1677,8 +1693,12 @@ cudaError_t launch_tiled_t(const NetView& v, unsigned long long* pair,
   DescLayout dl;
   e = desc_layout(tiled_smem_bytes(v), dm, PL, &dl);
   if (e != cudaSuccess) return e;
+  // plastic nets: a CTA per plastic tile, then one per tile_grp static ones
+  const uint32_t ctas =
+      PL ? v.pl_tiles + (v.n_tiles - v.pl_tiles + v.tile_grp - 1u) / v.tile_grp
+         : v.n_tiles;
   k_deliver_tiled<FMT, COUNT, PL, FAST, ONE, SHORT, GX>
-      <<<v.n_tiles, kTileThreads, dl.smem, s>>>(
+      <<<ctas, kTileThreads, dl.smem, s>>>(
       v, pair, done, list, from_list_range, advance_time, dl.off, dl.cap);
   return cudaGetLastError();
 }

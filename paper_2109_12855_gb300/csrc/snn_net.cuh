@@ -57,6 +57,7 @@ struct snn_net {
   uint32_t xcap = 0;
   const void* x_parts_ok = nullptr;  // last gathered-parts pointer validated
   uint32_t tile_w = 0, n_tiles = 0;
+  uint32_t pl_tiles = 0, tile_grp = 1;  // see NetView
   int lo_bits = 0;
   int window = 0;
   uint32_t mult_max = 0, k_in_max = 0, spikes_per_iv = 1;
@@ -111,6 +112,8 @@ struct snn_net {
     v.tile_off = tile_off;
     v.tile_w = tile_w;
     v.n_tiles = n_tiles;
+    v.pl_tiles = pl_tiles ? pl_tiles : n_tiles;
+    v.tile_grp = tile_grp ? tile_grp : 1u;
     v.d_min = dmin;
     v.d_max = dmax;
     v.window = window;
