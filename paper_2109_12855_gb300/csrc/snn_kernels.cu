@@ -225,14 +225,31 @@ __device__ __forceinline__ void update_body(const NetView& v, const UpdConst& c,
         const uint32_t wd[12] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y,
                                  r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
         const int a = (int)(tf & 3);
+        // inversion of each step's word: the group's guide and first
+        // threshold lookups are issued together (independent shared-memory
+        // loads); the search goes on only where the word passes the first
+        // threshold (a threshold inside its guide bucket), as the plain
+        // search would
+        uint32_t wq[kPrefetch];
+        int kq[kPrefetch];
+        uint32_t tq[kPrefetch];
+#pragma unroll
+        for (int q = 0; q < kPrefetch; ++q) {
+          // word (tf + q) mod 4 of block (tf + q) / 4: wd[a + q]
+          wq[q] = a == 0 ? wd[q] : a == 1 ? wd[q + 1]
+                : a == 2 ? wd[q + 2] : wd[q + 3];
+          kq[q] = s_guide[wq[q] >> 24];
+        }
+#pragma unroll
+        for (int q = 0; q < kPrefetch; ++q) tq[q] = s_thr[kq[q]];
 #pragma unroll
         for (int q = 0; q < kPrefetch; ++q) {
           if (q >= ng) continue;
-          // word (tf + q) mod 4 of block (tf + q) / 4: wd[a + q]
-          const uint32_t w = a == 0 ? wd[q] : a == 1 ? wd[q + 1]
-                           : a == 2 ? wd[q + 2] : wd[q + 3];
-          int k = s_guide[w >> 24];
-          while (k < c.n_thr - 1 && w >= s_thr[k]) ++k;
+          int k = kq[q];
+          if (k < c.n_thr - 1 && wq[q] >= tq[q]) {
+            ++k;
+            while (k < c.n_thr - 1 && wq[q] >= s_thr[k]) ++k;
+          }
           buf[q] += c.w_ext * (float)k;
         }
       }
