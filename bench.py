@@ -122,8 +122,8 @@ def stdp_config(w_e):
 # stands for the kernel it was measured on: the entry is used only while the
 # kernel sources (comments aside) hash to the recorded prefixes.
 TRAFFIC_B_PER_EVENT = {
-    "balanced-112500-fp32": (12.331, "cc8280a233936393", "ddb55fd96b82d881"),
-    "balanced-562500-bf16": (9.375, "cc8280a233936393", "ddb55fd96b82d881"),
+    "balanced-112500-fp32": (12.339, "09aa1a562d40154d", "19d84bddd44d9f03"),
+    "balanced-562500-bf16": (9.375, "09aa1a562d40154d", "19d84bddd44d9f03"),
 }
 # serving: a Poisson stream of independent balanced nets (BF16 records,
 # N log-uniform in [1,250, 112,500], 100 ms - 1 s each), mean rate in req/s
