@@ -120,6 +120,47 @@ def test_forced_spikes_weights_match_oracle(fmt, lam, alpha, w_max, bound):
         assert np.all(np.abs(rb - rb_o) <= 1e-4 * (np.abs(rb_o) + 1.0))
 
 
+def _plastic_geometry(n, n_exc, tw0, sms, k=4):
+    """The tile layout a plastic net takes (written out here from the rule:
+    the narrowest width, from max(64, ceil(n_exc / SMs)) up to the uniform
+    one, whose plastic tiles, one CTA each, plus the static tiles k to a CTA
+    fit one wave)."""
+    for tw in range(min(max(64, -(-n_exc // sms)), tw0), tw0 + 1):
+        nt, pt = -(-n // tw), -(-n_exc // tw)
+        if pt + -(-(nt - pt) // k) <= sms:
+            return tw, nt
+    return tw0, -(-n // tw0)
+
+
+def test_narrowed_plastic_tiles_weights_match_oracle():
+    """20,300 neurons: the plastic tiles narrow below the uniform width and
+    the static ones share CTAs four at a time (on 152 SMs: 142 plastic tiles
+    of 113 targets, 38 static ones, the last group of two); every plastic
+    weight still matches the oracle synapse by synapse."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n_e, n_i = 16000, 4300
+    net, store, ost = _nets(1, hist=16, lam=1.0, alpha=0.2, w_max=30.0,
+                            n_e=n_e, n_i=n_i, k_e=48, k_i=12, seed=31)
+    with net:
+        st = net.stats()
+        tw0 = max(-(-(n_e + n_i) // sms), 64)
+        tw, nt = _plastic_geometry(n_e + n_i, n_e, tw0, sms)
+        assert (st.tile_width, st.n_tiles) == (tw, nt)
+        assert tw < tw0
+        w_o, rb_o, n_pl = _run_forced(net, store, ost, 24, 0.05, seed=8)
+        st = net.stats()
+        assert st.error_flags == 0 and st.plastic_events == n_pl > 10000
+        rp, tg, dl, _ = net.read_store()
+        got = _canonical(rp, tg, dl, net.read_weights().astype(np.float64))
+        want = _canonical(store.row_ptr, store.tgt, store.delay, w_o)
+        for a, b in zip(got, want):
+            assert np.array_equal(a[:, :2], b[:, :2])
+            assert np.allclose(a[:, 2], b[:, 2], rtol=2e-5, atol=2e-5)
+        rb = net.read_rb()
+        assert np.all(np.abs(rb - rb_o) <= 1e-4 * (np.abs(rb_o) + 1.0))
+
+
 def test_short_history_counts_truncated_windows():
     # two post spikes kept: windows that reach further are counted
     net, store, ost = _nets(1, hist=2, lam=0.5, alpha=0.1, w_max=60.0)
