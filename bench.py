@@ -128,6 +128,12 @@ TRAFFIC_B_PER_EVENT = {
 # serving: a Poisson stream of independent balanced nets (BF16 records,
 # N log-uniform in [1,250, 112,500], 100 ms - 1 s each), mean rate in req/s
 SERVE_WORKLOADS = {"serve-poisson-20": 20.0}
+# L2 reduction throughput (red.global.add.f32, the ring-buffer additions):
+# buffers the size of the 112,500- and 562,500-neuron ring buffers (32 slots)
+# and one far beyond L2, scattered and sweeping cells
+PROBE_WORKLOADS = {"l2-red-probe": [(32 * 112500, "ring buffer, 112,500 neurons"),
+                                    (32 * 562500, "ring buffer, 562,500 neurons"),
+                                    (1 << 28, "1 GiB, beyond L2")]}
 
 
 # ---------------------------------------------------------------------------
@@ -1278,6 +1284,46 @@ def use_partition(workload: str, kind: str, world: int, partition: bool,
     return partitionable and (partition or (world > 1 and not replicas))
 
 
+def run_probe(args, sizes):
+    """Reductions per second of snn_probe_reductions per buffer size and
+    pattern: median of --steps timed launches after --warmup ones; the line's
+    value is the scattered rate at the first size."""
+    import torch
+    from paper_2109_12855_gb300 import snn
+    torch.cuda.set_device(0)
+    n_ops = 1 << 28
+    clocks = Clocks(0)
+    rows, launches = [], 0
+    clocks.start()
+    for n_cells, what in sizes:
+        buf = torch.zeros(n_cells, device="cuda")
+        for pattern, pname in ((snn.SNN_PROBE_SCATTER, "scatter"),
+                               (snn.SNN_PROBE_SWEEP, "sweep")):
+            for _ in range(args.warmup):
+                snn.snn_probe_reductions(buf, n_ops, pattern)
+            ms = sorted(snn.snn_probe_reductions(buf, n_ops, pattern)
+                        for _ in range(args.steps))
+            launches += args.warmup + args.steps
+            med = ms[len(ms) // 2]
+            rows.append({"cells": n_cells, "bytes": 4 * n_cells, "buffer": what,
+                         "pattern": pname, "ops": n_ops, "ms": med,
+                         "ops_per_s": n_ops / (med * 1e-3)})
+        del buf
+    clk = clocks.stop()
+    first = rows[0]
+    print(json.dumps({
+        "metric": "L2 reductions/s (red.global.add.f32, the ring-buffer additions)",
+        "value": first["ops_per_s"], "unit": "ops/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": first["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "ops_per_launch": n_ops,
+                   "l2": "the two ring-buffer sizes are L2-resident (the "
+                         "probe's own working set); the third exceeds L2"},
+        "probe": rows, "roofline": None, "cpu_baseline": None, "e2e": None,
+        "gpu_launches": launches, "clocks": clk}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1285,7 +1331,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) +
-                    sorted(SERVE_WORKLOADS), default=DEFAULT)
+                    sorted(SERVE_WORKLOADS) + sorted(PROBE_WORKLOADS),
+                    default=DEFAULT)
     ap.add_argument("--host-exchange", action="store_true",
                     help="with --partition: exchange through the host "
                          "(pending lists read back every interval)")
@@ -1323,6 +1370,16 @@ def main():
     args = ap.parse_args()
     nu_ext = args.nu_ext if args.nu_ext is not None else \
         NU_EXT_OF.get(args.workload, NU_EXT_8HZ)
+    if args.workload in PROBE_WORKLOADS:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the probe measures the GPU's L2; it has no "
+                              "CPU reference"}))
+            return
+        from paper_2109_12855_gb300 import build
+        build()
+        run_probe(args, PROBE_WORKLOADS[args.workload])
+        return
     if args.workload in SERVE_WORKLOADS:
         if args.impl == "reference":
             big = max(W.serving_stream(args.requests), key=lambda r:

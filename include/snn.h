@@ -551,6 +551,24 @@ uint64_t snn_debug_check_failures(void);
  * SNN_E_ARG for an index outside the store or an unknown field. */
 int snn_debug_poke_record(snn_net* net, uint64_t index, int field,
                           uint32_t value);
+/* Throughput probe of the L2 reductions that carry the ring-buffer
+ * additions of Algorithm REF (Section 3.2: rb[(t + d) mod S][target] += w;
+ * on the GPU one red.global.add.f32 per event in the atomic delivery, one
+ * per nonzero window cell in the tiled delivery's flush).  Adds 1.0f
+ * n_ops times into buf[n_cells]:
+ *  - buf: n_cells floats of DEVICE memory owned by the caller (not
+ *    cleared: each cell grows by the number of operations that hit it);
+ *  - pattern SNN_PROBE_SCATTER: operation k hits a hash of k scaled to
+ *    [0, n_cells) (scattered targets); SNN_PROBE_SWEEP: cell k mod n_cells
+ *    (32 consecutive cells per warp, like the flush);
+ *  - stream: a cudaStream_t (NULL: the legacy default stream); the call
+ *    synchronises it and returns in *ms the CUDA-event time of the launch.
+ * Errors: SNN_E_ARG (null or non-device buf, n_cells outside [1, 2^32),
+ * n_ops 0, unknown pattern), SNN_E_CUDA. */
+#define SNN_PROBE_SCATTER 0
+#define SNN_PROBE_SWEEP 1
+int snn_probe_reductions(float* buf, uint64_t n_cells, uint64_t n_ops,
+                         int pattern, void* stream, float* ms);
 /* The stream the net's work is enqueued on (*stream: a cudaStream_t; the
  * one given to snn_create, or the one the library created when none was
  * given).  Partitions that read each other's exchange buffers must share

@@ -23,6 +23,12 @@
 
 using namespace snn;
 
+namespace snn {
+// (snn_probe.cu)
+cudaError_t launch_red_probe(float* buf, uint32_t n_cells, uint64_t n_ops,
+                             int pattern, cudaStream_t s);
+}  // namespace snn
+
 namespace {
 
 thread_local std::string g_err;
@@ -1933,6 +1939,37 @@ int snn_sync(snn_net* net) {
   REQ(net, SNN_E_ARG, "null net");
   CK(cudaStreamSynchronize(net->stream));
   CK(cudaGetLastError());
+  return SNN_OK;
+}
+
+int snn_probe_reductions(float* buf, uint64_t n_cells, uint64_t n_ops,
+                         int pattern, void* stream, float* ms) {
+  REQ(buf && ms, SNN_E_ARG, "null argument");
+  REQ(n_cells >= 1 && n_cells < (1ull << 32), SNN_E_ARG,
+      "n_cells %llu outside [1, 2^32)", (unsigned long long)n_cells);
+  REQ(n_ops >= 1, SNN_E_ARG, "n_ops is 0");
+  REQ(pattern == SNN_PROBE_SCATTER || pattern == SNN_PROBE_SWEEP, SNN_E_ARG,
+      "unknown pattern %d", pattern);
+  cudaPointerAttributes pa;
+  const cudaError_t pe = cudaPointerGetAttributes(&pa, buf);
+  if (pe != cudaSuccess) cudaGetLastError();
+  REQ(pe == cudaSuccess && (pa.type == cudaMemoryTypeDevice ||
+                            pa.type == cudaMemoryTypeManaged),
+      SNN_E_ARG, "buf is not device memory");
+  CK(cudaSetDevice(pa.device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  cudaError_t e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaEventRecord(a, s);
+  if (e == cudaSuccess)
+    e = snn::launch_red_probe(buf, (uint32_t)n_cells, n_ops, pattern, s);
+  if (e == cudaSuccess) e = cudaEventRecord(b, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+  cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  CK(e);
   return SNN_OK;
 }
 

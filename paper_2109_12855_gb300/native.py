@@ -20,7 +20,8 @@ ROOT = os.path.dirname(PKG)
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsnn.so")
 LIB_CHECKED = os.path.join(PKG, "libsnn_check.so")
-SOURCES = ["snn_kernels.cu", "snn_build.cu", "snn_api.cu", "snn_serve.cu"]
+SOURCES = ["snn_kernels.cu", "snn_build.cu", "snn_api.cu", "snn_serve.cu",
+           "snn_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2", f"-I{os.path.join(ROOT, 'include')}"]

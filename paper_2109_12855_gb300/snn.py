@@ -49,6 +49,7 @@ EXPORTS = [
     "snn_debug_fail_allocations", "snn_exchange_capacity",
     "snn_set_exchange", "snn_deliver_exchanged", "snn_get_stream",
     "snn_checked", "snn_debug_check_failures", "snn_debug_poke_record",
+    "snn_probe_reductions",
 ]
 SNN_REQ_QUEUED, SNN_REQ_BUILDING, SNN_REQ_RUNNING, SNN_REQ_DONE = 0, 1, 2, 3
 SNN_REQ_FAILED = -1
@@ -219,6 +220,9 @@ def lib():
             "snn_get_stream": ([_P, C.POINTER(C.c_void_p)], C.c_int),
             "snn_checked": ([], C.c_int),
             "snn_debug_check_failures": ([], C.c_uint64),
+            "snn_probe_reductions": ([C.c_void_p, C.c_uint64, C.c_uint64,
+                                      C.c_int, C.c_void_p,
+                                      C.POINTER(C.c_float)], C.c_int),
             "snn_debug_poke_record": ([_P, C.c_uint64, C.c_int, C.c_uint32],
                                       C.c_int),
             "snn_set_exchange": ([_P, _P, C.c_uint64], C.c_int),
@@ -459,6 +463,21 @@ def snn_debug_poke_record(net, index: int, field: int, value: int):
     """Bounds-checked builds: corrupt one record's target (field 0) or delay
     (field 1)."""
     _check(lib().snn_debug_poke_record(net, index, field, value))
+
+
+SNN_PROBE_SCATTER, SNN_PROBE_SWEEP = 0, 1
+
+
+def snn_probe_reductions(buf, n_ops: int, pattern: int, stream: int = 0) -> float:
+    """Time n_ops L2 reductions (+1.0f) into the device float tensor buf
+    (scattered or sweeping cells); returns the launch's CUDA-event ms."""
+    ptr, mem = _buf(buf)
+    if mem != SNN_MEM_DEVICE or str(buf.dtype) != "torch.float32":
+        raise ValueError("buf must be a float32 device tensor")
+    ms = C.c_float()
+    _check(lib().snn_probe_reductions(ptr, buf.numel(), n_ops, pattern,
+                                      C.c_void_p(stream or None), C.byref(ms)))
+    return float(ms.value)
 
 
 def snn_get_stream(net) -> int:

@@ -102,11 +102,12 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
 
 def test_binding_constants_match_header(libpath):
     """The binding's copies of the header's constants (the allocation-free
-    scratch capacity, the status codes) equal the compiled values."""
+    scratch capacity, the status codes, the probe patterns) equal the
+    compiled values."""
     from paper_2109_12855_gb300 import snn
-    src = ('#include "snn.h"\n#include <stdio.h>\nint main(){printf("%u %d %d %d %u",'
+    src = ('#include "snn.h"\n#include <stdio.h>\nint main(){printf("%u %d %d %d %u %d %d",'
            '(unsigned)SNN_NOALLOC_MAX_SPIKES,SNN_E_ARG,SNN_E_STATE,SNN_E_TIMEOUT,'
-           '(unsigned)SNN_ERRF_CHECK);}')
+           '(unsigned)SNN_ERRF_CHECK,SNN_PROBE_SCATTER,SNN_PROBE_SWEEP);}')
     exe = os.path.join(ROOT, "paper_2109_12855_gb300", "_build", "consts")
     os.makedirs(os.path.dirname(exe), exist_ok=True)
     r = subprocess.run(["gcc", "-x", "c", "-I", os.path.join(ROOT, "include"),
@@ -116,4 +117,5 @@ def test_binding_constants_match_header(libpath):
     vals = [int(x) for x in subprocess.run([exe], capture_output=True,
                                            text=True).stdout.split()]
     assert vals == [snn.SNN_NOALLOC_MAX_SPIKES, snn.SNN_E_ARG, snn.SNN_E_STATE,
-                    snn.SNN_E_TIMEOUT, snn.SNN_ERRF_CHECK]
+                    snn.SNN_E_TIMEOUT, snn.SNN_ERRF_CHECK, snn.SNN_PROBE_SCATTER,
+                    snn.SNN_PROBE_SWEEP]
