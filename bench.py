@@ -139,6 +139,10 @@ PROBE_WORKLOADS = {"l2-red-probe": [(32 * 112500, "ring buffer, 112,500 neurons"
 # ---------------------------------------------------------------------------
 # helpers
 # ---------------------------------------------------------------------------
+# the nominal HBM3e bandwidth of the part, reported beside the measured copy
+HBM_NOMINAL_GBS = 7900.0
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -809,6 +813,7 @@ def run_ours(args, wl, fmt, bio_ms, kind, nu_ext):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm,
                      "peak_source": peak_kind,
+                     "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
                      "traffic": measured_traffic(args.workload,
                                                  ev_prof / max(n_del, 1)),
                      "traffic_unit": "bytes per launch (ncu dram read+write)",
