@@ -322,13 +322,13 @@ void choose_tiles(uint32_t n, int window, int32_t hint, size_t per_target,
 }
 
 // Plastic nets: a tile of excitatory targets applies the weight rule to its
-// E->E events, several times the work of a static tile of the same width
-// (measured: 3 to 5 times), and every tile takes a whole SM.  The static
-// tiles after the plastic ones therefore go kStaticTilesPerCta to a CTA,
-// and the width becomes the smallest (at least the chosen one's floor of
-// 64) whose CTAs still fit one wave, so that the plastic tiles are as narrow
-// as the SM count allows.  Nets already needing more than one wave keep
-// their geometry, one tile per CTA.
+// E->E events, about four times the work of a static tile of the same width
+// on the benchmark network, and every tile takes a whole SM.  The static
+// tiles after the plastic ones therefore go kStaticTilesPerCta to a CTA, and
+// the width becomes the smallest in [max(64, ceil(n_exc / SMs)), chosen
+// width] whose CTAs still fit one wave, so that the plastic tiles are as
+// narrow as the SM count allows.  Nets already needing more than one wave
+// keep their geometry, one tile per CTA.
 constexpr uint32_t kStaticTilesPerCta = 4;
 void balance_plastic_tiles(uint32_t n, uint32_t n_exc, uint32_t* tile_w,
                            int* lo_bits, uint32_t* n_tiles, uint32_t* pl_tiles,
