@@ -23,9 +23,11 @@ names the passage of the paper it follows:
   scheme driven by presynaptic spikes, weights computed at delivery; the
   cited pair-based power-law rule), with the readings stated in the C source.
 
-Parity unpinned: none of these has a worked example in the paper; all are
-pinned in ``tests/test_oracle_pins.py`` by closed forms, library routines,
-brute force and invariants.
+Pins: the paper prints no worked example, so none of these can be checked
+against numbers it prints; every one is pinned in
+``tests/test_oracle_pins.py`` (and ``tests/test_oracle_stdp.py``,
+``tests/test_oracle_threaded.py``) by closed forms, library routines, brute
+force and invariants.
 """
 from __future__ import annotations
 

@@ -32,9 +32,10 @@
  * its published definition (Salmon, Moraes, Dror & Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11).
  *
- * Parity unpinned: nothing here (the paper prints no worked example; its
- * model numbers live in a cited external table).  Every function is pinned
- * by closed forms, library routines, brute force or invariants in the tests.
+ * Pins: the paper prints no worked example (its model numbers live in a
+ * cited external table), so no function here can be checked against numbers
+ * it prints; every function is pinned by closed forms, library routines,
+ * brute force or invariants in the tests.
  */
 #include <math.h>
 #include <stdint.h>
