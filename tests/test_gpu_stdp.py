@@ -132,7 +132,8 @@ def _plastic_geometry(n, n_exc, tw0, sms, k=4):
     return tw0, -(-n // tw0)
 
 
-def test_narrowed_plastic_tiles_weights_match_oracle():
+@pytest.mark.parametrize("fmt", [0, 1], ids=["fp32", "bf16"])
+def test_narrowed_plastic_tiles_weights_match_oracle(fmt):
     """20,300 neurons: the plastic tiles narrow below the uniform width and
     the static ones share CTAs four at a time (on 152 SMs: 142 plastic tiles
     of 113 targets, 38 static ones, the last group of two); every plastic
@@ -140,7 +141,7 @@ def test_narrowed_plastic_tiles_weights_match_oracle():
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     n_e, n_i = 16000, 4300
-    net, store, ost = _nets(1, hist=16, lam=1.0, alpha=0.2, w_max=30.0,
+    net, store, ost = _nets(fmt, hist=16, lam=1.0, alpha=0.2, w_max=30.0,
                             n_e=n_e, n_i=n_i, k_e=48, k_i=12, seed=31)
     with net:
         st = net.stats()
