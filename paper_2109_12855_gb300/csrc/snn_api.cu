@@ -1956,19 +1956,22 @@ int snn_probe_reductions(float* buf, uint64_t n_cells, uint64_t n_ops,
   REQ(pe == cudaSuccess && (pa.type == cudaMemoryTypeDevice ||
                             pa.type == cudaMemoryTypeManaged),
       SNN_E_ARG, "buf is not device memory");
+  int prev = 0;
+  CK(cudaGetDevice(&prev));
   CK(cudaSetDevice(pa.device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t a = nullptr, b = nullptr;
-  CK(cudaEventCreate(&a));
-  cudaError_t e = cudaEventCreate(&b);
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
   if (e == cudaSuccess) e = cudaEventRecord(a, s);
   if (e == cudaSuccess)
     e = snn::launch_red_probe(buf, (uint32_t)n_cells, n_ops, pattern, s);
   if (e == cudaSuccess) e = cudaEventRecord(b, s);
   if (e == cudaSuccess) e = cudaEventSynchronize(b);
   if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
-  cudaEventDestroy(a);
+  if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
+  cudaSetDevice(prev);  // the caller's current device, as it was
   CK(e);
   return SNN_OK;
 }
