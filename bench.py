@@ -86,6 +86,11 @@ WORKLOADS = {
     "balanced-20000-fp32-45hz": (W.Balanced("balanced-20000", 16000, 4000,
                                             9000, 2250, 15, 15, "fp32", 0.0,
                                             150.0), 0, 150.0, "simulate"),
+    # the same 45 Hz network with BF16 8-byte records (the launch shape of
+    # the 1.27e9-synapse BF16 delivery)
+    "balanced-20000-bf16-45hz": (W.Balanced("balanced-20000", 16000, 4000,
+                                            9000, 2250, 15, 15, "bf16", 0.0,
+                                            150.0), 1, 150.0, "simulate"),
     # 93,750 neurons, in-degree 1,900, delays 10..20, BF16 with spread,
     # driven to ~47 Hz: ~4,400 spikes per 10-step interval and runs of ~25
     # records, the per-CTA shape of the 6.3e9-synapse delivery, on a 1.4 GB
@@ -97,6 +102,7 @@ WORKLOADS = {
 # drive of the profiling cases above (found with paper_2109_12855_gb300.tune
 # on a GB300 for the rates stated; all other workloads use NU_EXT_8HZ)
 NU_EXT_OF = {"balanced-20000-fp32-45hz": 89526.3671875,
+             "balanced-20000-bf16-45hz": 89526.3671875,
              "balanced-93750-k1900-bf16": 35632.32421875}
 DEFAULT = "balanced-112500-fp32"
 PLASTIC = {"balanced-112500-stdp-bf16", "stdp-20000-bf16"}
@@ -114,15 +120,17 @@ def stdp_config(w_e):
                 w_max=100.0, history=16)
 # DRAM bytes (read + write) per synaptic event of k_deliver_tiled, measured
 # by ncu on launches of a small simulated case (a few GB on the device; for
-# the 1.27e9-synapse network with its launch shape: in-degree, runs per
-# tile, window; for the 6.3e9 one a short-run BF16 case, whose runs are
-# shorter than the full network's) and divided by those launches' events
+# the 1.27e9-synapse network, FP32 and BF16, with its launch shape:
+# in-degree, runs per tile, window; for the 6.3e9 one a short-run BF16 case,
+# whose runs are shorter than the full network's) and divided by those
+# launches' events
 # (profiles/dram_k_deliver_tiled_*.md); bench.py scales it by the events of
 # an average full-size launch.  It
 # stands for the kernel it was measured on: the entry is used only while the
 # kernel sources (comments aside) hash to the recorded prefixes.
 TRAFFIC_B_PER_EVENT = {
     "balanced-112500-fp32": (12.339, "09aa1a562d40154d", "19d84bddd44d9f03"),
+    "balanced-112500-bf16": (8.332, "09aa1a562d40154d", "19d84bddd44d9f03"),
     "balanced-562500-bf16": (9.375, "09aa1a562d40154d", "19d84bddd44d9f03"),
 }
 # serving: a Poisson stream of independent balanced nets (BF16 records,
